@@ -1,0 +1,347 @@
+#!/usr/bin/env python3
+"""Benchmark of the sparse Sinkhorn-Knopp WMD on GB300.
+
+One step = one query against the whole resident corpus: the cdist/K build
+(K1) and the fused SDDMM+SpMM loop with the final reduction (K2+K3), i.e. all
+N WMD values for the paper-shaped workload (V=100000, d=300, N=5000
+documents of 20-150 Zipf(1.1) words, v_r=30, lambda=10, max_iter=15).
+
+Prints ONE JSON line (rank 0).  ``--impl reference`` times the FP64 CPU
+oracle on the host cores instead (the reference arm; there is no runnable
+reference implementation of the paper).  Multi-GPU runs (torchrun) are
+independent replicas: every rank answers the same query stream against its
+own copy of the corpus, with no data-path collective.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2005_06727_gb300 import synth  # noqa: E402
+
+METRIC = "query x doc WMDs/sec @15 iters, HBM GB/s % of peak; served p50/p99 latency"
+UNIT = "WMDs/s"
+L2_FLUSH_BYTES = 512 << 20
+FP32_LANES_PER_SM = 128
+NUM_SMS = 152
+WORKLOADS = {"paper": synth.PAPER, "tiny": synth.TINY, "large": synth.LARGE}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="paper")
+    ap.add_argument("--prec", choices=["fp32", "bf16"], default="fp32")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    return (int(os.environ.get("RANK", 0)), int(os.environ.get("LOCAL_RANK", 0)),
+            int(os.environ.get("WORLD_SIZE", 1)))
+
+
+def workload_name(w):
+    return (f"{w.name}: V={w.V} d={w.d} N={w.N} docs of {w.doc_lo}-{w.doc_hi} Zipf(1.1) words, "
+            f"v_r={w.vr_lo}, lambda={w.lam:g}, max_iter={w.max_iter}")
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+def recorded_traffic(kernel: str):
+    """DRAM bytes per launch from a committed ncu summary, if the kernel's
+    source is unchanged since the counters were taken."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        rec = json.load(open(path)).get(kernel)
+    except (OSError, ValueError):
+        return None
+    if not rec:
+        return None
+    src = os.path.join(ROOT, "paper_2005_06727_gb300", "csrc", rec["source"])
+    try:
+        sha = hashlib.sha256(open(src, "rb").read()).hexdigest()
+    except OSError:
+        return None
+    return rec["bytes_per_launch"] if sha == rec["source_sha256"] else None
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons while timing."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device: int):
+        self.device = device
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100", "-i", str(self.device)],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.thread.join(timeout=2)
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx = float(parts[2])
+            except ValueError:
+                continue
+            for nm, flag in zip(names, parts[5:9]):
+                if flag.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ------------------------------------------------------------------ oracle
+def time_oracle(w, vecs, c, q_ids, q_w, docs=None):
+    from oracle import sinkhorn_wmd as orc
+    t0 = time.perf_counter()
+    out = orc.sinkhorn_wmd_sparse(q_ids, q_w, c.row_ptr, c.doc_idx, c.val, c.N, vecs, w.lam,
+                                  w.max_iter, docs=docs)
+    return time.perf_counter() - t0, out
+
+
+def cpu_baseline(w, vecs, c, q_ids, q_w, budget_s=10.0):
+    """The oracle as it stands, whole queries, repeated until ~budget_s."""
+    times = []
+    while sum(times) < budget_s and len(times) < 5:
+        t, _ = time_oracle(w, vecs, c, q_ids, q_w)
+        times.append(t)
+    t = statistics.mean(times)
+    return {"value": w.N / t, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{len(times)} full queries (all {w.N} documents, v_r={len(q_ids)}), "
+                      f"FP64 numpy/scipy oracle, single thread, mean {t:.2f} s per query"}
+
+
+def run_reference(args, w):
+    rank, _, world = dist_env()
+    if rank != 0:
+        return
+    vecs, c, qs = synth.make_workload(w)
+    q_ids, q_w = qs[0]
+    # each step: a rotating window of documents, sized so that the whole run
+    # stays within a few minutes of CPU time
+    per_step = min(c.N, 1000)
+    steps = []
+    for k in range(args.warmup + args.steps):
+        docs = (np.arange(per_step) + k * per_step) % c.N
+        t, _ = time_oracle(w, vecs, c, q_ids, q_w, docs=docs)
+        if k >= args.warmup:
+            steps.append(t)
+    t = statistics.mean(steps)
+    value = per_step / t
+    sample = (f"{per_step} documents per step (rotating window of the {c.N}), M computed for "
+              f"their words only, FP64 numpy/scipy oracle, single thread")
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": workload_name(w), "impl": "FP64 CPU oracle"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }))
+
+
+# ------------------------------------------------------------------ ours
+def run_ours(args, w):
+    import torch
+    import torch.distributed as dist
+
+    rank, local_rank, world = dist_env()
+    if world > 1:
+        dist.init_process_group("nccl", init_method="env://")
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+
+    from paper_2005_06727_gb300 import build as build_mod
+    build_mod.build()
+    from paper_2005_06727_gb300 import wmd
+
+    prec = wmd.PREC_BF16_K if args.prec == "bf16" else wmd.PREC_FP32
+    vecs, c, qs = synth.make_workload(w)
+    q_ids, q_w = qs[0]
+    corpus = wmd.Corpus.from_synth(vecs, c, device=local_rank)
+    dq = wmd.DeviceQuery(corpus, q_ids, q_w, prec)
+    v_r = dq.v_r
+    stream = torch.cuda.current_stream(dev)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+
+    def step():
+        corpus.build_kernel_matrix(dq.ids, dq.w, v_r, w.lam, prec, dq.ws, dq.ws_bytes, stream)
+        corpus.sinkhorn_loop(v_r, w.lam, w.max_iter, prec, dq.ws, dq.ws_bytes, dq.out, stream)
+
+    for _ in range(max(args.warmup, 3)):
+        flush.zero_()
+        step()
+    torch.cuda.synchronize()
+
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True),
+           torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    clocks = ClockSampler(local_rank)
+    clocks.start()
+    time.sleep(0.3)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    for k in range(args.steps):
+        flush.zero_()                       # L2 flush (untimed, between steps)
+        e0, e1, e2 = ev[k]
+        e0.record(stream)
+        corpus.build_kernel_matrix(dq.ids, dq.w, v_r, w.lam, prec, dq.ws, dq.ws_bytes, stream)
+        e1.record(stream)
+        corpus.sinkhorn_loop(v_r, w.lam, w.max_iter, prec, dq.ws, dq.ws_bytes, dq.out, stream)
+        e2.record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clk = clocks.stop()
+
+    cdist_ms = sum(a.elapsed_time(b) for a, b, _ in ev) / args.steps
+    loop_ms = sum(b.elapsed_time(cc) for _, b, cc in ev) / args.steps
+    step_ms = sum(a.elapsed_time(cc) for a, _, cc in ev) / args.steps
+    t = torch.tensor([step_ms], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    step_ms_max = float(t.item())
+    value = world * c.N / (step_ms_max * 1e-3)
+
+    # end to end through the public host API: pinned query in, WMD[N] out
+    h_ids = torch.from_numpy(np.ascontiguousarray(q_ids)).pin_memory()
+    h_w = torch.from_numpy(np.ascontiguousarray(q_w)).pin_memory()
+    h_out = torch.empty(c.N, dtype=torch.float64).pin_memory()
+    ids_np, w_np, out_np = h_ids.numpy(), h_w.numpy(), h_out.numpy()
+    for _ in range(2):
+        corpus.query(ids_np, w_np, w.lam, w.max_iter, prec, out=out_np)
+    e2e_t = []
+    for _ in range(args.steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        corpus.query(ids_np, w_np, w.lam, w.max_iter, prec, out=out_np)
+        e2e_t.append(time.perf_counter() - t0)
+    e2e_ms = statistics.mean(e2e_t) * 1e3
+    te = torch.tensor([e2e_ms], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(te, op=dist.ReduceOp.MAX)
+    e2e_value = world * c.N / (float(te.item()) * 1e-3)
+    dev_out = dq.out[: c.N].cpu().numpy()
+    assert np.array_equal(dev_out, out_np), "device and host paths disagree"
+
+    # roofline of the dominant kernel
+    peaks, peak_kind = measured_peaks()
+    U, ldv = corpus.U, (w.d + 3) // 4 * 4
+    VR = 8
+    while VR < v_r:
+        VR *= 2
+    kelem = 2 if prec == wmd.PREC_BF16_K else 4
+    cdist_bytes = U * ldv * 4 + U * VR * kelem + U * 4 + v_r * ldv * 4
+    loop_flops = 4.0 * v_r * c.nnz * (w.max_iter + 1)
+    alu_peak = NUM_SMS * FP32_LANES_PER_SM * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6
+    kernels = {
+        "cdist_k": {"ms": cdist_ms, "bound": "hbm", "bytes": cdist_bytes,
+                    "achieved_gbs": cdist_bytes / (cdist_ms * 1e-3) / 1e9},
+        "sinkhorn_fused": {"ms": loop_ms, "bound": "alu", "flops": loop_flops,
+                           "achieved_tflops": loop_flops / (loop_ms * 1e-3) / 1e12,
+                           "k_gather_bytes": c.nnz * VR * kelem},
+    }
+    if cdist_ms >= loop_ms:
+        ach = cdist_bytes / (cdist_ms * 1e-3) / 1e9
+        roof = {"kernel": "cdist_k", "bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"],
+                "unit": "GB/s", "frac": ach / peaks["hbm_gbs"],
+                "traffic": recorded_traffic("cdist_k"),
+                "peak_source": f"{peak_kind} hbm_gbs (copy, burst)"}
+    else:
+        ach = loop_flops / (loop_ms * 1e-3) / 1e12
+        pk = alu_peak / 1e12
+        roof = {"kernel": "sinkhorn_fused", "bound": "alu", "achieved": ach, "peak": pk,
+                "unit": "TFLOP/s", "frac": ach / pk, "traffic": recorded_traffic("sinkhorn_fused"),
+                "peak_source": "152 SMs x 128 FP32 lanes x 2 flop x max SM clock"}
+
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": max(args.warmup, 3), "ms_per_step": step_ms_max, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32" if prec == wmd.PREC_FP32 else "bf16-K/f32",
+        "data": "synthetic (seeded Zipf(1.1) corpus, N(0,1/d) embeddings)",
+        "config": {"workload": workload_name(w), "v_r": v_r, "nnz": c.nnz, "active_words": U,
+                   "l2": "flushed between steps (512 MiB write)",
+                   "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(v_r * 8),
+                "d2h_bytes_per_step": int(c.N * 8), "ms_per_step": e2e_ms,
+                "path": "wmd_query (host buffers, pinned)"},
+        "roofline": roof,
+        "kernels": kernels,
+        "gpu_launches": 2 * args.steps,
+        "clocks": clk,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(w, vecs, c, q_ids, q_w)
+    if rank == 0:
+        print(json.dumps(out))
+    corpus.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    w = WORKLOADS[args.workload]
+    if args.impl == "reference":
+        run_reference(args, w)
+    else:
+        run_ours(args, w)
+
+
+if __name__ == "__main__":
+    main()

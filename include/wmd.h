@@ -1,0 +1,180 @@
+/*
+ * wmd.h -- C ABI of the GB300 sparse Sinkhorn-Knopp Word Mover's Distance.
+ *
+ * The library computes, for one query histogram r and many target histograms
+ * c (the columns of a V x N sparse matrix), the Sinkhorn distance of
+ * Algorithm 1 of Tithi & Petrini, "An Efficient Shared-memory Parallel
+ * Sinkhorn-Knopp Algorithm to Compute the Word Mover's Distance"
+ * (arXiv 2005.06727), in the sparse SDDMM + SpMM form of its Sec. 3:
+ *
+ *   I = (r > 0); M[i, w] = ||vecs[q_i] - vecs[w]||_2 (Sec. 2, unsquared);
+ *   K = exp(-lambda M);  x = 1/v_r;
+ *   repeat max_iter times:  u = 1/x;  v = c ./ (K^T u) at the nonzeros of c
+ *                           (SDDMM);  x = diag(1/r) K v  (SpMM)
+ *   u = 1/x;  v = c ./ (K^T u);  WMD_j = sum_i u_ij ((K .* M) v)_ij.
+ *
+ * Conventions shared by every entry point:
+ *  - All functions return a wmd_status; on failure wmd_last_error() returns a
+ *    thread-local message describing the first error.  No entry point aborts
+ *    or traps; CUDA errors are reported as WMD_ERR_CUDA.
+ *  - "host" pointers are ordinary CPU memory borrowed for the duration of the
+ *    call; "device" pointers are CUDA global memory on the corpus's device.
+ *    The caller owns every buffer it passes; the library owns the corpus and
+ *    server objects and the device copies inside them.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = the legacy default
+ *    stream).  Device-path entry points only enqueue work on it.
+ *  - No renormalisation: r and the columns of c are used exactly as given,
+ *    the paper assumes both sum to 1 (Sec. 3).
+ *  - lambda > 0 and K = exp(-lambda M) (Algorithm 1; the paper's Python passes
+ *    lambda negated, which this API does not).
+ *  - Results follow the IEEE arithmetic of the formula: a document without
+ *    words gives NaN when max_iter >= 1 (u = 1/0 meets a zero column) and 0
+ *    when max_iter == 0.
+ *  - Arithmetic: float32 for the loop (the BF16_K precision stores K in
+ *    bfloat16 and still accumulates in float32), float64 for the final
+ *    per-document sum.  Valid while lambda * max(M) < 87 so that K stays a
+ *    normal float32.
+ */
+#ifndef WMD_GB300_H
+#define WMD_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum wmd_status {
+  WMD_OK = 0,
+  WMD_ERR_INVALID_ARG = 1,   /* a size, pointer, id or weight is invalid       */
+  WMD_ERR_OUT_OF_MEMORY = 2, /* a device or host allocation failed, or an
+                                admission budget is exceeded                    */
+  WMD_ERR_CUDA = 3,          /* a CUDA runtime call or kernel launch failed     */
+  WMD_ERR_NOT_READY = 4,     /* a served request has not finished yet          */
+  WMD_ERR_TIMEOUT = 5,       /* a bounded wait ran out                         */
+  WMD_ERR_SHUTDOWN = 6,      /* the server is shutting down                    */
+  WMD_ERR_UNSUPPORTED = 7    /* e.g. v_r above WMD_MAX_VR                      */
+} wmd_status;
+
+typedef enum wmd_precision {
+  WMD_PREC_FP32 = 0,   /* K stored and used in float32                        */
+  WMD_PREC_BF16_K = 1  /* K stored in bfloat16, loop arithmetic in float32     */
+} wmd_precision;
+
+/* Largest number of query words (after dropping zero weights) per query. */
+#define WMD_MAX_VR 256
+
+typedef struct wmd_corpus wmd_corpus; /* opaque, owned by the library */
+typedef struct wmd_server wmd_server; /* opaque, owned by the library */
+
+typedef struct wmd_corpus_info {
+  int64_t V;        /* vocabulary size (rows of vecs and of c)               */
+  int32_t d;        /* embedding width                                       */
+  int64_t N;        /* number of target documents (columns of c)             */
+  int64_t nnz;      /* nonzeros of c                                         */
+  int64_t U;        /* active vocabulary: words that occur in some document  */
+  int32_t device;   /* CUDA device holding the corpus                        */
+  size_t device_bytes; /* device memory held by the corpus                   */
+} wmd_corpus_info;
+
+/* Thread-local description of the last failure in this thread ("" if none). */
+const char* wmd_last_error(void);
+
+/* Library version string. */
+const char* wmd_version(void);
+
+/* ---------------------------------------------------------------------------
+ * Query compaction (Algorithm 1, first line: I = (r > 0)).  Host only, no GPU.
+ * q_ids[n_q], q_w[n_q]: the sparse query r as (word id, weight) pairs, host.
+ * Entries with weight 0 are dropped; the kept pairs are written, in input
+ * order, to out_ids / out_w (host, capacity n_q each) and their count to
+ * *out_vr.  Errors (WMD_ERR_INVALID_ARG): an id outside [0, V), a duplicate id
+ * among the kept entries, a negative, NaN or infinite weight, n_q < 0.
+ * WMD_ERR_UNSUPPORTED: more than WMD_MAX_VR kept entries.
+ * ------------------------------------------------------------------------- */
+wmd_status wmd_compact_query(const int32_t* q_ids, const float* q_w, int32_t n_q,
+                             int64_t V, int32_t* out_ids, float* out_w,
+                             int32_t* out_vr);
+
+/* ---------------------------------------------------------------------------
+ * Corpus load (Sec. 3 inputs `vecs` and `c`).  Host buffers, synchronous.
+ * vecs:    V x d float32, row-major (row w = embedding of word w), host.
+ * c:       the paper's V x N CSR with rows = words: row_ptr[V+1] (int64,
+ *          row_ptr[0] = 0, non-decreasing, row_ptr[V] = nnz), doc_idx[nnz]
+ *          (int32 document ids in [0, N), strictly increasing within a row),
+ *          val[nnz] (float32, finite and > 0).  All host.
+ * device:  CUDA device ordinal that will hold the corpus.
+ * On success *out receives a corpus that keeps vecs, the row norms, and a
+ * document-major copy of c resident on the device until wmd_corpus_free.
+ * Errors: WMD_ERR_INVALID_ARG for any malformed input (checked on the host
+ * before anything is copied), WMD_ERR_OUT_OF_MEMORY, WMD_ERR_CUDA.
+ * ------------------------------------------------------------------------- */
+wmd_status wmd_corpus_load(const float* vecs, int64_t V, int32_t d,
+                           const int64_t* row_ptr, const int32_t* doc_idx,
+                           const float* val, int64_t N, int64_t nnz,
+                           int32_t device, wmd_corpus** out);
+
+/* Frees a corpus (NULL is accepted).  The caller must not free a corpus that
+ * a server or an in-flight device call still uses. */
+void wmd_corpus_free(wmd_corpus* corpus);
+
+wmd_status wmd_corpus_get_info(const wmd_corpus* corpus, wmd_corpus_info* out);
+
+/* ---------------------------------------------------------------------------
+ * One query, host buffers, synchronous (Sec. 3 `sinkhorn_wmd(r, c, vecs,
+ * lamda, max_iter)`).  q_ids/q_w: sparse query as in wmd_compact_query (host).
+ * out_wmd: host array of N doubles, WMD_j for every document j.
+ * The call compacts and validates the query on the host, copies it to the
+ * device, runs the cdist/K build and the fused loop, and copies the result
+ * back.  Calls on one corpus are serialised by an internal lock.
+ * Errors: those of wmd_compact_query, WMD_ERR_INVALID_ARG for lambda <= 0 or
+ * non-finite, max_iter < 0 or an empty query (v_r = 0), WMD_ERR_CUDA.
+ * ------------------------------------------------------------------------- */
+wmd_status wmd_query(wmd_corpus* corpus, const int32_t* q_ids, const float* q_w,
+                     int32_t n_q, float lambda, int32_t max_iter,
+                     wmd_precision prec, double* out_wmd);
+
+/* ---------------------------------------------------------------------------
+ * Device-resident path.  Stream ordered; nothing is synchronised.
+ *
+ * wmd_workspace_bytes: size of the caller-provided device workspace that the
+ * calls below need for a query of v_r words (0 < v_r <= WMD_MAX_VR).
+ *
+ * d_q_ids[v_r], d_q_w[v_r]: the COMPACTED query on the device (ids in [0, V),
+ * unique, weights > 0 -- e.g. the output of wmd_compact_query).  The kernels
+ * never read outside the corpus for an out-of-range id: its column of K
+ * becomes NaN and so does every result, but uniqueness is not re-checked.
+ * d_ws: device workspace of at least wmd_workspace_bytes(...) bytes, 256-byte
+ * aligned; it holds the query rows, 1/r and K between the two stages.
+ * d_out: device array of N doubles.
+ *
+ * wmd_build_kernel_matrix (Sec. 2 distance, Sec. 5 GEMM-type cdist,
+ * Algorithm 1 line K = exp(-lambda M)): K[w, i] for every active word w,
+ * word-major (the "on the fly transpose" of Sec. 3).
+ * wmd_sinkhorn_loop (Algorithm 1 loop and final reduction; the fused
+ * SDDMM_SpMM kernel of Sec. 3): max_iter iterations plus the final reduction
+ * for all N documents, reading K from the workspace.
+ * wmd_query_device: both stages.
+ * ------------------------------------------------------------------------- */
+size_t wmd_workspace_bytes(const wmd_corpus* corpus, int32_t v_r, wmd_precision prec);
+
+wmd_status wmd_build_kernel_matrix(wmd_corpus* corpus, const int32_t* d_q_ids,
+                                   const float* d_q_w, int32_t v_r, float lambda,
+                                   wmd_precision prec, void* d_ws, size_t ws_bytes,
+                                   void* stream);
+
+wmd_status wmd_sinkhorn_loop(wmd_corpus* corpus, int32_t v_r, float lambda,
+                             int32_t max_iter, wmd_precision prec, void* d_ws,
+                             size_t ws_bytes, double* d_out, void* stream);
+
+wmd_status wmd_query_device(wmd_corpus* corpus, const int32_t* d_q_ids,
+                            const float* d_q_w, int32_t v_r, float lambda,
+                            int32_t max_iter, wmd_precision prec, void* d_ws,
+                            size_t ws_bytes, double* d_out, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* WMD_GB300_H */

@@ -1,0 +1,384 @@
+// Host side of the C ABI: validation, corpus load, schedules and the query
+// entry points.  All device work is done by the kernels in cdist.cu and
+// sinkhorn.cu; nothing here computes a distance or a scaling vector.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <numeric>
+#include <vector>
+
+#include "wmd_internal.h"
+
+namespace wmd {
+
+namespace {
+thread_local std::string g_last_error;
+
+size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int dev) {
+    cudaGetDevice(&prev);
+    if (prev != dev) cudaSetDevice(dev);
+  }
+  ~DeviceGuard() {
+    int cur = -1;
+    cudaGetDevice(&cur);
+    if (prev >= 0 && cur != prev) cudaSetDevice(prev);
+  }
+};
+
+template <typename T>
+cudaError_t upload(T** dst, const T* src, size_t count, size_t* bytes) {
+  *dst = nullptr;
+  size_t b = std::max<size_t>(count, 1) * sizeof(T);
+  cudaError_t e = cudaMalloc(reinterpret_cast<void**>(dst), b);
+  if (e != cudaSuccess) return e;
+  *bytes += b;
+  if (count) e = cudaMemcpy(*dst, src, count * sizeof(T), cudaMemcpyHostToDevice);
+  return e;
+}
+
+void free_corpus_device(wmd_corpus* c) {
+  cudaFree(c->vecs);
+  cudaFree(c->norms);
+  cudaFree(c->perm);
+  cudaFree(c->doc_ptr);
+  cudaFree(c->doc_words);
+  cudaFree(c->doc_vals);
+  cudaFree(c->order);
+  for (auto& s : c->sched) cudaFree(s.d_items);
+  cudaFree(c->ws);
+  cudaFree(c->d_qids);
+  cudaFree(c->d_qw);
+  cudaFree(c->d_out);
+  if (c->stream) cudaStreamDestroy(c->stream);
+}
+
+wmd_status check_query_args(const wmd_corpus* c, int v_r, float lambda, int T) {
+  if (!c) return set_error(WMD_ERR_INVALID_ARG, "corpus is NULL");
+  if (v_r <= 0) return set_error(WMD_ERR_INVALID_ARG, "query has no word with positive weight");
+  if (v_r > WMD_MAX_VR) return set_error(WMD_ERR_UNSUPPORTED, "v_r exceeds WMD_MAX_VR");
+  if (!(lambda > 0.f) || !std::isfinite(lambda))
+    return set_error(WMD_ERR_INVALID_ARG, "lambda must be positive and finite");
+  if (T < 0) return set_error(WMD_ERR_INVALID_ARG, "max_iter must be >= 0");
+  return WMD_OK;
+}
+
+wmd_status check_ws(const wmd_corpus* c, int v_r, wmd_precision prec, const void* ws,
+                    size_t ws_bytes) {
+  if (prec != WMD_PREC_FP32 && prec != WMD_PREC_BF16_K)
+    return set_error(WMD_ERR_INVALID_ARG, "unknown precision");
+  if (!ws) return set_error(WMD_ERR_INVALID_ARG, "workspace is NULL");
+  if (reinterpret_cast<uintptr_t>(ws) % 256)
+    return set_error(WMD_ERR_INVALID_ARG, "workspace must be 256-byte aligned");
+  const WsLayout L = ws_layout(c, kClassVR[vr_class(v_r)], prec);
+  if (ws_bytes < L.total) return set_error(WMD_ERR_INVALID_ARG, "workspace too small");
+  return WMD_OK;
+}
+
+}  // namespace
+
+wmd_status set_error(wmd_status st, const std::string& msg) {
+  g_last_error = msg;
+  return st;
+}
+
+wmd_status cuda_error(cudaError_t e, const char* what) {
+  g_last_error = std::string(what) + ": " + cudaGetErrorString(e);
+  return e == cudaErrorMemoryAllocation ? WMD_ERR_OUT_OF_MEMORY : WMD_ERR_CUDA;
+}
+
+WsLayout ws_layout(const wmd_corpus* c, int VR, wmd_precision prec) {
+  WsLayout L;
+  size_t o = 0;
+  L.r_off = o;    o = align_up(o + (size_t)VR * sizeof(float), 256);
+  L.k_off = o;
+  const size_t kelem = prec == WMD_PREC_BF16_K ? 2 : 4;
+  o = align_up(o + (size_t)std::max<int64_t>(c->U, 1) * VR * kelem, 256);
+  L.total = o;
+  return L;
+}
+
+}  // namespace wmd
+
+using namespace wmd;
+
+extern "C" {
+
+const char* wmd_last_error(void) { return g_last_error.c_str(); }
+
+const char* wmd_version(void) { return "wmd-gb300 0.1 (sm_103a)"; }
+
+wmd_status wmd_compact_query(const int32_t* q_ids, const float* q_w, int32_t n_q, int64_t V,
+                             int32_t* out_ids, float* out_w, int32_t* out_vr) {
+  if (n_q < 0) return set_error(WMD_ERR_INVALID_ARG, "n_q < 0");
+  if (!out_vr || (n_q > 0 && (!q_ids || !q_w || !out_ids || !out_w)))
+    return set_error(WMD_ERR_INVALID_ARG, "NULL pointer");
+  int32_t k = 0;
+  std::vector<int32_t> seen;
+  seen.reserve(n_q);
+  for (int32_t i = 0; i < n_q; ++i) {
+    const float w = q_w[i];
+    if (!std::isfinite(w) || w < 0.f)
+      return set_error(WMD_ERR_INVALID_ARG, "query weight " + std::to_string(i) + " is negative or not finite");
+    if (q_ids[i] < 0 || q_ids[i] >= V)
+      return set_error(WMD_ERR_INVALID_ARG, "query id " + std::to_string(q_ids[i]) + " outside [0, V)");
+    if (w == 0.f) continue;  // I = (r > 0)
+    seen.push_back(q_ids[i]);
+    out_ids[k] = q_ids[i];
+    out_w[k] = w;
+    ++k;
+  }
+  std::sort(seen.begin(), seen.end());
+  if (std::adjacent_find(seen.begin(), seen.end()) != seen.end())
+    return set_error(WMD_ERR_INVALID_ARG, "duplicate query word id");
+  *out_vr = k;
+  if (k > WMD_MAX_VR) return set_error(WMD_ERR_UNSUPPORTED, "more than WMD_MAX_VR query words");
+  return WMD_OK;
+}
+
+wmd_status wmd_corpus_load(const float* vecs, int64_t V, int32_t d, const int64_t* row_ptr,
+                           const int32_t* doc_idx, const float* val, int64_t N, int64_t nnz,
+                           int32_t device, wmd_corpus** out) {
+  if (!out) return set_error(WMD_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  if (V <= 0 || V > INT32_MAX) return set_error(WMD_ERR_INVALID_ARG, "V must be in [1, 2^31)");
+  if (d <= 0) return set_error(WMD_ERR_INVALID_ARG, "d must be positive");
+  if (N < 0 || N > INT32_MAX) return set_error(WMD_ERR_INVALID_ARG, "N must be in [0, 2^31)");
+  if (nnz < 0) return set_error(WMD_ERR_INVALID_ARG, "nnz < 0");
+  if (!vecs || !row_ptr || (nnz > 0 && (!doc_idx || !val)))
+    return set_error(WMD_ERR_INVALID_ARG, "NULL input pointer");
+  if (row_ptr[0] != 0 || row_ptr[V] != nnz)
+    return set_error(WMD_ERR_INVALID_ARG, "row_ptr must start at 0 and end at nnz");
+  for (int64_t w = 0; w < V; ++w) {
+    if (row_ptr[w + 1] < row_ptr[w]) return set_error(WMD_ERR_INVALID_ARG, "row_ptr decreases");
+    for (int64_t e = row_ptr[w]; e < row_ptr[w + 1]; ++e) {
+      if (doc_idx[e] < 0 || doc_idx[e] >= N)
+        return set_error(WMD_ERR_INVALID_ARG, "doc_idx outside [0, N)");
+      if (e > row_ptr[w] && doc_idx[e] <= doc_idx[e - 1])
+        return set_error(WMD_ERR_INVALID_ARG, "doc_idx not strictly increasing within a row");
+      if (!(val[e] > 0.f) || !std::isfinite(val[e]))
+        return set_error(WMD_ERR_INVALID_ARG, "c values must be finite and > 0");
+    }
+  }
+  for (int64_t i = 0; i < V * (int64_t)d; ++i)
+    if (!std::isfinite(vecs[i])) return set_error(WMD_ERR_INVALID_ARG, "vecs holds a non-finite value");
+
+  wmd_corpus* c = new (std::nothrow) wmd_corpus();
+  if (!c) return set_error(WMD_ERR_OUT_OF_MEMORY, "host allocation failed");
+  c->device = device;
+  c->V = V;
+  c->N = N;
+  c->nnz = nnz;
+  c->d = d;
+  c->ldv = (int32_t)align_up((size_t)d, 4);  // 16-byte rows for vector loads
+
+  // active vocabulary first: device row of word w
+  std::vector<int32_t> perm(V);
+  int64_t U = 0;
+  for (int64_t w = 0; w < V; ++w)
+    if (row_ptr[w + 1] > row_ptr[w]) perm[w] = (int32_t)U++;
+  int64_t nxt = U;
+  for (int64_t w = 0; w < V; ++w)
+    if (row_ptr[w + 1] == row_ptr[w]) perm[w] = (int32_t)nxt++;
+  c->U = U;
+
+  // permuted, padded embeddings and their squared norms (float64 sums)
+  std::vector<float> hv((size_t)V * c->ldv, 0.f);
+  std::vector<float> hn(V);
+  for (int64_t w = 0; w < V; ++w) {
+    const float* src = vecs + (size_t)w * d;
+    float* dst = hv.data() + (size_t)perm[w] * c->ldv;
+    double s = 0.0;
+    for (int k = 0; k < d; ++k) {
+      dst[k] = src[k];
+      s += (double)src[k] * (double)src[k];
+    }
+    hn[perm[w]] = (float)s;
+  }
+
+  // document-major copy of c (CSR of c^T), words as device rows
+  std::vector<int64_t> dptr(N + 1, 0);
+  for (int64_t e = 0; e < nnz; ++e) dptr[doc_idx[e] + 1]++;
+  for (int64_t j = 0; j < N; ++j) dptr[j + 1] += dptr[j];
+  std::vector<int64_t> fill(dptr.begin(), dptr.end() - 1);
+  std::vector<int32_t> dwords(nnz);
+  std::vector<float> dvals(nnz);
+  for (int64_t w = 0; w < V; ++w)
+    for (int64_t e = row_ptr[w]; e < row_ptr[w + 1]; ++e) {
+      const int64_t pos = fill[doc_idx[e]]++;
+      dwords[pos] = perm[w];
+      dvals[pos] = val[e];
+    }
+
+  // documents by decreasing length (longest first), ties by id
+  std::vector<int32_t> order(N);
+  std::iota(order.begin(), order.end(), 0);
+  std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t b) {
+    return (dptr[a + 1] - dptr[a]) > (dptr[b + 1] - dptr[b]);
+  });
+
+  DeviceGuard g(device);
+  cudaError_t e = cudaSetDevice(device);
+  size_t bytes = 0;
+  if (e == cudaSuccess) e = upload(&c->vecs, hv.data(), hv.size(), &bytes);
+  if (e == cudaSuccess) e = upload(&c->norms, hn.data(), hn.size(), &bytes);
+  if (e == cudaSuccess) e = upload(&c->perm, perm.data(), perm.size(), &bytes);
+  if (e == cudaSuccess) e = upload(&c->doc_ptr, dptr.data(), dptr.size(), &bytes);
+  if (e == cudaSuccess) e = upload(&c->doc_words, dwords.data(), dwords.size(), &bytes);
+  if (e == cudaSuccess) e = upload(&c->doc_vals, dvals.data(), dvals.size(), &bytes);
+  if (e == cudaSuccess) e = upload(&c->order, order.data(), order.size(), &bytes);
+
+  // per query-width class: team size per document and CTA work items
+  for (int cls = 0; cls < kNumClasses && e == cudaSuccess; ++cls) {
+    const int64_t rpw = rows_per_warp(cls);
+    std::vector<LoopItem> items;
+    int64_t i = 0;
+    while (i < N) {
+      const int64_t n = dptr[order[i] + 1] - dptr[order[i]];
+      const int W = n <= rpw ? 1 : (n <= 2 * rpw ? 2 : 4);
+      const int per = 4 / W;
+      // the run of documents with the same team size (lengths are sorted)
+      int64_t j = i;
+      while (j < N) {
+        const int64_t m = dptr[order[j] + 1] - dptr[order[j]];
+        const int Wm = m <= rpw ? 1 : (m <= 2 * rpw ? 2 : 4);
+        if (Wm != W) break;
+        ++j;
+      }
+      for (int64_t b = i; b < j; b += per)
+        items.push_back(LoopItem{W, (int32_t)b, (int32_t)std::min<int64_t>(b + per, j), 0});
+      i = j;
+    }
+    c->sched[cls].n_items = (int32_t)items.size();
+    e = upload(&c->sched[cls].d_items, items.data(), items.size(), &bytes);
+  }
+  c->device_bytes = bytes;
+  if (e != cudaSuccess) {
+    wmd_status st = cuda_error(e, "corpus upload");
+    free_corpus_device(c);
+    delete c;
+    return st;
+  }
+  *out = c;
+  return WMD_OK;
+}
+
+void wmd_corpus_free(wmd_corpus* c) {
+  if (!c) return;
+  {
+    DeviceGuard g(c->device);
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    free_corpus_device(c);
+  }
+  delete c;
+}
+
+wmd_status wmd_corpus_get_info(const wmd_corpus* c, wmd_corpus_info* out) {
+  if (!c || !out) return set_error(WMD_ERR_INVALID_ARG, "NULL pointer");
+  out->V = c->V;
+  out->d = c->d;
+  out->N = c->N;
+  out->nnz = c->nnz;
+  out->U = c->U;
+  out->device = c->device;
+  out->device_bytes = c->device_bytes;
+  return WMD_OK;
+}
+
+size_t wmd_workspace_bytes(const wmd_corpus* c, int32_t v_r, wmd_precision prec) {
+  if (!c || v_r <= 0 || v_r > WMD_MAX_VR) return 0;
+  return ws_layout(c, kClassVR[vr_class(v_r)], prec).total;
+}
+
+wmd_status wmd_build_kernel_matrix(wmd_corpus* c, const int32_t* d_q_ids, const float* d_q_w,
+                                   int32_t v_r, float lambda, wmd_precision prec, void* d_ws,
+                                   size_t ws_bytes, void* stream) {
+  wmd_status st = check_query_args(c, v_r, lambda, 0);
+  if (st != WMD_OK) return st;
+  if (!d_q_ids || !d_q_w) return set_error(WMD_ERR_INVALID_ARG, "NULL query pointer");
+  if ((st = check_ws(c, v_r, prec, d_ws, ws_bytes)) != WMD_OK) return st;
+  DeviceGuard g(c->device);
+  const int VR = kClassVR[vr_class(v_r)];
+  const WsLayout L = ws_layout(c, VR, prec);
+  char* ws = static_cast<char*>(d_ws);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  float* r = reinterpret_cast<float*>(ws + L.r_off);
+  WMD_CUDA_TRY(launch_cdist(c, d_q_ids, d_q_w, v_r, VR, lambda, prec, ws + L.k_off, VR, 0, r, s));
+  return WMD_OK;
+}
+
+wmd_status wmd_sinkhorn_loop(wmd_corpus* c, int32_t v_r, float lambda, int32_t max_iter,
+                             wmd_precision prec, void* d_ws, size_t ws_bytes, double* d_out,
+                             void* stream) {
+  wmd_status st = check_query_args(c, v_r, lambda, max_iter);
+  if (st != WMD_OK) return st;
+  if (!d_out && c->N > 0) return set_error(WMD_ERR_INVALID_ARG, "d_out is NULL");
+  if ((st = check_ws(c, v_r, prec, d_ws, ws_bytes)) != WMD_OK) return st;
+  DeviceGuard g(c->device);
+  const int cls = vr_class(v_r);
+  const int VR = kClassVR[cls];
+  const WsLayout L = ws_layout(c, VR, prec);
+  char* ws = static_cast<char*>(d_ws);
+  const float* r = reinterpret_cast<const float*>(ws + L.r_off);
+  WMD_CUDA_TRY(launch_loop(c, cls, ws + L.k_off, VR, 0, r, v_r, lambda, max_iter, prec, d_out,
+                           static_cast<cudaStream_t>(stream)));
+  return WMD_OK;
+}
+
+wmd_status wmd_query_device(wmd_corpus* c, const int32_t* d_q_ids, const float* d_q_w,
+                            int32_t v_r, float lambda, int32_t max_iter, wmd_precision prec,
+                            void* d_ws, size_t ws_bytes, double* d_out, void* stream) {
+  wmd_status st = check_query_args(c, v_r, lambda, max_iter);
+  if (st != WMD_OK) return st;
+  st = wmd_build_kernel_matrix(c, d_q_ids, d_q_w, v_r, lambda, prec, d_ws, ws_bytes, stream);
+  if (st != WMD_OK) return st;
+  return wmd_sinkhorn_loop(c, v_r, lambda, max_iter, prec, d_ws, ws_bytes, d_out, stream);
+}
+
+wmd_status wmd_query(wmd_corpus* c, const int32_t* q_ids, const float* q_w, int32_t n_q,
+                     float lambda, int32_t max_iter, wmd_precision prec, double* out_wmd) {
+  if (!c) return set_error(WMD_ERR_INVALID_ARG, "corpus is NULL");
+  if (!out_wmd && c->N > 0) return set_error(WMD_ERR_INVALID_ARG, "out_wmd is NULL");
+  std::vector<int32_t> ids(std::max(n_q, 0));
+  std::vector<float> w(std::max(n_q, 0));
+  int32_t v_r = 0;
+  wmd_status st = wmd_compact_query(q_ids, q_w, n_q, c->V, ids.data(), w.data(), &v_r);
+  if (st != WMD_OK) return st;
+  if ((st = check_query_args(c, v_r, lambda, max_iter)) != WMD_OK) return st;
+  if (prec != WMD_PREC_FP32 && prec != WMD_PREC_BF16_K)
+    return set_error(WMD_ERR_INVALID_ARG, "unknown precision");
+
+  std::lock_guard<std::mutex> lock(c->mu);
+  DeviceGuard g(c->device);
+  if (!c->stream) WMD_CUDA_TRY(cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking));
+  const size_t need = wmd_workspace_bytes(c, v_r, prec);
+  if (c->ws_bytes < need) {
+    cudaFree(c->ws);
+    c->ws = nullptr;
+    c->ws_bytes = 0;
+    WMD_CUDA_TRY(cudaMalloc(&c->ws, need));
+    c->ws_bytes = need;
+  }
+  if (!c->d_qids) {
+    WMD_CUDA_TRY(cudaMalloc(&c->d_qids, WMD_MAX_VR * sizeof(int32_t)));
+    WMD_CUDA_TRY(cudaMalloc(&c->d_qw, WMD_MAX_VR * sizeof(float)));
+    WMD_CUDA_TRY(cudaMalloc(&c->d_out, std::max<int64_t>(c->N, 1) * sizeof(double)));
+  }
+  WMD_CUDA_TRY(cudaMemcpyAsync(c->d_qids, ids.data(), v_r * sizeof(int32_t), cudaMemcpyHostToDevice, c->stream));
+  WMD_CUDA_TRY(cudaMemcpyAsync(c->d_qw, w.data(), v_r * sizeof(float), cudaMemcpyHostToDevice, c->stream));
+  st = wmd_query_device(c, c->d_qids, c->d_qw, v_r, lambda, max_iter, prec, c->ws, c->ws_bytes,
+                        c->d_out, c->stream);
+  if (st != WMD_OK) {
+    cudaStreamSynchronize(c->stream);
+    return st;
+  }
+  if (c->N > 0)
+    WMD_CUDA_TRY(cudaMemcpyAsync(out_wmd, c->d_out, c->N * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  WMD_CUDA_TRY(cudaStreamSynchronize(c->stream));
+  return WMD_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,101 @@
+// Internal declarations shared by the translation units of the WMD library.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+
+#include <cstdint>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "../../include/wmd.h"
+
+namespace wmd {
+
+// ---------------------------------------------------------------- errors
+wmd_status set_error(wmd_status st, const std::string& msg);
+wmd_status cuda_error(cudaError_t e, const char* what);
+
+#define WMD_CUDA_TRY(expr)                                  \
+  do {                                                      \
+    cudaError_t e_ = (expr);                                \
+    if (e_ != cudaSuccess) return ::wmd::cuda_error(e_, #expr); \
+  } while (0)
+
+// ---------------------------------------------------------------- query width classes
+// The query is padded to one of these widths (VR); K rows have VR entries.
+constexpr int kNumClasses = 6;
+constexpr int kClassVR[kNumClasses] = {8, 16, 32, 64, 128, 256};
+
+inline int vr_class(int v_r) {
+  for (int c = 0; c < kNumClasses; ++c)
+    if (v_r <= kClassVR[c]) return c;
+  return -1;
+}
+
+// Rows one warp keeps in registers for a class (lanes-per-row-group x rows
+// per lane); must match the kernel configurations in sinkhorn.cu.
+int rows_per_warp(int cls);
+
+// One CTA work item of the fused loop: a team size W (warps per document),
+// and the range [begin, end) of the length-sorted document order that the
+// CTA's 4/W teams take, one document each.
+struct LoopItem {
+  int32_t W;
+  int32_t begin;
+  int32_t end;
+  int32_t pad;
+};
+
+struct Schedule {
+  LoopItem* d_items = nullptr;
+  int32_t n_items = 0;
+};
+
+}  // namespace wmd
+
+struct wmd_corpus {
+  int device = 0;
+  int64_t V = 0, N = 0, nnz = 0, U = 0;
+  int32_t d = 0, ldv = 0;  // embedding width and padded row stride (floats)
+
+  // device, resident
+  float* vecs = nullptr;       // V x ldv, rows permuted: active words first
+  float* norms = nullptr;      // V, squared row norms (fp64 sum, rounded)
+  int32_t* perm = nullptr;     // V: word id -> device row
+  int64_t* doc_ptr = nullptr;  // N+1, document-major CSR of c^T
+  int32_t* doc_words = nullptr;// nnz, device rows (< U) sorted within a doc
+  float* doc_vals = nullptr;   // nnz
+  int32_t* order = nullptr;    // N, documents by decreasing length
+  wmd::Schedule sched[wmd::kNumClasses];
+  size_t device_bytes = 0;
+
+  // host path (wmd_query) state, guarded by mu
+  std::mutex mu;
+  cudaStream_t stream = nullptr;
+  void* ws = nullptr;
+  size_t ws_bytes = 0;
+  int32_t* d_qids = nullptr;
+  float* d_qw = nullptr;
+  double* d_out = nullptr;
+};
+
+namespace wmd {
+
+// Workspace carve-up for one query of class VR: the padded query weights r
+// (VR floats) and the word-major K (U x VR).
+struct WsLayout {
+  size_t r_off, k_off, total;
+};
+WsLayout ws_layout(const wmd_corpus* c, int VR, wmd_precision prec);
+
+// Kernel launchers (cdist.cu / sinkhorn.cu).
+cudaError_t launch_cdist(const wmd_corpus* c, const int32_t* q_ids, const float* q_w, int v_r,
+                         int VR, float lambda, wmd_precision prec, void* K, int ldk, int kcol0,
+                         float* r_out, cudaStream_t s);
+cudaError_t launch_loop(const wmd_corpus* c, int cls, const void* K, int ldk, int kcol0,
+                        const float* r, int v_r, float lambda, int T, wmd_precision prec,
+                        double* out, cudaStream_t s);
+
+}  // namespace wmd

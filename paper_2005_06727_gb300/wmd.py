@@ -1,0 +1,230 @@
+"""Thin Python binding of the C ABI in ``include/wmd.h`` (ctypes).
+
+This module only marshals arguments: every step of the method runs in the
+CUDA library ``libwmd_gb300.so``.  There is no CPU fallback; if the library is
+missing the import of a function raises :class:`WMDError`.
+
+Names follow the C entry points: ``corpus_load`` / :class:`Corpus`,
+``Corpus.query`` (``wmd_query``), ``Corpus.query_device``
+(``wmd_query_device``), ``Corpus.build_kernel_matrix``,
+``Corpus.sinkhorn_loop`` and ``compact_query``.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import re
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libwmd_gb300.so")
+HEADER = os.path.join(os.path.dirname(HERE), "include", "wmd.h")
+
+WMD_OK = 0
+WMD_ERR_INVALID_ARG = 1
+WMD_ERR_OUT_OF_MEMORY = 2
+WMD_ERR_CUDA = 3
+WMD_ERR_NOT_READY = 4
+WMD_ERR_TIMEOUT = 5
+WMD_ERR_SHUTDOWN = 6
+WMD_ERR_UNSUPPORTED = 7
+
+PREC_FP32 = 0
+PREC_BF16_K = 1
+MAX_VR = 256
+
+_STATUS = {0: "OK", 1: "INVALID_ARG", 2: "OUT_OF_MEMORY", 3: "CUDA", 4: "NOT_READY",
+           5: "TIMEOUT", 6: "SHUTDOWN", 7: "UNSUPPORTED"}
+
+
+class WMDError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"wmd status {_STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class CorpusInfo(C.Structure):
+    _fields_ = [("V", C.c_int64), ("d", C.c_int32), ("N", C.c_int64), ("nnz", C.c_int64),
+                ("U", C.c_int64), ("device", C.c_int32), ("device_bytes", C.c_size_t)]
+
+
+_lib = None
+
+_P = C.c_void_p
+_SIGS = {
+    "wmd_last_error": (C.c_char_p, []),
+    "wmd_version": (C.c_char_p, []),
+    "wmd_compact_query": (C.c_int, [_P, _P, C.c_int32, C.c_int64, _P, _P, _P]),
+    "wmd_corpus_load": (C.c_int, [_P, C.c_int64, C.c_int32, _P, _P, _P, C.c_int64, C.c_int64,
+                                  C.c_int32, _P]),
+    "wmd_corpus_free": (None, [_P]),
+    "wmd_corpus_get_info": (C.c_int, [_P, _P]),
+    "wmd_query": (C.c_int, [_P, _P, _P, C.c_int32, C.c_float, C.c_int32, C.c_int, _P]),
+    "wmd_workspace_bytes": (C.c_size_t, [_P, C.c_int32, C.c_int]),
+    "wmd_build_kernel_matrix": (C.c_int, [_P, _P, _P, C.c_int32, C.c_float, C.c_int, _P,
+                                          C.c_size_t, _P]),
+    "wmd_sinkhorn_loop": (C.c_int, [_P, C.c_int32, C.c_float, C.c_int32, C.c_int, _P,
+                                    C.c_size_t, _P, _P]),
+    "wmd_query_device": (C.c_int, [_P, _P, _P, C.c_int32, C.c_float, C.c_int32, C.c_int, _P,
+                                   C.c_size_t, _P, _P]),
+}
+
+
+def lib():
+    """Load ``libwmd_gb300.so`` (built by ``paper_2005_06727_gb300.build``)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise WMDError(WMD_ERR_CUDA, f"CUDA library not built: {LIB_PATH} is missing "
+                                         "(run paper_2005_06727_gb300.build.build())")
+        L = C.CDLL(LIB_PATH)
+        for name, (res, args) in _SIGS.items():
+            f = getattr(L, name, None)
+            if f is None:
+                continue
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def declared_functions() -> list[str]:
+    """Names of the functions declared in include/wmd.h."""
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(wmd_[a-z_0-9]+)\s*\(", src)))
+
+
+def _check(st: int):
+    if st != WMD_OK:
+        raise WMDError(st, lib().wmd_last_error().decode(errors="replace"))
+
+
+def _ptr(a: np.ndarray):
+    return a.ctypes.data_as(C.c_void_p) if a.size else None
+
+
+def compact_query(q_ids, q_w, V: int):
+    """``wmd_compact_query``: drop zero weights (I = r > 0) and validate."""
+    ids = np.ascontiguousarray(q_ids, dtype=np.int32)
+    w = np.ascontiguousarray(q_w, dtype=np.float32)
+    if ids.shape != w.shape:
+        raise WMDError(WMD_ERR_INVALID_ARG, "ids and weights differ in length")
+    out_ids = np.zeros(max(ids.size, 1), np.int32)
+    out_w = np.zeros(max(ids.size, 1), np.float32)
+    vr = C.c_int32(0)
+    _check(lib().wmd_compact_query(_ptr(ids), _ptr(w), ids.size, V, _ptr(out_ids), _ptr(out_w),
+                                   C.byref(vr)))
+    return out_ids[:vr.value].copy(), out_w[:vr.value].copy()
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        import torch
+        return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, int):
+        return C.c_void_p(stream)
+    return C.c_void_p(stream.cuda_stream)
+
+
+def _dptr(t):
+    """Device pointer of a torch tensor (or a raw int)."""
+    if t is None:
+        return None
+    if isinstance(t, int):
+        return C.c_void_p(t)
+    return C.c_void_p(t.data_ptr())
+
+
+class Corpus:
+    """``wmd_corpus``: embeddings and the V x N CSR ``c`` resident on a GPU."""
+
+    def __init__(self, vecs, row_ptr, doc_idx, val, N: int, device: int = 0):
+        vecs = np.ascontiguousarray(vecs, dtype=np.float32)
+        row_ptr = np.ascontiguousarray(row_ptr, dtype=np.int64)
+        doc_idx = np.ascontiguousarray(doc_idx, dtype=np.int32)
+        val = np.ascontiguousarray(val, dtype=np.float32)
+        V, d = vecs.shape
+        h = C.c_void_p()
+        _check(lib().wmd_corpus_load(_ptr(vecs), V, d, _ptr(row_ptr), _ptr(doc_idx), _ptr(val),
+                                     int(N), int(val.size), int(device), C.byref(h)))
+        self._h = h
+        info = CorpusInfo()
+        _check(lib().wmd_corpus_get_info(self._h, C.byref(info)))
+        self.V, self.d, self.N, self.nnz, self.U = info.V, info.d, info.N, info.nnz, info.U
+        self.device = info.device
+        self.device_bytes = info.device_bytes
+
+    @classmethod
+    def from_synth(cls, vecs, corpus, device: int = 0):
+        return cls(vecs, corpus.row_ptr, corpus.doc_idx, corpus.val, corpus.N, device)
+
+    @property
+    def handle(self):
+        return self._h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().wmd_corpus_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -------------------------------------------------------------- host path
+    def query(self, q_ids, q_w, lam: float, max_iter: int, prec: int = PREC_FP32,
+              out: np.ndarray | None = None) -> np.ndarray:
+        """``wmd_query``: host buffers in, WMD[N] (float64) out."""
+        ids = np.ascontiguousarray(q_ids, dtype=np.int32)
+        w = np.ascontiguousarray(q_w, dtype=np.float32)
+        if out is None:
+            out = np.empty(self.N, np.float64)
+        _check(lib().wmd_query(self._h, _ptr(ids), _ptr(w), ids.size, float(lam), int(max_iter),
+                               int(prec), _ptr(out)))
+        return out
+
+    # -------------------------------------------------------------- device path
+    def workspace_bytes(self, v_r: int, prec: int = PREC_FP32) -> int:
+        return int(lib().wmd_workspace_bytes(self._h, int(v_r), int(prec)))
+
+    def build_kernel_matrix(self, d_ids, d_w, v_r, lam, prec, ws, ws_bytes, stream=None):
+        _check(lib().wmd_build_kernel_matrix(self._h, _dptr(d_ids), _dptr(d_w), int(v_r),
+                                             float(lam), int(prec), _dptr(ws), int(ws_bytes),
+                                             _stream_ptr(stream)))
+
+    def sinkhorn_loop(self, v_r, lam, max_iter, prec, ws, ws_bytes, d_out, stream=None):
+        _check(lib().wmd_sinkhorn_loop(self._h, int(v_r), float(lam), int(max_iter), int(prec),
+                                       _dptr(ws), int(ws_bytes), _dptr(d_out),
+                                       _stream_ptr(stream)))
+
+    def query_device(self, d_ids, d_w, v_r, lam, max_iter, prec, ws, ws_bytes, d_out,
+                     stream=None):
+        _check(lib().wmd_query_device(self._h, _dptr(d_ids), _dptr(d_w), int(v_r), float(lam),
+                                      int(max_iter), int(prec), _dptr(ws), int(ws_bytes),
+                                      _dptr(d_out), _stream_ptr(stream)))
+
+
+class DeviceQuery:
+    """Device buffers (torch) for the stream-ordered path of one query."""
+
+    def __init__(self, corpus: Corpus, q_ids, q_w, prec: int = PREC_FP32):
+        import torch
+        ids, w = compact_query(q_ids, q_w, corpus.V)
+        dev = torch.device("cuda", corpus.device)
+        self.v_r = int(ids.size)
+        self.prec = prec
+        self.ids = torch.from_numpy(ids).to(dev)
+        self.w = torch.from_numpy(w).to(dev)
+        self.ws_bytes = corpus.workspace_bytes(self.v_r, prec)
+        self.ws = torch.empty(self.ws_bytes, dtype=torch.uint8, device=dev)
+        self.out = torch.empty(max(corpus.N, 1), dtype=torch.float64, device=dev)
+        self.corpus = corpus
+
+    def run(self, lam: float, max_iter: int, stream=None):
+        self.corpus.query_device(self.ids, self.w, self.v_r, lam, max_iter, self.prec, self.ws,
+                                 self.ws_bytes, self.out, stream)
+        return self.out

@@ -1,0 +1,98 @@
+"""The C-ABI library builds, loads and exports every declared symbol; host-side
+logic (query compaction, input validation) behaves as documented.  No GPU."""
+import ctypes
+import os
+
+import numpy as np
+import pytest
+
+from paper_2005_06727_gb300 import build as build_mod
+from paper_2005_06727_gb300 import wmd
+
+
+@pytest.fixture(scope="module")
+def lib():
+    build_mod.build()
+    return wmd.lib()
+
+
+def test_every_declared_function_is_exported(lib):
+    names = wmd.declared_functions()
+    assert len(names) >= 10
+    raw = ctypes.CDLL(wmd.LIB_PATH)
+    missing = [n for n in names if not hasattr(raw, n)]
+    assert not missing, missing
+
+
+def test_library_is_built_for_sm_103a(lib):
+    assert b"sm_103a" in lib.wmd_version()
+    assert "arch=compute_103a,code=sm_103a" in " ".join(build_mod.ARCH)
+
+
+def test_compact_query_drops_zero_weights_and_keeps_order(lib):
+    ids, w = wmd.compact_query([7, 2, 9, 4], [0.25, 0.0, 0.5, 0.25], 10)
+    assert ids.tolist() == [7, 9, 4]
+    assert w.tolist() == [0.25, 0.5, 0.25]
+    ids, w = wmd.compact_query([], [], 10)
+    assert ids.size == 0
+
+
+@pytest.mark.parametrize("ids,w,msg", [
+    ([1, 1], [0.5, 0.5], "duplicate"),
+    ([1, 10], [0.5, 0.5], "outside"),
+    ([-1], [1.0], "outside"),
+    ([1], [-0.5], "negative"),
+    ([1], [float("nan")], "not finite"),
+    ([1], [float("inf")], "not finite"),
+])
+def test_compact_query_rejects_bad_input(lib, ids, w, msg):
+    with pytest.raises(wmd.WMDError) as e:
+        wmd.compact_query(ids, w, 10)
+    assert e.value.status == wmd.WMD_ERR_INVALID_ARG
+    assert msg in str(e.value)
+
+
+def test_compact_query_zero_weight_duplicates_are_ignored(lib):
+    ids, _ = wmd.compact_query([3, 3], [0.0, 1.0], 10)
+    assert ids.tolist() == [3]
+
+
+def test_compact_query_too_many_words(lib):
+    n = wmd.MAX_VR + 1
+    with pytest.raises(wmd.WMDError) as e:
+        wmd.compact_query(np.arange(n), np.full(n, 1.0 / n), 1000)
+    assert e.value.status == wmd.WMD_ERR_UNSUPPORTED
+
+
+def _corpus_args():
+    vecs = np.ones((4, 3), np.float32)
+    row_ptr = np.array([0, 1, 1, 3, 3], np.int64)
+    doc_idx = np.array([0, 0, 1], np.int32)
+    val = np.array([0.5, 0.5, 1.0], np.float32)
+    return vecs, row_ptr, doc_idx, val, 2
+
+
+@pytest.mark.parametrize("mutate,msg", [
+    (lambda a: a[1].__setitem__(4, 2), "end at nnz"),
+    (lambda a: a[1].__setitem__(2, 0), "decreases"),
+    (lambda a: a[2].__setitem__(0, 5), "outside [0, N)"),
+    (lambda a: a[2].__setitem__(2, 0), "strictly increasing"),
+    (lambda a: a[3].__setitem__(1, 0.0), "> 0"),
+    (lambda a: a[3].__setitem__(1, np.nan), "> 0"),
+    (lambda a: a[0].__setitem__((0, 0), np.inf), "non-finite"),
+])
+def test_corpus_load_validates_on_host(lib, mutate, msg):
+    """Malformed inputs are rejected before anything touches a GPU."""
+    args = list(_corpus_args())
+    mutate(args)
+    with pytest.raises(wmd.WMDError) as e:
+        wmd.Corpus(*args)
+    assert e.value.status == wmd.WMD_ERR_INVALID_ARG
+    assert msg in str(e.value)
+
+
+def test_missing_library_fails_loudly(monkeypatch, tmp_path):
+    monkeypatch.setattr(wmd, "_lib", None)
+    monkeypatch.setattr(wmd, "LIB_PATH", str(tmp_path / "absent.so"))
+    with pytest.raises(wmd.WMDError):
+        wmd.lib()

@@ -1,0 +1,249 @@
+"""Parity of the CUDA path against the FP64 oracle (GPU only).
+
+Tolerance: the float32 path must match the oracle within 1e-5 relative per
+document (absolute floor 1e-7); the bfloat16-stored K path within 5e-3.  NaN
+results (empty documents) must coincide.  Every call goes through the C ABI.
+"""
+import numpy as np
+import pytest
+
+from oracle import sinkhorn_wmd as orc
+from paper_2005_06727_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+FP32_RTOL = 1e-5
+BF16_RTOL = 5e-3
+
+
+@pytest.fixture(scope="module")
+def wmd():
+    from paper_2005_06727_gb300 import build as build_mod
+    build_mod.build()
+    from paper_2005_06727_gb300 import wmd as w
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    return w
+
+
+def assert_parity(got, want, rtol, what=""):
+    got = np.asarray(got, np.float64)
+    want = np.asarray(want, np.float64)
+    assert got.shape == want.shape
+    nan_w = np.isnan(want)
+    assert np.array_equal(np.isnan(got), nan_w), f"{what}: NaN pattern differs"
+    g, w = got[~nan_w], want[~nan_w]
+    rel = np.abs(g - w) / np.maximum(np.abs(w), 1e-7)
+    worst = int(np.argmax(rel)) if rel.size else 0
+    assert rel.size == 0 or rel.max() <= rtol, (
+        f"{what}: max rel err {rel.max():.3e} at {worst}: got {g[worst]!r} want {w[worst]!r}")
+    return float(rel.max()) if rel.size else 0.0
+
+
+def oracle(vecs, c, q_ids, q_w, lam, T, docs=None):
+    return orc.sinkhorn_wmd_sparse(q_ids, q_w, c.row_ptr, c.doc_idx, c.val, c.N, vecs, lam, T,
+                                   docs=docs)
+
+
+def _docs(c):
+    return [(c.doc_words[c.doc_ptr[j]:c.doc_ptr[j + 1]], c.doc_vals[c.doc_ptr[j]:c.doc_ptr[j + 1]])
+            for j in range(c.N)]
+
+
+# ---------------------------------------------------------------- workloads
+def test_tiny_workload(wmd):
+    w = synth.TINY
+    vecs, c, qs = synth.make_workload(w)
+    corpus = wmd.Corpus.from_synth(vecs, c)
+    q_ids, q_w = qs[0]
+    want = oracle(vecs, c, q_ids, q_w, w.lam, w.max_iter)
+    got = corpus.query(q_ids, q_w, w.lam, w.max_iter)
+    assert_parity(got, want, FP32_RTOL, "tiny fp32")
+    got16 = corpus.query(q_ids, q_w, w.lam, w.max_iter, wmd.PREC_BF16_K)
+    assert_parity(got16, want, BF16_RTOL, "tiny bf16")
+
+
+def test_paper_shaped_workload_all_documents(wmd):
+    """V=100000, N=5000, 20-150 words per document, v_r=30, lambda=10, T=15:
+    the workload the benchmark times, compared on every document."""
+    w = synth.PAPER
+    vecs, c, qs = synth.make_workload(w)
+    corpus = wmd.Corpus.from_synth(vecs, c)
+    q_ids, q_w = qs[0]
+    want = oracle(vecs, c, q_ids, q_w, w.lam, w.max_iter)
+    got = corpus.query(q_ids, q_w, w.lam, w.max_iter)
+    assert_parity(got, want, FP32_RTOL, "paper-shaped fp32")
+    # the device-resident path (the one the benchmark times) gives the same bits
+    dq = wmd.DeviceQuery(corpus, q_ids, q_w)
+    dev = dq.run(w.lam, w.max_iter).cpu().numpy()
+    import torch
+    torch.cuda.synchronize()
+    assert np.array_equal(dev[: c.N], got)
+
+
+def test_large_workload_sampled_documents(wmd):
+    """V=100000, N=100000, 20-200 words, v_r=64: sampled documents, FP32 and
+    the bfloat16-stored K variant."""
+    w = synth.LARGE
+    vecs, c, qs = synth.make_workload(w)
+    corpus = wmd.Corpus.from_synth(vecs, c)
+    q_ids, q_w = qs[0]
+    rng = np.random.default_rng(0)
+    lens = np.diff(c.doc_ptr)
+    docs = np.unique(np.concatenate([rng.choice(c.N, 400, replace=False),
+                                     np.argsort(lens)[-20:], np.argsort(lens)[:20]]))
+    want = oracle(vecs, c, q_ids, q_w, w.lam, w.max_iter, docs=docs)
+    got = corpus.query(q_ids, q_w, w.lam, w.max_iter)
+    assert_parity(got[docs], want, FP32_RTOL, "large fp32")
+    got16 = corpus.query(q_ids, q_w, w.lam, w.max_iter, wmd.PREC_BF16_K)
+    assert_parity(got16[docs], want, BF16_RTOL, "large bf16")
+    assert np.all(np.isfinite(got))
+
+
+# ---------------------------------------------------------------- query widths and document shapes
+@pytest.mark.parametrize("v_r", [1, 2, 7, 8, 9, 16, 17, 31, 32, 33, 64, 65, 100, 128, 129, 200, 256])
+def test_query_widths(wmd, v_r):
+    """Every padded width class, ragged widths on both sides of each boundary."""
+    V, N = 3000, 61
+    vecs = synth.make_vecs(V, 300, 40 + v_r)
+    c = synth.make_corpus(V, N, 1, 60, 50 + v_r)
+    q_ids, q_w = synth.make_query(V, v_r, 60 + v_r)
+    corpus = wmd.Corpus.from_synth(vecs, c)
+    for T in (0, 1, 15):
+        want = oracle(vecs, c, q_ids, q_w, 10.0, T)
+        got = corpus.query(q_ids, q_w, 10.0, T)
+        assert_parity(got, want, FP32_RTOL, f"v_r={v_r} T={T}")
+
+
+@pytest.mark.parametrize("v_r,lengths", [
+    (30, [1, 2, 95, 96, 97, 150, 192, 193, 385, 700]),    # 1, 2, 4 warps; chunked beyond 384
+    (64, [47, 48, 49, 96, 97, 200, 400]),
+    (8, [383, 384, 385, 1000]),
+    (200, [5, 12, 13, 48, 49, 300]),
+])
+def test_document_lengths_across_team_sizes(wmd, v_r, lengths):
+    V = 4000
+    vecs = synth.make_vecs(V, 300, 3)
+    rng = np.random.default_rng(v_r)
+    docs = []
+    for n in lengths:
+        ids = np.sort(rng.choice(V, n, replace=False)).astype(np.int32)
+        wts = rng.random(n) + 0.05
+        docs.append((ids, (wts / wts.sum()).astype(np.float32)))
+    c = synth.corpus_from_docs(V, docs)
+    q_ids, q_w = synth.make_query(V, v_r, 9)
+    corpus = wmd.Corpus.from_synth(vecs, c)
+    for T in (1, 15):
+        want = oracle(vecs, c, q_ids, q_w, 10.0, T)
+        got = corpus.query(q_ids, q_w, 10.0, T)
+        assert_parity(got, want, FP32_RTOL, f"lengths v_r={v_r} T={T}")
+        got16 = corpus.query(q_ids, q_w, 10.0, T, wmd.PREC_BF16_K)
+        assert_parity(got16, want, BF16_RTOL, f"lengths bf16 v_r={v_r} T={T}")
+
+
+def test_closed_form_cases_on_gpu(wmd):
+    """v_r = 1 and single-word documents have closed forms (see the oracle pins)."""
+    V = 500
+    vecs = synth.make_vecs(V, 300, 77)
+    docs = [(np.array([w], np.int32), np.array([1.0], np.float32)) for w in (0, 3, 499)]
+    docs.append((np.array([1, 2, 3], np.int32), np.array([0.25, 0.25, 0.5], np.float32)))
+    c = synth.corpus_from_docs(V, docs)
+    corpus = wmd.Corpus.from_synth(vecs, c)
+    import scipy.spatial.distance as ssd
+    # one query word
+    got = corpus.query([3], [1.0], 10.0, 15)
+    M = ssd.cdist(vecs[[3]].astype(np.float64), vecs.astype(np.float64))[0]
+    want = np.array([M[0], 0.0, M[499], 0.25 * M[1] + 0.25 * M[2]])
+    np.testing.assert_allclose(got, want, rtol=FP32_RTOL, atol=1e-7)
+    # single-word documents receive all the query mass
+    q_ids = np.array([3, 10, 20], np.int32)
+    q_w = np.array([0.5, 0.25, 0.25], np.float32)
+    got = corpus.query(q_ids, q_w, 10.0, 15)
+    Mq = ssd.cdist(vecs[q_ids].astype(np.float64), vecs.astype(np.float64))
+    for j, w_ in enumerate((0, 3, 499)):
+        assert abs(got[j] - np.sum(q_w * Mq[:, w_])) <= FP32_RTOL * abs(got[j]) + 1e-7
+
+
+def test_empty_documents_and_degenerate_corpora(wmd):
+    V = 800
+    vecs = synth.make_vecs(V, 300, 5)
+    c0 = synth.make_corpus(V, 9, 3, 30, 6)
+    docs = _docs(c0)
+    docs.insert(0, (np.zeros(0, np.int32), np.zeros(0, np.float32)))
+    docs.insert(5, (np.zeros(0, np.int32), np.zeros(0, np.float32)))
+    c = synth.corpus_from_docs(V, docs)
+    q_ids, q_w = synth.make_query(V, 12, 7)
+    corpus = wmd.Corpus.from_synth(vecs, c)
+    for T in (0, 1, 15):
+        want = oracle(vecs, c, q_ids, q_w, 10.0, T)
+        got = corpus.query(q_ids, q_w, 10.0, T)
+        assert_parity(got, want, FP32_RTOL, f"empty docs T={T}")
+    # a corpus without any nonzero and one without documents
+    cz = synth.corpus_from_docs(V, [(np.zeros(0, np.int32), np.zeros(0, np.float32))] * 3)
+    got = wmd.Corpus.from_synth(vecs, cz).query(q_ids, q_w, 10.0, 5)
+    assert np.all(np.isnan(got))
+    cn = synth.corpus_from_docs(V, [])
+    assert wmd.Corpus.from_synth(vecs, cn).query(q_ids, q_w, 10.0, 5).shape == (0,)
+
+
+def test_zero_weight_query_words_are_dropped(wmd):
+    V = 1000
+    vecs = synth.make_vecs(V, 300, 8)
+    c = synth.make_corpus(V, 20, 5, 40, 9)
+    q_ids, q_w = synth.make_query(V, 10, 10)
+    corpus = wmd.Corpus.from_synth(vecs, c)
+    base = corpus.query(q_ids, q_w, 10.0, 15)
+    ids2 = np.concatenate([[V - 1], q_ids, [V - 2]]).astype(np.int32)
+    w2 = np.concatenate([[0.0], q_w, [0.0]]).astype(np.float32)
+    np.testing.assert_array_equal(corpus.query(ids2, w2, 10.0, 15), base)
+
+
+def test_odd_embedding_width_and_other_lambdas(wmd):
+    V = 1500
+    # (8, 10): few dimensions put some distinct words close together, where the
+    # GEMM form |a|^2 + |b|^2 - 2ab loses digits to cancellation (Sec. 5)
+    for d, lam, tol in [(37, 3.0, FP32_RTOL), (8, 10.0, 1e-4), (512, 20.0, FP32_RTOL)]:
+        vecs = synth.make_vecs(V, d, d)
+        c = synth.make_corpus(V, 33, 4, 50, d + 1)
+        q_ids, q_w = synth.make_query(V, 21, d + 2)
+        corpus = wmd.Corpus.from_synth(vecs, c)
+        want = oracle(vecs, c, q_ids, q_w, lam, 15)
+        got = corpus.query(q_ids, q_w, lam, 15)
+        assert_parity(got, want, tol, f"d={d} lambda={lam}")
+
+
+def test_invalid_arguments_return_errors(wmd):
+    V = 100
+    vecs = synth.make_vecs(V, 8, 1)
+    c = synth.make_corpus(V, 4, 2, 5, 2)
+    corpus = wmd.Corpus.from_synth(vecs, c)
+    for args, st in [(([1], [1.0], 0.0, 5), wmd.WMD_ERR_INVALID_ARG),
+                     (([1], [1.0], float("nan"), 5), wmd.WMD_ERR_INVALID_ARG),
+                     (([1], [1.0], 1.0, -1), wmd.WMD_ERR_INVALID_ARG),
+                     (([1], [0.0], 1.0, 5), wmd.WMD_ERR_INVALID_ARG),
+                     (([100], [1.0], 1.0, 5), wmd.WMD_ERR_INVALID_ARG)]:
+        with pytest.raises(wmd.WMDError) as e:
+            corpus.query(*args)
+        assert e.value.status == st
+    import torch
+    ws = torch.empty(16, dtype=torch.uint8, device="cuda")
+    with pytest.raises(wmd.WMDError):
+        corpus.query_device(torch.zeros(1, dtype=torch.int32, device="cuda"),
+                            torch.ones(1, device="cuda"), 1, 1.0, 1, wmd.PREC_FP32, ws, 16,
+                            torch.empty(4, dtype=torch.float64, device="cuda"))
+
+
+def test_out_of_range_device_id_gives_nan_not_a_fault(wmd):
+    import torch
+    V = 200
+    vecs = synth.make_vecs(V, 16, 1)
+    c = synth.make_corpus(V, 5, 2, 9, 2)
+    corpus = wmd.Corpus.from_synth(vecs, c)
+    ids = torch.tensor([3, V + 5], dtype=torch.int32, device="cuda")
+    w = torch.tensor([0.5, 0.5], device="cuda")
+    nb = corpus.workspace_bytes(2)
+    ws = torch.empty(nb, dtype=torch.uint8, device="cuda")
+    out = torch.empty(c.N, dtype=torch.float64, device="cuda")
+    corpus.query_device(ids, w, 2, 10.0, 5, wmd.PREC_FP32, ws, nb, out)
+    torch.cuda.synchronize()
+    assert torch.isnan(out).all()
