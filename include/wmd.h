@@ -146,15 +146,17 @@ wmd_status wmd_query(wmd_corpus* corpus, const int32_t* q_ids, const float* q_w,
  * never read outside the corpus for an out-of-range id: its column of K
  * becomes NaN and so does every result, but uniqueness is not re-checked.
  * d_ws: device workspace of at least wmd_workspace_bytes(...) bytes, 256-byte
- * aligned; it holds the query rows, 1/r and K between the two stages.
+ * aligned; it holds r, K and K .* M between the two stages.
  * d_out: device array of N doubles.
  *
  * wmd_build_kernel_matrix (Sec. 2 distance, Sec. 5 GEMM-type cdist,
- * Algorithm 1 line K = exp(-lambda M)): K[w, i] for every active word w,
- * word-major (the "on the fly transpose" of Sec. 3).
+ * Algorithm 1 line K = exp(-lambda M)): K[w, i] and (K .* M)[w, i] for every
+ * active word w (a word that occurs in some document), word-major (the "on
+ * the fly transpose" of Sec. 3), plus the padded weights r, into d_ws.
  * wmd_sinkhorn_loop (Algorithm 1 loop and final reduction; the fused
  * SDDMM_SpMM kernel of Sec. 3): max_iter iterations plus the final reduction
- * for all N documents, reading K from the workspace.
+ * for all N documents, reading K, K .* M and r from the workspace that
+ * wmd_build_kernel_matrix filled (same v_r and precision).
  * wmd_query_device: both stages.
  * ------------------------------------------------------------------------- */
 size_t wmd_workspace_bytes(const wmd_corpus* corpus, int32_t v_r, wmd_precision prec);
@@ -164,9 +166,9 @@ wmd_status wmd_build_kernel_matrix(wmd_corpus* corpus, const int32_t* d_q_ids,
                                    wmd_precision prec, void* d_ws, size_t ws_bytes,
                                    void* stream);
 
-wmd_status wmd_sinkhorn_loop(wmd_corpus* corpus, int32_t v_r, float lambda,
-                             int32_t max_iter, wmd_precision prec, void* d_ws,
-                             size_t ws_bytes, double* d_out, void* stream);
+wmd_status wmd_sinkhorn_loop(wmd_corpus* corpus, int32_t v_r, int32_t max_iter,
+                             wmd_precision prec, void* d_ws, size_t ws_bytes,
+                             double* d_out, void* stream);
 
 wmd_status wmd_query_device(wmd_corpus* corpus, const int32_t* d_q_ids,
                             const float* d_q_w, int32_t v_r, float lambda,

@@ -3,6 +3,8 @@
 // sinkhorn.cu; nothing here computes a distance or a scaling vector.
 #include <algorithm>
 #include <cmath>
+#include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <numeric>
 #include <vector>
@@ -48,6 +50,7 @@ void free_corpus_device(wmd_corpus* c) {
   cudaFree(c->doc_words);
   cudaFree(c->doc_vals);
   cudaFree(c->order);
+  cudaFree(c->d_err);
   for (auto& s : c->sched) cudaFree(s.d_items);
   cudaFree(c->ws);
   cudaFree(c->d_qids);
@@ -94,9 +97,12 @@ WsLayout ws_layout(const wmd_corpus* c, int VR, wmd_precision prec) {
   WsLayout L;
   size_t o = 0;
   L.r_off = o;    o = align_up(o + (size_t)VR * sizeof(float), 256);
-  L.k_off = o;
   const size_t kelem = prec == WMD_PREC_BF16_K ? 2 : 4;
-  o = align_up(o + (size_t)std::max<int64_t>(c->U, 1) * VR * kelem, 256);
+  const size_t kbytes = align_up((size_t)std::max<int64_t>(c->U, 1) * VR * kelem, 256);
+  L.k_off = o;
+  o += kbytes;
+  L.km_off = o;
+  o += kbytes;
   L.total = o;
   return L;
 }
@@ -230,6 +236,18 @@ wmd_status wmd_corpus_load(const float* vecs, int64_t V, int32_t d, const int64_
   if (e == cudaSuccess) e = upload(&c->doc_words, dwords.data(), dwords.size(), &bytes);
   if (e == cudaSuccess) e = upload(&c->doc_vals, dvals.data(), dvals.size(), &bytes);
   if (e == cudaSuccess) e = upload(&c->order, order.data(), order.size(), &bytes);
+  if (e == cudaSuccess) {
+    const int zero = 0;
+    e = upload(&c->d_err, &zero, 1, &bytes);
+  }
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device);
+  if (e == cudaSuccess) {
+    // WMD_CDIST_KERNEL=simt keeps cdist on the CUDA cores (used by the tests
+    // that compare both kernels); otherwise the tensor-core kernel is used
+    const char* kern = std::getenv("WMD_CDIST_KERNEL");
+    const bool simt = kern && std::strcmp(kern, "simt") == 0;
+    c->tmap_ok = !simt && make_vecs_tensor_map(c);
+  }
 
   // per query-width class: team size per document and CTA work items
   for (int cls = 0; cls < kNumClasses && e == cudaSuccess; ++cls) {
@@ -306,14 +324,14 @@ wmd_status wmd_build_kernel_matrix(wmd_corpus* c, const int32_t* d_q_ids, const 
   char* ws = static_cast<char*>(d_ws);
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   float* r = reinterpret_cast<float*>(ws + L.r_off);
-  WMD_CUDA_TRY(launch_cdist(c, d_q_ids, d_q_w, v_r, VR, lambda, prec, ws + L.k_off, VR, 0, r, s));
+  WMD_CUDA_TRY(launch_cdist(c, d_q_ids, d_q_w, v_r, VR, lambda, prec, ws + L.k_off,
+                            ws + L.km_off, VR, 0, r, s));
   return WMD_OK;
 }
 
-wmd_status wmd_sinkhorn_loop(wmd_corpus* c, int32_t v_r, float lambda, int32_t max_iter,
-                             wmd_precision prec, void* d_ws, size_t ws_bytes, double* d_out,
-                             void* stream) {
-  wmd_status st = check_query_args(c, v_r, lambda, max_iter);
+wmd_status wmd_sinkhorn_loop(wmd_corpus* c, int32_t v_r, int32_t max_iter, wmd_precision prec,
+                             void* d_ws, size_t ws_bytes, double* d_out, void* stream) {
+  wmd_status st = check_query_args(c, v_r, 1.f, max_iter);
   if (st != WMD_OK) return st;
   if (!d_out && c->N > 0) return set_error(WMD_ERR_INVALID_ARG, "d_out is NULL");
   if ((st = check_ws(c, v_r, prec, d_ws, ws_bytes)) != WMD_OK) return st;
@@ -323,7 +341,8 @@ wmd_status wmd_sinkhorn_loop(wmd_corpus* c, int32_t v_r, float lambda, int32_t m
   const WsLayout L = ws_layout(c, VR, prec);
   char* ws = static_cast<char*>(d_ws);
   const float* r = reinterpret_cast<const float*>(ws + L.r_off);
-  WMD_CUDA_TRY(launch_loop(c, cls, ws + L.k_off, VR, 0, r, v_r, lambda, max_iter, prec, d_out,
+  WMD_CUDA_TRY(launch_loop(c, cls, ws + L.k_off, ws + L.km_off, VR, 0, r, v_r, max_iter, prec,
+                           d_out,
                            static_cast<cudaStream_t>(stream)));
   return WMD_OK;
 }
@@ -335,7 +354,7 @@ wmd_status wmd_query_device(wmd_corpus* c, const int32_t* d_q_ids, const float* 
   if (st != WMD_OK) return st;
   st = wmd_build_kernel_matrix(c, d_q_ids, d_q_w, v_r, lambda, prec, d_ws, ws_bytes, stream);
   if (st != WMD_OK) return st;
-  return wmd_sinkhorn_loop(c, v_r, lambda, max_iter, prec, d_ws, ws_bytes, d_out, stream);
+  return wmd_sinkhorn_loop(c, v_r, max_iter, prec, d_ws, ws_bytes, d_out, stream);
 }
 
 wmd_status wmd_query(wmd_corpus* c, const int32_t* q_ids, const float* q_w, int32_t n_q,
@@ -365,7 +384,7 @@ wmd_status wmd_query(wmd_corpus* c, const int32_t* q_ids, const float* q_w, int3
   if (!c->d_qids) {
     WMD_CUDA_TRY(cudaMalloc(&c->d_qids, WMD_MAX_VR * sizeof(int32_t)));
     WMD_CUDA_TRY(cudaMalloc(&c->d_qw, WMD_MAX_VR * sizeof(float)));
-    WMD_CUDA_TRY(cudaMalloc(&c->d_out, std::max<int64_t>(c->N, 1) * sizeof(double)));
+    WMD_CUDA_TRY(cudaMalloc(&c->d_out, (std::max<int64_t>(c->N, 1) + 1) * sizeof(double)));
   }
   WMD_CUDA_TRY(cudaMemcpyAsync(c->d_qids, ids.data(), v_r * sizeof(int32_t), cudaMemcpyHostToDevice, c->stream));
   WMD_CUDA_TRY(cudaMemcpyAsync(c->d_qw, w.data(), v_r * sizeof(float), cudaMemcpyHostToDevice, c->stream));
@@ -377,7 +396,20 @@ wmd_status wmd_query(wmd_corpus* c, const int32_t* q_ids, const float* q_w, int3
   }
   if (c->N > 0)
     WMD_CUDA_TRY(cudaMemcpyAsync(out_wmd, c->d_out, c->N * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  int err = 0;
+  WMD_CUDA_TRY(cudaMemcpyAsync(&err, c->d_err, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
   WMD_CUDA_TRY(cudaStreamSynchronize(c->stream));
+  if (err) {
+    static const char* roles[] = {"?", "producer (stage free)", "converter (tile landed)",
+                                  "MMA (accumulator free)", "MMA (tile converted)",
+                                  "epilogue (accumulator full)"};
+    const int role = (err >> 24) & 0x3f;
+    char msg[160];
+    std::snprintf(msg, sizeof msg,
+                  "a device-side wait in the cdist kernel timed out: %s, iteration %d (code 0x%08x)",
+                  roles[role < 6 ? role : 0], err & 0xffffff, (unsigned)err);
+    return set_error(WMD_ERR_TIMEOUT, msg);
+  }
   return WMD_OK;
 }
 

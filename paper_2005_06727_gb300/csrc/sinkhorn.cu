@@ -20,11 +20,8 @@
 // Column j of lane pi is c(j) = (j / 4) * 4 PI + 4 pi + j % 4, so one float4
 // load per 4 columns reads 16 PI contiguous bytes per row group.
 //
-// K .* M for the final step is recovered from K itself: M = -ln(K) / lambda,
-// exact for K = 1 (the query's own word) and within a few float32 ulps while
-// K is a normal float.
-#include <cfloat>
-
+// The final step reads K .* M (written next to K by the cdist kernel) for the
+// document's words once.
 #include "wmd_internal.h"
 
 namespace wmd {
@@ -35,30 +32,30 @@ struct LoopParams {
   const int32_t* doc_words;
   const float* doc_vals;
   const void* K;
+  const void* KM;
   int ldk;
   int kcol0;
   const float* r;
   int v_r;
   int T;
-  double inv_lambda;
   const LoopItem* items;
   const int32_t* order;
   double* out;
+  const int* err;  // set by a cdist kernel that gave up waiting: results are NaN
 };
 
+// Loads the C columns of K row `row` that lane pi owns, as C/2 float2 pairs.
 template <typename KT, int C, int PI>
 __device__ __forceinline__ void load_krow(const KT* __restrict__ Kb, int64_t row, int ldk,
-                                          int kcol0, int pi, float (&dst)[C]) {
+                                          int kcol0, int pi, float2 (&dst)[C / 2]) {
   if constexpr (sizeof(KT) == 4) {
     const float4* src =
         reinterpret_cast<const float4*>(reinterpret_cast<const float*>(Kb) + row * ldk + kcol0);
 #pragma unroll
     for (int g = 0; g < C / 4; ++g) {
       const float4 t = __ldg(src + g * PI + pi);
-      dst[4 * g + 0] = t.x;
-      dst[4 * g + 1] = t.y;
-      dst[4 * g + 2] = t.z;
-      dst[4 * g + 3] = t.w;
+      dst[2 * g + 0] = make_float2(t.x, t.y);
+      dst[2 * g + 1] = make_float2(t.z, t.w);
     }
   } else {
     const uint2* src = reinterpret_cast<const uint2*>(
@@ -66,10 +63,8 @@ __device__ __forceinline__ void load_krow(const KT* __restrict__ Kb, int64_t row
 #pragma unroll
     for (int g = 0; g < C / 4; ++g) {
       const uint2 t = __ldg(src + g * PI + pi);
-      dst[4 * g + 0] = __uint_as_float(t.x << 16);
-      dst[4 * g + 1] = __uint_as_float(t.x & 0xffff0000u);
-      dst[4 * g + 2] = __uint_as_float(t.y << 16);
-      dst[4 * g + 3] = __uint_as_float(t.y & 0xffff0000u);
+      dst[2 * g + 0] = make_float2(__uint_as_float(t.x << 16), __uint_as_float(t.x & 0xffff0000u));
+      dst[2 * g + 1] = make_float2(__uint_as_float(t.y << 16), __uint_as_float(t.y & 0xffff0000u));
     }
   }
 }
@@ -78,215 +73,278 @@ __device__ __forceinline__ void team_barrier(int id, int nthreads) {
   asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
 }
 
-template <int VR, int PI, int RMAX, typename KT>
-__global__ void __launch_bounds__(128, 2) sinkhorn_fused_kernel(LoopParams p) {
+// Hardware reciprocal (PTX rcp.approx, about 1 ulp); operands here are never
+// zero: padding rows and columns are seeded so that their sums stay positive.
+__device__ __forceinline__ float fast_rcp(float x) {
+  float y;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
+struct TeamCtx {
+  int doc;
+  int64_t beg;
+  int n;
+  int W;
+  int kw;
+  int team;
+  int warp;
+  int lane;
+  int pi;
+  int pw;
+  int rpw_res;  // rows per warp when the document is register resident
+  int nch;      // chunks this warp handles
+  float* red;   // [2][4][VR] partial x of every warp of the CTA
+  double* wred; // [4] partial WMD of every warp of the CTA
+};
+
+// The whole solve of one document by one team, with R rows per lane known at
+// compile time (no per-row guards, so every phase is one straight-line block).
+// RELOAD: the document is longer than the team's registers; each pass re-reads
+// its chunks of K (from L2) instead of keeping them resident.
+template <int VR, int PI, int R, bool RELOAD, typename KT>
+__device__ __forceinline__ void solve(const LoopParams& p, const TeamCtx& t) {
   constexpr int C = VR / PI;
+  constexpr int C2 = C / 2;
   constexpr int PW = 32 / PI;
-  constexpr int RPW = PW * RMAX;
-  static_assert(C % 4 == 0, "columns per lane must be a multiple of 4");
-
-  __shared__ float red[2][4][VR];
-  __shared__ double wred[4];
-
-  const int warp = threadIdx.x >> 5;
-  const int lane = threadIdx.x & 31;
-  const int pi = lane % PI;
-  const int pw = lane / PI;
-  const LoopItem item = p.items[blockIdx.x];
-  const int W = item.W;
-  const int team = warp / W;
-  const int kw = warp - team * W;  // warp index inside the team
-  const int slot = item.begin + team;
-  if (team >= 4 / W || slot >= item.end) return;  // whole team leaves together
-
-  const int doc = p.order[slot];
-  const int64_t beg = p.doc_ptr[doc];
-  const int n = (int)(p.doc_ptr[doc + 1] - beg);
-  if (n == 0) {
-    if (kw == 0 && lane == 0) p.out[doc] = p.T >= 1 ? __longlong_as_double(0x7ff8000000000000ll) : 0.0;
-    return;
-  }
   const KT* Kb = static_cast<const KT*>(p.K);
+  const KT* KMb = static_cast<const KT*>(p.KM);
 
-  // rows of this warp: one resident chunk, or several chunks re-read per pass
-  const bool resident = n <= W * RPW;
-  int rpw_res = (n + W - 1) / W;
-  int nch;
-  if (resident) {
-    nch = (kw * rpw_res < n) ? 1 : 0;
-  } else {
-    const int nchunks_total = (n + RPW - 1) / RPW;
-    nch = (nchunks_total - kw + W - 1) / W;
-    if (nch < 0) nch = 0;
-  }
-
-  // query weights and the initial u = 1 / x = v_r for my columns
-  float rr[C], u[C];
+  // query weights and the initial u = 1 / x = v_r for my columns; x0 seeds
+  // the SpMM sums of padding columns with 1 so that 1/x stays finite there
+  // (their r is 0, so u = r / x = 0 and K = 0 keeps them out of every sum)
+  float2 rr[C2], u[C2], x0[C2];
 #pragma unroll
-  for (int j = 0; j < C; ++j) {
-    const int col = (j >> 2) * 4 * PI + 4 * pi + (j & 3);
-    const bool live = col < p.v_r;
-    rr[j] = live ? p.r[col] : 0.f;
-    u[j] = live ? (float)p.v_r : 0.f;
+  for (int q = 0; q < C2; ++q) {
+    const int col = (q >> 1) * 4 * PI + 4 * t.pi + 2 * (q & 1);
+    const bool l0 = col < p.v_r, l1 = col + 1 < p.v_r;
+    rr[q] = make_float2(l0 ? p.r[col] : 0.f, l1 ? p.r[col + 1] : 0.f);
+    u[q] = make_float2(l0 ? (float)p.v_r : 0.f, l1 ? (float)p.v_r : 0.f);
+    const bool seed = t.pw == 0 && t.kw == 0;
+    x0[q] = make_float2(l0 || !seed ? 0.f : 1.f, l1 || !seed ? 0.f : 1.f);
   }
 
-  float kt[RMAX][C];
-  float cw[RMAX];
-  int reff = 0;  // rows of the current chunk held by each row group
-
+  float2 kt[R][C2];
+  float cw[R];
+  auto chunk = [&](int m, int& start, int& len) {
+    if (RELOAD) {
+      start = (m * t.W + t.kw) * (PW * R);
+      len = min(PW * R, t.n - start);
+    } else {
+      start = t.kw * t.rpw_res;
+      len = min(t.rpw_res, t.n - start);
+    }
+  };
   auto load_chunk = [&](int m) {
     int start, len;
-    if (resident) {
-      start = kw * rpw_res;
-      len = min(rpw_res, n - start);
-    } else {
-      start = (m * W + kw) * RPW;
-      len = min(RPW, n - start);
-    }
-    reff = (len + PW - 1) / PW;
+    chunk(m, start, len);
 #pragma unroll
-    for (int rI = 0; rI < RMAX; ++rI) {
-      const int row = rI * PW + pw;
-      if (rI < reff && row < len) {
-        const int64_t e = beg + start + row;
-        const int wrow = p.doc_words[e];
+    for (int rI = 0; rI < R; ++rI) {
+      const int row = rI * PW + t.pw;
+      if (row < len) {
+        const int64_t e = t.beg + start + row;
         cw[rI] = p.doc_vals[e];
-        load_krow<KT, C, PI>(Kb, wrow, p.ldk, p.kcol0, pi, kt[rI]);
+        load_krow<KT, C, PI>(Kb, p.doc_words[e], p.ldk, p.kcol0, t.pi, kt[rI]);
       } else {
+        // padding row: c = 0 gives v = 0, and K = 1 keeps s > 0 so that
+        // c / s needs no guard
         cw[rI] = 0.f;
 #pragma unroll
-        for (int j = 0; j < C; ++j) kt[rI][j] = 0.f;
+        for (int q = 0; q < C2; ++q) kt[rI][q] = make_float2(1.f, 1.f);
       }
     }
   };
-
-  if (resident && nch) load_chunk(0);
+  if (!RELOAD && t.nch) load_chunk(0);
 
   int buf = 0;
-  double wacc = 0.0;
+  float wacc = 0.f;
   for (int it = 0; it <= p.T; ++it) {
     const bool last = it == p.T;
-    float xp[C];
+    float2 xp[C2];
 #pragma unroll
-    for (int j = 0; j < C; ++j) xp[j] = 0.f;
+    for (int q = 0; q < C2; ++q) xp[q] = x0[q];
 
-    for (int m = 0; m < nch; ++m) {
-      if (!resident) load_chunk(m);
-      // SDDMM: s_w = sum_i K[w, i] u_i over my columns, then over the PI lanes
-      float s[RMAX];
+    for (int m = 0; m < t.nch; ++m) {
+      if (RELOAD) load_chunk(m);
+      // SDDMM: s_w = sum_i K[w, i] u_i, my columns then the PI lanes of the row
+      float s[R];
 #pragma unroll
-      for (int rI = 0; rI < RMAX; ++rI) {
-        if (rI < reff) {
-          float a0 = 0.f, a1 = 0.f;
+      for (int rI = 0; rI < R; ++rI) {
+        float2 a = make_float2(0.f, 0.f);
 #pragma unroll
-          for (int j = 0; j < C; j += 2) {
-            a0 = fmaf(kt[rI][j], u[j], a0);
-            a1 = fmaf(kt[rI][j + 1], u[j + 1], a1);
-          }
-          s[rI] = a0 + a1;
-        }
+        for (int q = 0; q < C2; ++q) a = __ffma2_rn(kt[rI][q], u[q], a);
+        s[rI] = a.x + a.y;
       }
 #pragma unroll
       for (int off = 1; off < PI; off <<= 1) {
 #pragma unroll
-        for (int rI = 0; rI < RMAX; ++rI)
-          if (rI < reff) s[rI] += __shfl_xor_sync(0xffffffffu, s[rI], off);
+        for (int rI = 0; rI < R; ++rI) s[rI] += __shfl_xor_sync(0xffffffffu, s[rI], off);
       }
-      // v_w = c_w / s_w (rows past the document end carry c = 0, v = 0)
-      float v[RMAX];
+      // v_w = c_w / s_w (padding rows carry c = 0 and give v = 0)
+      float v[R];
 #pragma unroll
-      for (int rI = 0; rI < RMAX; ++rI)
-        v[rI] = (rI < reff && cw[rI] > 0.f) ? __fdividef(cw[rI], s[rI]) : 0.f;
+      for (int rI = 0; rI < R; ++rI) v[rI] = cw[rI] * fast_rcp(s[rI]);
 
       if (!last) {
         // SpMM: x_i += K[w, i] v_w over my rows
 #pragma unroll
-        for (int rI = 0; rI < RMAX; ++rI) {
-          if (rI < reff) {
+        for (int rI = 0; rI < R; ++rI) {
+          const float2 vv = make_float2(v[rI], v[rI]);
 #pragma unroll
-            for (int j = 0; j < C; ++j) xp[j] = fmaf(kt[rI][j], v[rI], xp[j]);
-          }
+          for (int q = 0; q < C2; ++q) xp[q] = __ffma2_rn(kt[rI][q], vv, xp[q]);
         }
       } else {
-        // final reduction: sum_w v_w sum_i u_i K[w,i] M[w,i], M = -ln(K)/lambda
+        // final reduction: sum_w v_w sum_i u_i (K .* M)[w, i]; a lane's few
+        // terms are summed in float32, lanes and warps in float64
+        int start, len;
+        chunk(m, start, len);
 #pragma unroll
-        for (int rI = 0; rI < RMAX; ++rI) {
-          if (rI < reff) {
-            float t = 0.f;
+        for (int rI = 0; rI < R; ++rI) {
+          const int row = rI * PW + t.pw;
+          if (row < len) {
+            float2 km[C2];
+            load_krow<KT, C, PI>(KMb, p.doc_words[t.beg + start + row], p.ldk, p.kcol0, t.pi, km);
+            float2 a = make_float2(0.f, 0.f);
 #pragma unroll
-            for (int j = 0; j < C; ++j) {
-              const float kk = kt[rI][j];
-              const float km = kk >= FLT_MIN ? -kk * __logf(kk) : 0.f;
-              t = fmaf(u[j], km, t);
-            }
-            wacc += (double)v[rI] * (double)t;
+            for (int q = 0; q < C2; ++q) a = __ffma2_rn(km[q], u[q], a);
+            wacc = fmaf(v[rI], a.x + a.y, wacc);
           }
         }
       }
     }
 
     if (!last) {
-      // x: sum over the PW row groups of this warp ...
+      // x: sum over the PW row groups of the warp ...
 #pragma unroll
       for (int off = PI; off < 32; off <<= 1) {
 #pragma unroll
-        for (int j = 0; j < C; ++j) xp[j] += __shfl_xor_sync(0xffffffffu, xp[j], off);
+        for (int q = 0; q < C2; ++q) {
+          const float2 o = make_float2(__shfl_xor_sync(0xffffffffu, xp[q].x, off),
+                                       __shfl_xor_sync(0xffffffffu, xp[q].y, off));
+          xp[q] = __fadd2_rn(xp[q], o);
+        }
       }
-      // ... and over the warps of the team
-      if (W > 1) {
-        if (pw == 0) {
+      // ... and over the warps of the team (fixed order, so deterministic)
+      if (t.W > 1) {
+        float* red = t.red + buf * 4 * VR;
+        if (t.pw == 0) {
 #pragma unroll
-          for (int j = 0; j < C; ++j) {
-            const int col = (j >> 2) * 4 * PI + 4 * pi + (j & 3);
-            red[buf][warp][col] = xp[j];
+          for (int q = 0; q < C2; ++q) {
+            const int col = (q >> 1) * 4 * PI + 4 * t.pi + 2 * (q & 1);
+            *reinterpret_cast<float2*>(&red[t.warp * VR + col]) = xp[q];
           }
         }
-        team_barrier(1 + team, 32 * W);
+        team_barrier(1 + t.team, 32 * t.W);
 #pragma unroll
-        for (int j = 0; j < C; ++j) {
-          const int col = (j >> 2) * 4 * PI + 4 * pi + (j & 3);
-          float x = 0.f;
-          for (int k2 = 0; k2 < W; ++k2) x += red[buf][team * W + k2][col];
-          xp[j] = x;
+        for (int q = 0; q < C2; ++q) {
+          const int col = (q >> 1) * 4 * PI + 4 * t.pi + 2 * (q & 1);
+          float2 x = make_float2(0.f, 0.f);
+          for (int k2 = 0; k2 < t.W; ++k2)
+            x = __fadd2_rn(x, *reinterpret_cast<const float2*>(&red[(t.team * t.W + k2) * VR + col]));
+          xp[q] = x;
         }
         buf ^= 1;
       }
       // u = 1 / x with x = diag(1/r) (K v):  u_i = r_i / (K v)_i
 #pragma unroll
-      for (int j = 0; j < C; ++j) u[j] = rr[j] > 0.f ? __fdividef(rr[j], xp[j]) : 0.f;
+      for (int q = 0; q < C2; ++q)
+        u[q] = __fmul2_rn(rr[q], make_float2(fast_rcp(xp[q].x), fast_rcp(xp[q].y)));
     }
   }
 
   // WMD_j: sum over the lanes of the warp, then over the team's warps
+  double wsum = (double)wacc;
 #pragma unroll
-  for (int off = 1; off < 32; off <<= 1) wacc += __shfl_xor_sync(0xffffffffu, wacc, off);
-  if (W > 1) {
-    if (lane == 0) wred[warp] = wacc;
-    team_barrier(1 + team, 32 * W);
-    if (kw == 0 && lane == 0) {
-      double t = 0.0;
-      for (int k2 = 0; k2 < W; ++k2) t += wred[team * W + k2];
-      p.out[doc] = t * p.inv_lambda;
+  for (int off = 1; off < 32; off <<= 1) wsum += __shfl_xor_sync(0xffffffffu, wsum, off);
+  if (t.W > 1) {
+    if (t.lane == 0) t.wred[t.warp] = wsum;
+    team_barrier(1 + t.team, 32 * t.W);
+    if (t.kw == 0 && t.lane == 0) {
+      double acc = 0.0;
+      for (int k2 = 0; k2 < t.W; ++k2) acc += t.wred[t.team * t.W + k2];
+      p.out[t.doc] = acc;
     }
-  } else if (lane == 0) {
-    p.out[doc] = wacc * p.inv_lambda;
+  } else if (t.lane == 0) {
+    p.out[t.doc] = wsum;
   }
 }
 
-// Per-class tile shapes: {VR, PI, RMAX}; RMAX * (VR / PI) = 96 registers of K.
+template <int VR, int PI, int RMAX, int MINB, typename KT>
+__global__ void __launch_bounds__(128, MINB) sinkhorn_fused_kernel(LoopParams p) {
+  constexpr int C = VR / PI;
+  constexpr int PW = 32 / PI;
+  constexpr int RPW = PW * RMAX;
+  constexpr int S = RMAX / 4;  // resident tiles come in 4 row-count steps
+  static_assert(C % 4 == 0, "columns per lane must be a multiple of 4");
+  static_assert(RMAX % 4 == 0, "RMAX must split into 4 steps");
+
+  __shared__ __align__(16) float red[2 * 4 * VR];
+  __shared__ double wred[4];
+
+  TeamCtx t;
+  t.warp = threadIdx.x >> 5;
+  t.lane = threadIdx.x & 31;
+  t.pi = t.lane % PI;
+  t.pw = t.lane / PI;
+  const LoopItem item = p.items[blockIdx.x];
+  t.W = item.W;
+  t.team = t.warp / t.W;
+  t.kw = t.warp - t.team * t.W;
+  const int slot = item.begin + t.team;
+  if (t.team >= 4 / t.W || slot >= item.end) return;  // whole team leaves together
+
+  t.doc = p.order[slot];
+  t.beg = p.doc_ptr[t.doc];
+  t.n = (int)(p.doc_ptr[t.doc + 1] - t.beg);
+  if (*p.err) {
+    if (t.kw == 0 && t.lane == 0) p.out[t.doc] = __longlong_as_double(0x7ff8000000000000ll);
+    return;
+  }
+  if (t.n == 0) {
+    if (t.kw == 0 && t.lane == 0)
+      p.out[t.doc] = p.T >= 1 ? __longlong_as_double(0x7ff8000000000000ll) : 0.0;
+    return;
+  }
+  t.red = red;
+  t.wred = wred;
+
+  if (t.n <= t.W * RPW) {
+    // register resident: one chunk of rpw_res rows per warp
+    t.rpw_res = (t.n + t.W - 1) / t.W;
+    const int start = t.kw * t.rpw_res;
+    t.nch = start < t.n ? 1 : 0;
+    const int len = t.nch ? min(t.rpw_res, t.n - start) : 0;
+    const int reff = (len + PW - 1) / PW;
+    switch ((reff + S - 1) / S) {
+      case 0:
+      case 1: solve<VR, PI, 1 * S, false, KT>(p, t); break;
+      case 2: solve<VR, PI, 2 * S, false, KT>(p, t); break;
+      case 3: solve<VR, PI, 3 * S, false, KT>(p, t); break;
+      default: solve<VR, PI, 4 * S, false, KT>(p, t); break;
+    }
+  } else {
+    t.rpw_res = 0;
+    const int nchunks_total = (t.n + RPW - 1) / RPW;
+    t.nch = max(0, (nchunks_total - t.kw + t.W - 1) / t.W);
+    solve<VR, PI, RMAX, true, KT>(p, t);
+  }
+}
+
+// Per-class tile shapes: {VR, PI, RMAX, CTAs per SM}; RMAX * (VR / PI) floats
+// of K per lane (96 or 128 registers).
 template <int CLS> struct ClassCfg;
-template <> struct ClassCfg<0> { static constexpr int VR = 8, PI = 2, RMAX = 24; };
-template <> struct ClassCfg<1> { static constexpr int VR = 16, PI = 4, RMAX = 24; };
-template <> struct ClassCfg<2> { static constexpr int VR = 32, PI = 4, RMAX = 12; };
-template <> struct ClassCfg<3> { static constexpr int VR = 64, PI = 8, RMAX = 12; };
-template <> struct ClassCfg<4> { static constexpr int VR = 128, PI = 8, RMAX = 6; };
-template <> struct ClassCfg<5> { static constexpr int VR = 256, PI = 16, RMAX = 6; };
+template <> struct ClassCfg<0> { static constexpr int VR = 8, PI = 2, RMAX = 24, MINB = 2; };
+template <> struct ClassCfg<1> { static constexpr int VR = 16, PI = 4, RMAX = 24, MINB = 3; };
+template <> struct ClassCfg<2> { static constexpr int VR = 32, PI = 4, RMAX = 12, MINB = 3; };
+template <> struct ClassCfg<3> { static constexpr int VR = 64, PI = 8, RMAX = 12, MINB = 3; };
+template <> struct ClassCfg<4> { static constexpr int VR = 128, PI = 8, RMAX = 8, MINB = 2; };
+template <> struct ClassCfg<5> { static constexpr int VR = 256, PI = 16, RMAX = 8, MINB = 2; };
 
 template <int CLS, typename KT>
 cudaError_t launch_cls(const LoopParams& p, int n_items, cudaStream_t s) {
   using Cf = ClassCfg<CLS>;
   if (n_items == 0) return cudaSuccess;
-  sinkhorn_fused_kernel<Cf::VR, Cf::PI, Cf::RMAX, KT><<<n_items, 128, 0, s>>>(p);
+  sinkhorn_fused_kernel<Cf::VR, Cf::PI, Cf::RMAX, Cf::MINB, KT><<<n_items, 128, 0, s>>>(p);
   return cudaGetLastError();
 }
 
@@ -315,23 +373,24 @@ int rows_per_warp(int cls) {
   }
 }
 
-cudaError_t launch_loop(const wmd_corpus* c, int cls, const void* K, int ldk, int kcol0,
-                        const float* r, int v_r, float lambda, int T, wmd_precision prec,
+cudaError_t launch_loop(const wmd_corpus* c, int cls, const void* K, const void* KM, int ldk,
+                        int kcol0, const float* r, int v_r, int T, wmd_precision prec,
                         double* out, cudaStream_t s) {
   LoopParams p;
   p.doc_ptr = c->doc_ptr;
   p.doc_words = c->doc_words;
   p.doc_vals = c->doc_vals;
   p.K = K;
+  p.KM = KM;
   p.ldk = ldk;
   p.kcol0 = kcol0;
   p.r = r;
   p.v_r = v_r;
   p.T = T;
-  p.inv_lambda = 1.0 / (double)lambda;
   p.items = c->sched[cls].d_items;
   p.order = c->order;
   p.out = out;
+  p.err = c->d_err;
   if (prec == WMD_PREC_BF16_K) return dispatch_loop<__nv_bfloat16>(cls, p, c->sched[cls].n_items, s);
   return dispatch_loop<float>(cls, p, c->sched[cls].n_items, s);
 }

@@ -70,6 +70,10 @@ struct wmd_corpus {
   int32_t* order = nullptr;    // N, documents by decreasing length
   wmd::Schedule sched[wmd::kNumClasses];
   size_t device_bytes = 0;
+  int num_sms = 0;
+  int* d_err = nullptr;        // device-side timeout flag (sticky); also read by wmd_query
+  bool tmap_ok = false;        // tensor-core cdist available (TMA descriptor built)
+  alignas(64) unsigned char tmap_vecs[128];  // CUtensorMap of vecs (128-byte tiles of 128 rows)
 
   // host path (wmd_query) state, guarded by mu
   std::mutex mu;
@@ -78,24 +82,28 @@ struct wmd_corpus {
   size_t ws_bytes = 0;
   int32_t* d_qids = nullptr;
   float* d_qw = nullptr;
-  double* d_out = nullptr;
+  double* d_out = nullptr;     // N doubles followed by one int error word (host path)
 };
 
 namespace wmd {
 
 // Workspace carve-up for one query of class VR: the padded query weights r
-// (VR floats) and the word-major K (U x VR).
+// (VR floats) and the word-major K and K .* M (U x VR each).
 struct WsLayout {
-  size_t r_off, k_off, total;
+  size_t r_off, k_off, km_off, total;
 };
 WsLayout ws_layout(const wmd_corpus* c, int VR, wmd_precision prec);
 
 // Kernel launchers (cdist.cu / sinkhorn.cu).
 cudaError_t launch_cdist(const wmd_corpus* c, const int32_t* q_ids, const float* q_w, int v_r,
-                         int VR, float lambda, wmd_precision prec, void* K, int ldk, int kcol0,
-                         float* r_out, cudaStream_t s);
-cudaError_t launch_loop(const wmd_corpus* c, int cls, const void* K, int ldk, int kcol0,
-                        const float* r, int v_r, float lambda, int T, wmd_precision prec,
+                         int VR, float lambda, wmd_precision prec, void* K, void* KM, int ldk,
+                         int kcol0, float* r_out, cudaStream_t s);
+cudaError_t launch_cdist_tc(const wmd_corpus* c, const int32_t* q_ids, const float* q_w, int v_r,
+                            int VR, float lambda, wmd_precision prec, void* K, void* KM, int ldk,
+                            int kcol0, float* r_out, int* err, cudaStream_t s);
+bool make_vecs_tensor_map(wmd_corpus* c);
+cudaError_t launch_loop(const wmd_corpus* c, int cls, const void* K, const void* KM, int ldk,
+                        int kcol0, const float* r, int v_r, int T, wmd_precision prec,
                         double* out, cudaStream_t s);
 
 }  // namespace wmd

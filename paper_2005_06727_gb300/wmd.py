@@ -64,8 +64,7 @@ _SIGS = {
     "wmd_workspace_bytes": (C.c_size_t, [_P, C.c_int32, C.c_int]),
     "wmd_build_kernel_matrix": (C.c_int, [_P, _P, _P, C.c_int32, C.c_float, C.c_int, _P,
                                           C.c_size_t, _P]),
-    "wmd_sinkhorn_loop": (C.c_int, [_P, C.c_int32, C.c_float, C.c_int32, C.c_int, _P,
-                                    C.c_size_t, _P, _P]),
+    "wmd_sinkhorn_loop": (C.c_int, [_P, C.c_int32, C.c_int32, C.c_int, _P, C.c_size_t, _P, _P]),
     "wmd_query_device": (C.c_int, [_P, _P, _P, C.c_int32, C.c_float, C.c_int32, C.c_int, _P,
                                    C.c_size_t, _P, _P]),
 }
@@ -196,10 +195,9 @@ class Corpus:
                                              float(lam), int(prec), _dptr(ws), int(ws_bytes),
                                              _stream_ptr(stream)))
 
-    def sinkhorn_loop(self, v_r, lam, max_iter, prec, ws, ws_bytes, d_out, stream=None):
-        _check(lib().wmd_sinkhorn_loop(self._h, int(v_r), float(lam), int(max_iter), int(prec),
-                                       _dptr(ws), int(ws_bytes), _dptr(d_out),
-                                       _stream_ptr(stream)))
+    def sinkhorn_loop(self, v_r, max_iter, prec, ws, ws_bytes, d_out, stream=None):
+        _check(lib().wmd_sinkhorn_loop(self._h, int(v_r), int(max_iter), int(prec), _dptr(ws),
+                                       int(ws_bytes), _dptr(d_out), _stream_ptr(stream)))
 
     def query_device(self, d_ids, d_w, v_r, lam, max_iter, prec, ws, ws_bytes, d_out,
                      stream=None):

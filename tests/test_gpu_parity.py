@@ -247,3 +247,79 @@ def test_out_of_range_device_id_gives_nan_not_a_fault(wmd):
     corpus.query_device(ids, w, 2, 10.0, 5, wmd.PREC_FP32, ws, nb, out)
     torch.cuda.synchronize()
     assert torch.isnan(out).all()
+
+
+# ---------------------------------------------------------------- K1 directly
+def _active_words(c):
+    return np.flatnonzero(np.diff(c.row_ptr))
+
+
+def _workspace_k(wmd, corpus, dq, VR, prec):
+    """K and K .* M (U x VR) read back from the workspace after the cdist stage."""
+    import torch
+    U = corpus.U
+    esz = 2 if prec == wmd.PREC_BF16_K else 4
+    k_off = 256 if VR * 4 <= 256 else (VR * 4 + 255) // 256 * 256
+    kbytes = (U * VR * esz + 255) // 256 * 256
+    raw = dq.ws.cpu()
+    dt = torch.bfloat16 if esz == 2 else torch.float32
+    K = raw[k_off:k_off + U * VR * esz].view(dt).float().numpy().reshape(U, VR)
+    KM = raw[k_off + kbytes:k_off + kbytes + U * VR * esz].view(dt).float().numpy().reshape(U, VR)
+    return K, KM
+
+
+@pytest.mark.parametrize("kernel", ["tc", "simt"])
+@pytest.mark.parametrize("v_r", [5, 16, 30, 64, 100])
+def test_cdist_kernel_matrix_elementwise(wmd, monkeypatch, kernel, v_r):
+    """K = exp(-lambda M) and K .* M against the oracle's FP64 distances, for
+    the tensor-core (3xTF32) and the CUDA-core kernel; the query's own words
+    give K = 1 and K .* M = 0 exactly."""
+    import torch
+    if kernel == "simt":
+        monkeypatch.setenv("WMD_CDIST_KERNEL", "simt")
+    else:
+        monkeypatch.delenv("WMD_CDIST_KERNEL", raising=False)
+    V, lam = 5000, 10.0
+    vecs = synth.make_vecs(V, 300, 11)
+    c = synth.make_corpus(V, 300, 5, 60, 12)
+    q_ids, q_w = synth.make_query(V, v_r, 13)
+    corpus = wmd.Corpus.from_synth(vecs, c)
+    # float32 tolerance from the arithmetic: m^2 = |a|^2 + |b|^2 - 2 a.b carries
+    # a few ulps of |a|^2 + |b|^2 ~ 2 (about 1e-6 absolute); distinct N(0, 1/d)
+    # words are >= ~0.5 apart, so |dm| <= 1e-6 and |dK / K| = lambda |dm| <= 1e-5.
+    # bfloat16 storage adds its 2^-9 rounding.
+    for prec, rtol in [(wmd.PREC_FP32, 1e-5), (wmd.PREC_BF16_K, 1e-2)]:
+        dq = wmd.DeviceQuery(corpus, q_ids, q_w, prec)
+        corpus.build_kernel_matrix(dq.ids, dq.w, dq.v_r, lam, prec, dq.ws, dq.ws_bytes)
+        torch.cuda.synchronize()
+        VR = 8
+        while VR < v_r:
+            VR *= 2
+        K, KM = _workspace_k(wmd, corpus, dq, VR, prec)
+        words = _active_words(c)
+        M = orc.cdist(vecs, q_ids, words).T                    # U x v_r
+        Kw = np.exp(-lam * M)
+        np.testing.assert_allclose(K[:, :v_r], Kw, rtol=rtol, atol=0)
+        np.testing.assert_allclose(KM[:, :v_r], Kw * M, rtol=rtol, atol=1e-30)
+        assert np.all(K[:, v_r:] == 0) and np.all(KM[:, v_r:] == 0)
+        own = np.isin(words, q_ids)
+        rows, cols = np.nonzero(words[:, None] == q_ids[None, :])
+        assert np.all(K[rows, cols] == 1.0) and np.all(KM[rows, cols] == 0.0)
+        assert own.sum() == len(rows)
+
+
+@pytest.mark.parametrize("kernel", ["tc", "simt"])
+def test_paper_shaped_with_both_cdist_kernels(wmd, monkeypatch, kernel):
+    if kernel == "simt":
+        monkeypatch.setenv("WMD_CDIST_KERNEL", "simt")
+    else:
+        monkeypatch.delenv("WMD_CDIST_KERNEL", raising=False)
+    w = synth.PAPER
+    vecs, c, qs = synth.make_workload(w)
+    corpus = wmd.Corpus.from_synth(vecs, c)
+    q_ids, q_w = qs[0]
+    rng = np.random.default_rng(5)
+    docs = np.sort(rng.choice(c.N, 300, replace=False))
+    want = oracle(vecs, c, q_ids, q_w, w.lam, w.max_iter, docs=docs)
+    got = corpus.query(q_ids, q_w, w.lam, w.max_iter)
+    assert_parity(got[docs], want, FP32_RTOL, f"paper-shaped fp32 {kernel}")
