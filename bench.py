@@ -281,7 +281,7 @@ def run_ours(args, w):
 
     # roofline of the dominant kernel
     peaks, peak_kind = measured_peaks()
-    U, ldv = corpus.U, (w.d + 3) // 4 * 4
+    U, ldv = corpus.U, w.d
     VR = 8
     while VR < v_r:
         VR *= 2

@@ -179,7 +179,9 @@ wmd_status wmd_corpus_load(const float* vecs, int64_t V, int32_t d, const int64_
   c->N = N;
   c->nnz = nnz;
   c->d = d;
-  c->ldv = (int32_t)align_up((size_t)d, 4);  // 16-byte rows for vector loads
+  // rows padded to 128 bytes: every 32-float k-block of a row is one whole
+  // cache line for the TMA tiles of the cdist kernel
+  c->ldv = (int32_t)align_up((size_t)d, 32);
 
   // active vocabulary first: device row of word w
   std::vector<int32_t> perm(V);
@@ -401,13 +403,13 @@ wmd_status wmd_query(wmd_corpus* c, const int32_t* q_ids, const float* q_w, int3
   WMD_CUDA_TRY(cudaStreamSynchronize(c->stream));
   if (err) {
     static const char* roles[] = {"?", "producer (stage free)", "converter (tile landed)",
-                                  "MMA (accumulator free)", "MMA (tile converted)",
-                                  "epilogue (accumulator full)"};
+                                  "MMA (accumulator free)", "MMA (tile landed or converted)",
+                                  "epilogue (accumulator full)", "converter (lo slot free)"};
     const int role = (err >> 24) & 0x3f;
     char msg[160];
     std::snprintf(msg, sizeof msg,
                   "a device-side wait in the cdist kernel timed out: %s, iteration %d (code 0x%08x)",
-                  roles[role < 6 ? role : 0], err & 0xffffff, (unsigned)err);
+                  roles[role < 7 ? role : 0], err & 0xffffff, (unsigned)err);
     return set_error(WMD_ERR_TIMEOUT, msg);
   }
   return WMD_OK;

@@ -6,7 +6,9 @@
 // vocabulary (V x d), and the same kernel also emits K (Algorithm 1).  Here
 // that GEMM runs on tcgen05 with float32 accuracy from TF32 inputs
 // (3xTF32: a = a_hi + a_lo, a.b ~ a_hi.b_hi + a_hi.b_lo + a_lo.b_hi, dropping
-// only a_lo.b_lo, which is 2^-20 relative), accumulating in TMEM.
+// only a_lo.b_lo, which is 2^-20 relative), accumulating in TMEM.  B is kept
+// as one 2N-row operand [B_hi; B_lo], so a_hi.b_hi and a_hi.b_lo come out of
+// a single N = 2N MMA that reads the A tile once; a_lo.b_hi is a second MMA.
 //
 // One persistent CTA per SM walks 128-row tiles of the active vocabulary:
 //   warp 8        TMA producer: 128 x 32 float32 k-blocks of vecs, 128B-swizzled
@@ -14,7 +16,8 @@
 //   warp 9        MMA issuer (one thread) and TMEM owner
 //   warps 0..3    epilogue: TMEM -> registers, m, K, K .* M, word-major stores
 // The query side (B, N x d) is gathered once per CTA into shared memory, split
-// into hi/lo parts and kept resident.  Accumulators are double buffered in
+// into hi/lo parts and kept resident.  The hi part of A is the landed float32
+// tile itself (the tensor core reads the tf32 bits of each operand).  Accumulators are double buffered in
 // TMEM so the epilogue of tile t overlaps the MMAs of tile t+1.  Every wait is
 // bounded: on a timeout the CTA raises a flag, drains what it issued, frees
 // its TMEM and returns.
@@ -57,6 +60,21 @@ struct Params {
   int KB;
   int* err;
 };
+
+#ifdef WMD_TC_TRACE
+// Timeline of the first CTAs (globaltimer, ns) for tuning: [cta][event][index].
+__device__ long long g_tc_trace[4][8][64];
+__device__ __forceinline__ void trace(int ev, int idx) {
+  if (blockIdx.x < 4 && idx < 64) {
+    long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    g_tc_trace[blockIdx.x][ev][idx] = t;
+  }
+}
+#define TC_TRACE(ev, idx) trace(ev, idx)
+#else
+#define TC_TRACE(ev, idx) ((void)0)
+#endif
 
 // ------------------------------------------------------------------ PTX helpers
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -177,7 +195,7 @@ __device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
 
 // Instruction descriptor for kind::tf32: D float32, A and B tf32, both
 // K-major, shape M x N.
-constexpr uint32_t idesc_tf32(int M, int N) {
+__host__ __device__ constexpr uint32_t idesc_tf32(int M, int N) {
   return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(N >> 3) << 17) |
          ((uint32_t)(M >> 4) << 24);
 }
@@ -218,9 +236,11 @@ __device__ __forceinline__ void tmem_load<32>(uint32_t taddr, float* v) {
   for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+// TMEM columns per tile buffer: 2N for a_hi.[b_hi | b_lo] and N for
+// a_lo.b_hi; two buffers, rounded up to a power of two.
 template <int N>
-constexpr int tmem_cols() {
-  return 2 * N <= 32 ? 32 : (2 * N <= 64 ? 64 : (2 * N <= 128 ? 128 : 256));
+__host__ __device__ constexpr int tmem_cols() {
+  return 6 * N <= 32 ? 32 : (6 * N <= 64 ? 64 : (6 * N <= 128 ? 128 : (6 * N <= 256 ? 256 : 512)));
 }
 
 // Stores the first n (a multiple of 4, n <= N) values of a row.
@@ -247,21 +267,25 @@ __device__ __forceinline__ void store_row(__nv_bfloat16* dst, const float (&v)[N
 }
 
 // ------------------------------------------------------------------ kernel
-template <int N, int S, typename KT>
+// N: query columns of the tile (MMA N); S: TMA stages of A; LS: slots of the
+// lo-part ring (the hi part is the landed float32 tile itself: the tensor
+// core reads only the tf32 bits of each operand, and lo = a - tf32(a)).
+template <int N, int S, int LS, typename KT>
 __global__ void __launch_bounds__(kThreads, 1)
     cdist_tc_kernel(const __grid_constant__ CUtensorMap tmap_a, const Params p) {
-  constexpr uint32_t kIdesc = idesc_tf32(kM, N);
+  constexpr uint32_t kIdesc2 = idesc_tf32(kM, 2 * N);  // a_hi . [b_hi | b_lo]
+  constexpr uint32_t kIdesc = idesc_tf32(kM, N);       // a_lo . b_hi
   constexpr int kCols = tmem_cols<N>();
+  static_assert(LS < S, "the lo ring must be shorter than the stage ring");
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
 
   const int KB = p.KB;
-  const int bblock = N * 128;                   // bytes of one B k-block
-  uint8_t* Bhi = smem;
-  uint8_t* Blo = Bhi + KB * bblock;
-  uint8_t* Abuf = Blo + KB * bblock;            // S stages, hi in place after conversion
-  uint8_t* Lbuf = Abuf + S * kStageBytes;       // S stages of lo parts
-  uint64_t* bars = reinterpret_cast<uint64_t*>(Lbuf + S * kStageBytes);
+  const int bblock = 2 * N * 128;               // bytes of one [B_hi; B_lo] k-block
+  uint8_t* Bcat = smem;
+  uint8_t* Abuf = Bcat + KB * bblock;           // S stages of landed float32 tiles
+  uint8_t* Lbuf = Abuf + S * kStageBytes;       // LS slots of lo parts
+  uint64_t* bars = reinterpret_cast<uint64_t*>(Lbuf + LS * kStageBytes);
   uint64_t* full = bars;
   uint64_t* conv = full + S;
   uint64_t* empty = conv + S;
@@ -277,25 +301,9 @@ __global__ void __launch_bounds__(kThreads, 1)
   const int tid = threadIdx.x;
   const int warp = tid >> 5;
   const int lane = tid & 31;
+  if (tid == 0) TC_TRACE(5, 0);
 
-  // ---- prologue: query columns, barriers, TMEM, resident B (hi/lo)
-  if (tid < N) {
-    int row = -1;
-    float nq = 0.f;
-    if (tid < p.v_r) {
-      const int64_t id = p.q_ids[tid];
-      if (id >= 0 && id < p.V) {
-        row = p.perm[id];
-        nq = p.norms[row];
-      } else {
-        row = -2;
-        nq = __int_as_float(0x7fc00000);
-      }
-    }
-    qrow_s[tid] = row;
-    qn_s[tid] = nq;
-  }
-  if (p.r_out && blockIdx.x == 0 && tid < p.VR) p.r_out[tid] = tid < p.v_r ? p.q_w[tid] : 0.f;
+  // ---- prologue: barriers and TMEM only, so that the producer starts at once
   if (tid == 0) {
     for (int s = 0; s < S; ++s) {
       mbar_init(&full[s], 1);
@@ -313,39 +321,77 @@ __global__ void __launch_bounds__(kThreads, 1)
     fence_async_smem();
   }
   if (warp == 9) tmem_alloc(tmem_base_s, kCols);
-  __syncthreads();
-
-  // B[n][k] = query row n, split into tf32 hi and lo parts, written in the
-  // 128B-swizzled K-major layout: chunk c of row n lands at chunk c ^ (n % 8)
-  for (int idx = tid; idx < N * KB * 8; idx += kThreads) {
-    const int n = idx / (KB * 8);
-    const int rem = idx - n * KB * 8;
-    const int kb = rem >> 3;
-    const int ch = rem & 7;
-    const int k = kb * kKB + ch * 4;
-    const int row = qrow_s[n];
-    float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-    if (row >= 0 && k < p.ldv)
-      v = __ldg(reinterpret_cast<const float4*>(p.vecs + (size_t)row * p.ldv + k));
-    else if (row == -2)
-      v = make_float4(__int_as_float(0x7fc00000), 0.f, 0.f, 0.f);
-    float4 hi, lo;
-    hi.x = __uint_as_float(__float_as_uint(v.x) & 0xFFFFE000u);
-    hi.y = __uint_as_float(__float_as_uint(v.y) & 0xFFFFE000u);
-    hi.z = __uint_as_float(__float_as_uint(v.z) & 0xFFFFE000u);
-    hi.w = __uint_as_float(__float_as_uint(v.w) & 0xFFFFE000u);
-    lo = make_float4(v.x - hi.x, v.y - hi.y, v.z - hi.z, v.w - hi.w);
-    const int off = kb * bblock + n * 128 + ((ch ^ (n & 7)) << 4);
-    *reinterpret_cast<float4*>(Bhi + off) = hi;
-    *reinterpret_cast<float4*>(Blo + off) = lo;
-  }
-  fence_async_smem();
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem_base = *tmem_base_s;
-
   const int nlt = (p.num_tiles - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x;
+
+  if (warp != 8) {
+    // ---------------------------------------------------------------- B, all but the producer
+    // query columns (device row, norm), the padded weights, then the resident
+    // B = query rows split into tf32 hi and lo parts in the 128B-swizzled
+    // K-major layout (chunk c of row n lands at chunk c ^ (n % 8)); every
+    // thread issues all its loads before its first store
+    constexpr int kBT = kThreads - 32;
+    const int bt = tid < 256 ? tid : tid - 32;  // 0 .. 287
+    if (bt < N) {
+      int row = -1;
+      if (bt < p.v_r) {
+        const int64_t id = p.q_ids[bt];
+        row = (id >= 0 && id < p.V) ? p.perm[id] : -2;
+      }
+      qrow_s[bt] = row;
+    }
+    if (p.r_out && blockIdx.x == 0 && bt < p.VR) p.r_out[bt] = bt < p.v_r ? p.q_w[bt] : 0.f;
+    asm volatile("bar.sync 1, %0;" ::"r"(kBT) : "memory");
+    const int total = N * KB * 8;
+    for (int base = bt; base < total; base += kBT * 12) {
+      float4 v[12];
+#pragma unroll
+      for (int j = 0; j < 12; ++j) {
+        const int idx = base + j * kBT;
+        v[j] = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (idx < total) {
+          const int n = idx / (KB * 8);
+          const int rem = idx - n * KB * 8;
+          const int k = (rem >> 3) * kKB + (rem & 7) * 4;
+          const int row = qrow_s[n];
+          if (row >= 0 && k < p.ldv)
+            v[j] = __ldg(reinterpret_cast<const float4*>(p.vecs + (size_t)row * p.ldv + k));
+          else if (row == -2)
+            v[j] = make_float4(__int_as_float(0x7fc00000), 0.f, 0.f, 0.f);
+        }
+      }
+#pragma unroll
+      for (int j = 0; j < 12; ++j) {
+        const int idx = base + j * kBT;
+        if (idx < total) {
+          const int n = idx / (KB * 8);
+          const int rem = idx - n * KB * 8;
+          const int kb = rem >> 3;
+          const int ch = rem & 7;
+          float4 hi;
+          hi.x = __uint_as_float(__float_as_uint(v[j].x) & 0xFFFFE000u);
+          hi.y = __uint_as_float(__float_as_uint(v[j].y) & 0xFFFFE000u);
+          hi.z = __uint_as_float(__float_as_uint(v[j].z) & 0xFFFFE000u);
+          hi.w = __uint_as_float(__float_as_uint(v[j].w) & 0xFFFFE000u);
+          const float4 lo = make_float4(v[j].x - hi.x, v[j].y - hi.y, v[j].z - hi.z, v[j].w - hi.w);
+          const int nl = n + N;  // row of the lo part in the 2N-row operand
+          *reinterpret_cast<float4*>(Bcat + kb * bblock + n * 128 + ((ch ^ (n & 7)) << 4)) = hi;
+          *reinterpret_cast<float4*>(Bcat + kb * bblock + nl * 128 + ((ch ^ (nl & 7)) << 4)) = lo;
+        }
+      }
+    }
+    // norms of the query words (off the load chain of B)
+    if (bt < N) {
+      const int row = qrow_s[bt];
+      qn_s[bt] = row >= 0 ? p.norms[row] : (row == -2 ? __int_as_float(0x7fc00000) : 0.f);
+    }
+    fence_async_smem();
+    asm volatile("bar.sync 1, %0;" ::"r"(kBT) : "memory");  // B resident for everyone
+    if (tid == 0) TC_TRACE(5, 1);
+  }
 
   if (warp == 8) {
     // ---------------------------------------------------------------- producer
@@ -364,6 +410,7 @@ __global__ void __launch_bounds__(kThreads, 1)
           }
           mbar_expect_tx(&full[s], kStageBytes);
           tma_load_2d(Abuf + s * kStageBytes, &tmap_a, &full[s], kb * kKB, w0);
+          TC_TRACE(0, it);
         }
       }
       if (*abort_flag) {
@@ -377,6 +424,8 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
   } else if (warp >= 4 && warp < 8) {
     // ---------------------------------------------------------------- converters
+    // lo = a - tf32(a) of every landed tile, into ring slot it % LS once the
+    // MMAs that read that slot (iteration it - LS) have completed
     const int ct = tid - 128;
     int it = 0;
     bool ok = true;
@@ -388,19 +437,26 @@ __global__ void __launch_bounds__(kThreads, 1)
           ok = false;
           break;
         }
-        float4* A4 = reinterpret_cast<float4*>(Abuf + s * kStageBytes);
-        float4* L4 = reinterpret_cast<float4*>(Lbuf + s * kStageBytes);
+        if (ct == 0) TC_TRACE(1, it);
+        if (it >= LS) {
+          const int j = it - LS;
+          if (!mbar_wait(&empty[j % S], (uint32_t)(j / S) & 1u, abort_flag, 6, it)) {
+            ok = false;
+            break;
+          }
+        }
+        const float4* A4 = reinterpret_cast<const float4*>(Abuf + s * kStageBytes);
+        float4* L4 = reinterpret_cast<float4*>(Lbuf + (it % LS) * kStageBytes);
+        float4 v[kStageBytes / 16 / 128];
+#pragma unroll
+        for (int j = 0; j < kStageBytes / 16 / 128; ++j) v[j] = A4[ct + 128 * j];
 #pragma unroll
         for (int j = 0; j < kStageBytes / 16 / 128; ++j) {
-          const int i = ct + 128 * j;
-          const float4 v = A4[i];
-          float4 hi;
-          hi.x = __uint_as_float(__float_as_uint(v.x) & 0xFFFFE000u);
-          hi.y = __uint_as_float(__float_as_uint(v.y) & 0xFFFFE000u);
-          hi.z = __uint_as_float(__float_as_uint(v.z) & 0xFFFFE000u);
-          hi.w = __uint_as_float(__float_as_uint(v.w) & 0xFFFFE000u);
-          A4[i] = hi;
-          L4[i] = make_float4(v.x - hi.x, v.y - hi.y, v.z - hi.z, v.w - hi.w);
+          const float4 a = v[j];
+          L4[ct + 128 * j] = make_float4(a.x - __uint_as_float(__float_as_uint(a.x) & 0xFFFFE000u),
+                                         a.y - __uint_as_float(__float_as_uint(a.y) & 0xFFFFE000u),
+                                         a.z - __uint_as_float(__float_as_uint(a.z) & 0xFFFFE000u),
+                                         a.w - __uint_as_float(__float_as_uint(a.w) & 0xFFFFE000u));
         }
         fence_async_smem();
         mbar_arrive(&conv[s]);
@@ -417,25 +473,35 @@ __global__ void __launch_bounds__(kThreads, 1)
         const uint32_t aph = (uint32_t)(lt >> 1) & 1u;
         if (!mbar_wait(&tempty[ab], aph ^ 1u, abort_flag, 3, lt)) break;
         tc_fence_after();
-        const uint32_t d_tmem = tmem_base + (uint32_t)(ab * N);
+        const uint32_t d_tmem = tmem_base + (uint32_t)(ab * 3 * N);
         for (int kb = 0; kb < KB; ++kb, ++it) {
           const int s = it % S;
           const uint32_t ph = (uint32_t)(it / S) & 1u;
-          if (!mbar_wait(&conv[s], ph, abort_flag, 4, it)) {
+          const uint32_t a_hi = smem_u32(Abuf + s * kStageBytes);
+          const uint32_t a_lo = smem_u32(Lbuf + (it % LS) * kStageBytes);
+          const uint32_t b_cat = smem_u32(Bcat + kb * bblock);  // rows 0..N-1 are b_hi
+          // a_hi . [b_hi | b_lo] as soon as the tile lands ...
+          if (!mbar_wait(&full[s], ph, abort_flag, 4, it)) {
             ok = false;
             break;
           }
           tc_fence_after();
-          const uint32_t a_hi = smem_u32(Abuf + s * kStageBytes);
-          const uint32_t a_lo = smem_u32(Lbuf + s * kStageBytes);
-          const uint32_t b_hi = smem_u32(Bhi + kb * bblock);
-          const uint32_t b_lo = smem_u32(Blo + kb * bblock);
 #pragma unroll
           for (int ks = 0; ks < kKB / 8; ++ks) {
             const uint32_t o = ks * 32;  // 8 tf32 = 32 bytes along K
-            mma_tf32(d_tmem, sw128_desc(a_lo + o), sw128_desc(b_hi + o), kIdesc, (kb | ks) != 0);
-            mma_tf32(d_tmem, sw128_desc(a_hi + o), sw128_desc(b_lo + o), kIdesc, 1);
-            mma_tf32(d_tmem, sw128_desc(a_hi + o), sw128_desc(b_hi + o), kIdesc, 1);
+            mma_tf32(d_tmem, sw128_desc(a_hi + o), sw128_desc(b_cat + o), kIdesc2, (kb | ks) != 0);
+          }
+          // ... a_lo . b_hi once the converters wrote the lo part
+          if (!mbar_wait(&conv[s], ph, abort_flag, 4, it)) {
+            ok = false;
+            break;
+          }
+          TC_TRACE(2, it);
+          tc_fence_after();
+#pragma unroll
+          for (int ks = 0; ks < kKB / 8; ++ks) {
+            const uint32_t o = ks * 32;
+            mma_tf32(d_tmem + 2 * N, sw128_desc(a_lo + o), sw128_desc(b_cat + o), kIdesc, (kb | ks) != 0);
           }
           mma_commit(&empty[s]);
         }
@@ -454,37 +520,43 @@ __global__ void __launch_bounds__(kThreads, 1)
     for (int lt = 0; lt < nlt; ++lt) {
       const int ab = lt & 1;
       const uint32_t aph = (uint32_t)(lt >> 1) & 1u;
+      const int64_t w = (int64_t)((int)blockIdx.x + lt * (int)gridDim.x) * kM + row_in_tile;
+      const float nw = w < p.U ? p.norms[w] : 0.f;  // issued before the wait
       if (!mbar_wait(&tfull[ab], aph, abort_flag, 5, lt)) break;
+      if (tid == 0) TC_TRACE(3, lt);
       tc_fence_after();
-      const uint32_t taddr = tmem_base + ((uint32_t)(warp * 32) << 16) + (uint32_t)(ab * N);
+      // a.b = a_hi.b_hi (columns 0..N-1) + a_hi.b_lo (N..2N-1) + a_lo.b_hi (2N..3N-1)
+      const uint32_t taddr = tmem_base + ((uint32_t)(warp * 32) << 16) + (uint32_t)(ab * 3 * N);
+      constexpr int CH = N < 32 ? N : 32;
 #pragma unroll
-      for (int c = 0; c < N; c += (N < 32 ? N : 32)) tmem_load<(N < 32 ? N : 32)>(taddr + c, acc + c);
+      for (int c = 0; c < N; c += CH) {
+        float t1[CH], t2[CH];
+        tmem_load<CH>(taddr + c, acc + c);
+        tmem_load<CH>(taddr + N + c, t1);
+        tmem_load<CH>(taddr + 2 * N + c, t2);
+#pragma unroll
+        for (int j = 0; j < CH; ++j) acc[c + j] = (t2[j] + t1[j]) + acc[c + j];
+      }
       tc_fence_before();
       mbar_arrive(&tempty[ab]);
 
-      const int64_t w = (int64_t)((int)blockIdx.x + lt * (int)gridDim.x) * kM + row_in_tile;
       if (w < p.U) {
-        const float nw = p.norms[w];
+        // m^2 = |a|^2 + |b|^2 - 2 a.b (clamped), K = exp(-lambda m), K .* M;
+        // the query's own word is exactly m = 0; padding columns are 0 and an
+        // id outside [0, V) gives NaN
         float kv[N], kmv[N];
 #pragma unroll
         for (int j = 0; j < N; ++j) {
+          const float m = sqrtf(fmaxf((nw + qn_s[j]) - 2.f * acc[j], 0.f));
+          const float e = expf(-p.lambda * m);
           const int qr = qrow_s[j];
-          float k, km;
-          if (j >= p.v_r) {
-            k = km = 0.f;
-          } else if (qr == (int)w) {
-            k = 1.f;
-            km = 0.f;
-          } else if (qr == -2) {
-            k = km = __int_as_float(0x7fc00000);
-          } else {
-            const float m2 = (nw + qn_s[j]) - 2.f * acc[j];
-            const float m = sqrtf(fmaxf(m2, 0.f));
-            k = expf(-p.lambda * m);
-            km = k * m;
-          }
-          kv[j] = k;
-          kmv[j] = km;
+          const bool own = qr == (int)w;
+          float k = own ? 1.f : e;
+          float km = own ? 0.f : e * m;
+          k = qr == -2 ? __int_as_float(0x7fc00000) : k;
+          km = qr == -2 ? __int_as_float(0x7fc00000) : km;
+          kv[j] = j < p.v_r ? k : 0.f;
+          kmv[j] = j < p.v_r ? km : 0.f;
         }
         const size_t o = (size_t)w * p.ldk + p.kcol0;
         store_row<N>(static_cast<KT*>(p.K) + o, kv, N < p.VR ? N : p.VR);
@@ -493,8 +565,10 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
   }
 
+  if (warp == 0 && lane == 0) TC_TRACE(4, 0);
   tc_fence_before();
   __syncthreads();
+  if (tid == 0) TC_TRACE(5, 2);
   if (warp == 9) {
     tc_fence_after();
     tmem_dealloc(tmem_base, kCols);
@@ -502,9 +576,9 @@ __global__ void __launch_bounds__(kThreads, 1)
   if (tid == 0 && *abort_flag) atomicCAS(p.err, 0, *abort_flag);
 }
 
-template <int N, int S>
+template <int N, int S, int LS>
 size_t smem_bytes(int KB) {
-  return 1024 + 2 * (size_t)KB * N * 128 + 2 * (size_t)S * kStageBytes + (3 * S + 5) * 8 +
+  return 1024 + 2 * (size_t)KB * N * 128 + (size_t)(S + LS) * kStageBytes + (3 * S + 5) * 8 +
          N * 8 + 16;
 }
 
@@ -523,19 +597,15 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
   return fn;
 }
 
-template <int N, int S, typename KT>
+template <int N, int S, int LS, typename KT>
 cudaError_t launch_t(const wmd_corpus* c, const Params& p, cudaStream_t s) {
-  const size_t bytes = smem_bytes<N, S>(p.KB);
-  static bool attr_set = false;
-  if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(cdist_tc_kernel<N, S, KT>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-    if (e != cudaSuccess) return e;
-    attr_set = true;
-  }
+  const size_t bytes = smem_bytes<N, S, LS>(p.KB);
+  cudaError_t e = cudaFuncSetAttribute(cdist_tc_kernel<N, S, LS, KT>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  if (e != cudaSuccess) return e;
   const int grid = std::max(1, std::min(p.num_tiles, c->num_sms));
   const CUtensorMap* map = reinterpret_cast<const CUtensorMap*>(c->tmap_vecs);
-  cdist_tc_kernel<N, S, KT><<<grid, kThreads, bytes, s>>>(*map, p);
+  cdist_tc_kernel<N, S, LS, KT><<<grid, kThreads, bytes, s>>>(*map, p);
   return cudaGetLastError();
 }
 
@@ -587,15 +657,15 @@ cudaError_t launch_cdist_tc(const wmd_corpus* c, const int32_t* q_ids, const flo
   const bool bf = prec == WMD_PREC_BF16_K;
   const size_t limit = 232448;
   if (VR <= 16) {
-    if (tc::smem_bytes<16, 4>(p.KB) > limit) return cudaErrorNotSupported;
-    return bf ? tc::launch_t<16, 4, __nv_bfloat16>(c, p, s) : tc::launch_t<16, 4, float>(c, p, s);
+    if (tc::smem_bytes<16, 8, 3>(p.KB) > limit) return cudaErrorNotSupported;
+    return bf ? tc::launch_t<16, 8, 3, __nv_bfloat16>(c, p, s) : tc::launch_t<16, 8, 3, float>(c, p, s);
   }
   if (VR <= 32) {
-    if (tc::smem_bytes<32, 4>(p.KB) > limit) return cudaErrorNotSupported;
-    return bf ? tc::launch_t<32, 4, __nv_bfloat16>(c, p, s) : tc::launch_t<32, 4, float>(c, p, s);
+    if (tc::smem_bytes<32, 6, 3>(p.KB) > limit) return cudaErrorNotSupported;
+    return bf ? tc::launch_t<32, 6, 3, __nv_bfloat16>(c, p, s) : tc::launch_t<32, 6, 3, float>(c, p, s);
   }
-  if (tc::smem_bytes<64, 2>(p.KB) > limit) return cudaErrorNotSupported;
-  return bf ? tc::launch_t<64, 2, __nv_bfloat16>(c, p, s) : tc::launch_t<64, 2, float>(c, p, s);
+  if (tc::smem_bytes<64, 3, 1>(p.KB) > limit) return cudaErrorNotSupported;
+  return bf ? tc::launch_t<64, 3, 1, __nv_bfloat16>(c, p, s) : tc::launch_t<64, 3, 1, float>(c, p, s);
 }
 
 }  // namespace wmd
