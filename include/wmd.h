@@ -175,6 +175,28 @@ wmd_status wmd_query_device(wmd_corpus* corpus, const int32_t* d_q_ids,
                             int32_t max_iter, wmd_precision prec, void* d_ws,
                             size_t ws_bytes, double* d_out, void* stream);
 
+/* ---------------------------------------------------------------------------
+ * Device-resident query that allocates nothing (the paper has no counterpart;
+ * this is a service for callers that may not call cudaMalloc, e.g. because
+ * their own memory manager already owns all device memory, or because an
+ * allocation would synchronise the device in a latency-critical thread).
+ *
+ * Same computation, arguments and preconditions as wmd_query_device, without
+ * d_ws: the workspace is a 16 MiB scratch array compiled into the library
+ * (every GPU that loads the library holds it until the process exits).
+ * Queries whose workspace (wmd_workspace_bytes) exceeds 16 MiB are rejected
+ * with WMD_ERR_UNSUPPORTED.  The first call on a device looks up the array's
+ * device address for that device; make that first call before any stream
+ * capture.  All calls share the one array and each call overwrites what it
+ * reads, so calls whose kernels overlap on the GPU (different streams, or
+ * different corpora on the same device) race and must be serialised by the
+ * caller.  Allocates no memory: no cudaMalloc, no cudaFree.
+ * ------------------------------------------------------------------------- */
+wmd_status wmd_query_device_noalloc(wmd_corpus* corpus, const int32_t* d_q_ids,
+                                    const float* d_q_w, int32_t v_r, float lambda,
+                                    int32_t max_iter, wmd_precision prec,
+                                    double* d_out, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -67,6 +67,8 @@ _SIGS = {
     "wmd_sinkhorn_loop": (C.c_int, [_P, C.c_int32, C.c_int32, C.c_int, _P, C.c_size_t, _P, _P]),
     "wmd_query_device": (C.c_int, [_P, _P, _P, C.c_int32, C.c_float, C.c_int32, C.c_int, _P,
                                    C.c_size_t, _P, _P]),
+    "wmd_query_device_noalloc": (C.c_int, [_P, _P, _P, C.c_int32, C.c_float, C.c_int32, C.c_int,
+                                           _P, _P]),
 }
 
 
@@ -204,6 +206,18 @@ class Corpus:
         _check(lib().wmd_query_device(self._h, _dptr(d_ids), _dptr(d_w), int(v_r), float(lam),
                                       int(max_iter), int(prec), _dptr(ws), int(ws_bytes),
                                       _dptr(d_out), _stream_ptr(stream)))
+
+
+def query_device_noalloc(corpus: "Corpus", d_ids, d_w, v_r, lam, max_iter, prec, d_out,
+                         stream=None):
+    """``wmd_query_device_noalloc``: the device path without a workspace.
+
+    For callers that may not allocate device memory: the library's built-in
+    16 MiB scratch array stands in for the workspace.  Calls share that array,
+    so they must not overlap on the GPU."""
+    _check(lib().wmd_query_device_noalloc(corpus.handle, _dptr(d_ids), _dptr(d_w), int(v_r),
+                                          float(lam), int(max_iter), int(prec), _dptr(d_out),
+                                          _stream_ptr(stream)))
 
 
 class DeviceQuery:
