@@ -176,6 +176,75 @@ wmd_status wmd_query_device(wmd_corpus* corpus, const int32_t* d_q_ids,
                             size_t ws_bytes, double* d_out, void* stream);
 
 /* ---------------------------------------------------------------------------
+ * Batched queries (many queries of uneven v_r, one resident corpus).  The
+ * paper computes one query against many documents (Sec. 3); a batch is that
+ * computation for every query, with each query's K block laid out next to the
+ * others' and one fused-loop launch per query-width class covering every
+ * (query, document) pair.  A query's results do not depend on the rest of the
+ * batch (bit-identical to wmd_query).
+ *
+ * nq queries in CSR form: query q is q_ids[q_ptr[q] .. q_ptr[q+1]) with weights
+ * q_w[...] (host; compacted and validated like wmd_compact_query), lambda[q]
+ * its regulariser.  out: host, nq x N doubles, row-major (row q = query q).
+ * Synchronous.  Repeated calls with the same shape (widths, lambdas,
+ * max_iter, precision) replay a captured CUDA graph.  Errors: those of
+ * wmd_query for any query, WMD_ERR_INVALID_ARG for a malformed q_ptr.
+ * ------------------------------------------------------------------------- */
+wmd_status wmd_query_batch(wmd_corpus* corpus, int32_t nq, const int64_t* q_ptr,
+                           const int32_t* q_ids, const float* q_w, const float* lambda,
+                           int32_t max_iter, wmd_precision prec, double* out);
+
+/* ---------------------------------------------------------------------------
+ * Serving: continuous batching over a resident corpus.
+ *
+ * wmd_serve_submit copies and validates one query (host buffers, same rules
+ * as wmd_query) and returns a ticket at once.  A scheduler thread owned by the
+ * server admits waiting requests, oldest first, into batches whenever one of
+ * its `slots` is free (a slot = one CUDA stream with its own buffers), up to
+ * `max_batch` requests and the slot's share of `mem_budget` device bytes
+ * (mem_budget / slots; a request needs 2 U VR sizeof(K) + 8 N bytes).  New
+ * batches start while earlier ones still run on other streams.
+ * wmd_serve_poll waits at most timeout_us for the ticket: WMD_OK (out_wmd,
+ * host, N doubles, filled; the ticket is retired), WMD_ERR_NOT_READY
+ * (timeout_us == 0 and not finished), WMD_ERR_TIMEOUT (timeout_us > 0 ran
+ * out), or the request's own error; WMD_ERR_INVALID_ARG for an unknown ticket.
+ * wmd_serve_cancel retires a ticket (a request already on the GPU finishes
+ * and its result is dropped).  Submit answers WMD_ERR_OUT_OF_MEMORY for a
+ * request larger than one slot's budget, WMD_ERR_NOT_READY when max_pending
+ * requests already wait, WMD_ERR_SHUTDOWN during wmd_server_destroy.
+ * wmd_server_destroy finishes the batches on the GPU, fails the requests
+ * still waiting with WMD_ERR_SHUTDOWN and frees the server (not the corpus).
+ * ------------------------------------------------------------------------- */
+typedef struct wmd_server_options {
+  int32_t max_batch;   /* most requests in one batch (default 64)              */
+  int32_t slots;       /* batches in flight at once (default 2, at most 16)    */
+  size_t mem_budget;   /* device bytes shared by all slots (default 8 GiB)     */
+  int64_t max_pending; /* waiting requests before submit refuses (default 65536) */
+} wmd_server_options;
+
+typedef struct wmd_server_stats {
+  int64_t submitted;
+  int64_t completed;
+  int64_t cancelled;
+  int64_t batches;
+  int64_t max_batch_seen;
+  int64_t pending;
+  int64_t in_flight_batches;
+} wmd_server_stats;
+
+/* opt: NULL for the defaults. */
+wmd_status wmd_server_create(wmd_corpus* corpus, const wmd_server_options* opt,
+                             wmd_server** out);
+wmd_status wmd_serve_submit(wmd_server* server, const int32_t* q_ids, const float* q_w,
+                            int32_t n_q, float lambda, int32_t max_iter,
+                            wmd_precision prec, uint64_t* ticket);
+wmd_status wmd_serve_poll(wmd_server* server, uint64_t ticket, double* out_wmd,
+                          int64_t timeout_us);
+wmd_status wmd_serve_cancel(wmd_server* server, uint64_t ticket);
+wmd_status wmd_server_get_stats(wmd_server* server, wmd_server_stats* out);
+void wmd_server_destroy(wmd_server* server);
+
+/* ---------------------------------------------------------------------------
  * Device-resident query that allocates nothing (the paper has no counterpart;
  * this is a service for callers that may not call cudaMalloc, e.g. because
  * their own memory manager already owns all device memory, or because an

@@ -19,7 +19,7 @@ OBJ = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libwmd_gb300.so")
 ROOT = os.path.dirname(HERE)
 
-SOURCES = ["api.cu", "cdist.cu", "cdist_tc.cu", "sinkhorn.cu", "noalloc.cu"]
+SOURCES = ["api.cu", "cdist.cu", "cdist_tc.cu", "sinkhorn.cu", "serve.cu", "noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          "--expt-relaxed-constexpr", "-I", os.path.join(ROOT, "include")]

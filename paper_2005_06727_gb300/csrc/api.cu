@@ -288,6 +288,7 @@ wmd_status wmd_corpus_load(const float* vecs, int64_t V, int32_t d, const int64_
 
 void wmd_corpus_free(wmd_corpus* c) {
   if (!c) return;
+  release_batch_state(c);
   {
     DeviceGuard g(c->device);
     if (c->stream) cudaStreamSynchronize(c->stream);

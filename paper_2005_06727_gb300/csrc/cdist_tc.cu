@@ -27,6 +27,7 @@
 #include <algorithm>
 #include <cstdlib>
 #include <cstring>
+#include <mutex>
 
 #include "wmd_internal.h"
 
@@ -600,9 +601,20 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
 template <int N, int S, int LS, typename KT>
 cudaError_t launch_t(const wmd_corpus* c, const Params& p, cudaStream_t s) {
   const size_t bytes = smem_bytes<N, S, LS>(p.KB);
-  cudaError_t e = cudaFuncSetAttribute(cdist_tc_kernel<N, S, LS, KT>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-  if (e != cudaSuccess) return e;
+  // the shared-memory limit is raised once per device and size (never inside
+  // a stream capture: the first launch of a shape always runs eagerly)
+  static std::mutex mu;
+  static size_t set_bytes[64] = {};
+  {
+    std::lock_guard<std::mutex> lock(mu);
+    const int dev = c->device < 64 ? c->device : 63;
+    if (set_bytes[dev] < bytes) {
+      cudaError_t e = cudaFuncSetAttribute(cdist_tc_kernel<N, S, LS, KT>,
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+      if (e != cudaSuccess) return e;
+      set_bytes[dev] = bytes;
+    }
+  }
   const int grid = std::max(1, std::min(p.num_tiles, c->num_sms));
   const CUtensorMap* map = reinterpret_cast<const CUtensorMap*>(c->tmap_vecs);
   cdist_tc_kernel<N, S, LS, KT><<<grid, kThreads, bytes, s>>>(*map, p);

@@ -42,6 +42,7 @@ struct LoopParams {
   const int32_t* order;
   double* out;
   const int* err;  // set by a cdist kernel that gave up waiting: results are NaN
+  const QueryDesc* queries;  // blockIdx.y selects the query; NULL: the fields above
 };
 
 // Loads the C columns of K row `row` that lane pi owns, as C/2 float2 pairs.
@@ -92,6 +93,7 @@ struct TeamCtx {
   int lane;
   int pi;
   int pw;
+  QueryDesc q;  // the query this CTA works for
   int rpw_res;  // rows per warp when the document is register resident
   int nch;      // chunks this warp handles
   float* red;   // [2][4][VR] partial x of every warp of the CTA
@@ -117,9 +119,9 @@ __device__ __forceinline__ void solve(const LoopParams& p, const TeamCtx& t) {
 #pragma unroll
   for (int q = 0; q < C2; ++q) {
     const int col = (q >> 1) * 4 * PI + 4 * t.pi + 2 * (q & 1);
-    const bool l0 = col < p.v_r, l1 = col + 1 < p.v_r;
-    rr[q] = make_float2(l0 ? p.r[col] : 0.f, l1 ? p.r[col + 1] : 0.f);
-    u[q] = make_float2(l0 ? (float)p.v_r : 0.f, l1 ? (float)p.v_r : 0.f);
+    const bool l0 = col < t.q.v_r, l1 = col + 1 < t.q.v_r;
+    rr[q] = make_float2(l0 ? t.q.r[col] : 0.f, l1 ? t.q.r[col + 1] : 0.f);
+    u[q] = make_float2(l0 ? (float)t.q.v_r : 0.f, l1 ? (float)t.q.v_r : 0.f);
     const bool seed = t.pw == 0 && t.kw == 0;
     x0[q] = make_float2(l0 || !seed ? 0.f : 1.f, l1 || !seed ? 0.f : 1.f);
   }
@@ -144,7 +146,7 @@ __device__ __forceinline__ void solve(const LoopParams& p, const TeamCtx& t) {
       if (row < len) {
         const int64_t e = t.beg + start + row;
         cw[rI] = p.doc_vals[e];
-        load_krow<KT, C, PI>(Kb, p.doc_words[e], p.ldk, p.kcol0, t.pi, kt[rI]);
+        load_krow<KT, C, PI>(Kb, p.doc_words[e], p.ldk, t.q.kcol0, t.pi, kt[rI]);
       } else {
         // padding row: c = 0 gives v = 0, and K = 1 keeps s > 0 so that
         // c / s needs no guard
@@ -203,7 +205,7 @@ __device__ __forceinline__ void solve(const LoopParams& p, const TeamCtx& t) {
           const int row = rI * PW + t.pw;
           if (row < len) {
             float2 km[C2];
-            load_krow<KT, C, PI>(KMb, p.doc_words[t.beg + start + row], p.ldk, p.kcol0, t.pi, km);
+            load_krow<KT, C, PI>(KMb, p.doc_words[t.beg + start + row], p.ldk, t.q.kcol0, t.pi, km);
             float2 a = make_float2(0.f, 0.f);
 #pragma unroll
             for (int q = 0; q < C2; ++q) a = __ffma2_rn(km[q], u[q], a);
@@ -262,10 +264,10 @@ __device__ __forceinline__ void solve(const LoopParams& p, const TeamCtx& t) {
     if (t.kw == 0 && t.lane == 0) {
       double acc = 0.0;
       for (int k2 = 0; k2 < t.W; ++k2) acc += t.wred[t.team * t.W + k2];
-      p.out[t.doc] = acc;
+      t.q.out[t.doc] = acc;
     }
   } else if (t.lane == 0) {
-    p.out[t.doc] = wsum;
+    t.q.out[t.doc] = wsum;
   }
 }
 
@@ -282,6 +284,14 @@ __global__ void __launch_bounds__(128, MINB) sinkhorn_fused_kernel(LoopParams p)
   __shared__ double wred[4];
 
   TeamCtx t;
+  if (p.queries) {
+    t.q = p.queries[blockIdx.y];
+  } else {
+    t.q.r = p.r;
+    t.q.out = p.out;
+    t.q.kcol0 = p.kcol0;
+    t.q.v_r = p.v_r;
+  }
   t.warp = threadIdx.x >> 5;
   t.lane = threadIdx.x & 31;
   t.pi = t.lane % PI;
@@ -297,12 +307,12 @@ __global__ void __launch_bounds__(128, MINB) sinkhorn_fused_kernel(LoopParams p)
   t.beg = p.doc_ptr[t.doc];
   t.n = (int)(p.doc_ptr[t.doc + 1] - t.beg);
   if (*p.err) {
-    if (t.kw == 0 && t.lane == 0) p.out[t.doc] = __longlong_as_double(0x7ff8000000000000ll);
+    if (t.kw == 0 && t.lane == 0) t.q.out[t.doc] = __longlong_as_double(0x7ff8000000000000ll);
     return;
   }
   if (t.n == 0) {
     if (t.kw == 0 && t.lane == 0)
-      p.out[t.doc] = p.T >= 1 ? __longlong_as_double(0x7ff8000000000000ll) : 0.0;
+      t.q.out[t.doc] = p.T >= 1 ? __longlong_as_double(0x7ff8000000000000ll) : 0.0;
     return;
   }
   t.red = red;
@@ -341,22 +351,23 @@ template <> struct ClassCfg<4> { static constexpr int VR = 128, PI = 8, RMAX = 8
 template <> struct ClassCfg<5> { static constexpr int VR = 256, PI = 16, RMAX = 8, MINB = 2; };
 
 template <int CLS, typename KT>
-cudaError_t launch_cls(const LoopParams& p, int n_items, cudaStream_t s) {
+cudaError_t launch_cls(const LoopParams& p, int n_items, int nq, cudaStream_t s) {
   using Cf = ClassCfg<CLS>;
-  if (n_items == 0) return cudaSuccess;
-  sinkhorn_fused_kernel<Cf::VR, Cf::PI, Cf::RMAX, Cf::MINB, KT><<<n_items, 128, 0, s>>>(p);
+  if (n_items == 0 || nq == 0) return cudaSuccess;
+  dim3 grid((unsigned)n_items, (unsigned)nq);
+  sinkhorn_fused_kernel<Cf::VR, Cf::PI, Cf::RMAX, Cf::MINB, KT><<<grid, 128, 0, s>>>(p);
   return cudaGetLastError();
 }
 
 template <typename KT>
-cudaError_t dispatch_loop(int cls, const LoopParams& p, int n_items, cudaStream_t s) {
+cudaError_t dispatch_loop(int cls, const LoopParams& p, int n_items, int nq, cudaStream_t s) {
   switch (cls) {
-    case 0: return launch_cls<0, KT>(p, n_items, s);
-    case 1: return launch_cls<1, KT>(p, n_items, s);
-    case 2: return launch_cls<2, KT>(p, n_items, s);
-    case 3: return launch_cls<3, KT>(p, n_items, s);
-    case 4: return launch_cls<4, KT>(p, n_items, s);
-    default: return launch_cls<5, KT>(p, n_items, s);
+    case 0: return launch_cls<0, KT>(p, n_items, nq, s);
+    case 1: return launch_cls<1, KT>(p, n_items, nq, s);
+    case 2: return launch_cls<2, KT>(p, n_items, nq, s);
+    case 3: return launch_cls<3, KT>(p, n_items, nq, s);
+    case 4: return launch_cls<4, KT>(p, n_items, nq, s);
+    default: return launch_cls<5, KT>(p, n_items, nq, s);
   }
 }
 
@@ -373,9 +384,8 @@ int rows_per_warp(int cls) {
   }
 }
 
-cudaError_t launch_loop(const wmd_corpus* c, int cls, const void* K, const void* KM, int ldk,
-                        int kcol0, const float* r, int v_r, int T, wmd_precision prec,
-                        double* out, cudaStream_t s) {
+static LoopParams base_params(const wmd_corpus* c, int cls, const void* K, const void* KM,
+                              int ldk, int T) {
   LoopParams p;
   p.doc_ptr = c->doc_ptr;
   p.doc_words = c->doc_words;
@@ -383,16 +393,37 @@ cudaError_t launch_loop(const wmd_corpus* c, int cls, const void* K, const void*
   p.K = K;
   p.KM = KM;
   p.ldk = ldk;
-  p.kcol0 = kcol0;
-  p.r = r;
-  p.v_r = v_r;
+  p.kcol0 = 0;
+  p.r = nullptr;
+  p.v_r = 0;
   p.T = T;
   p.items = c->sched[cls].d_items;
   p.order = c->order;
-  p.out = out;
+  p.out = nullptr;
   p.err = c->d_err;
-  if (prec == WMD_PREC_BF16_K) return dispatch_loop<__nv_bfloat16>(cls, p, c->sched[cls].n_items, s);
-  return dispatch_loop<float>(cls, p, c->sched[cls].n_items, s);
+  p.queries = nullptr;
+  return p;
+}
+
+cudaError_t launch_loop(const wmd_corpus* c, int cls, const void* K, const void* KM, int ldk,
+                        int kcol0, const float* r, int v_r, int T, wmd_precision prec,
+                        double* out, cudaStream_t s) {
+  LoopParams p = base_params(c, cls, K, KM, ldk, T);
+  p.kcol0 = kcol0;
+  p.r = r;
+  p.v_r = v_r;
+  p.out = out;
+  if (prec == WMD_PREC_BF16_K) return dispatch_loop<__nv_bfloat16>(cls, p, c->sched[cls].n_items, 1, s);
+  return dispatch_loop<float>(cls, p, c->sched[cls].n_items, 1, s);
+}
+
+cudaError_t launch_loop_batch(const wmd_corpus* c, int cls, const void* K, const void* KM,
+                              int ldk, const QueryDesc* d_queries, int nq, int T,
+                              wmd_precision prec, cudaStream_t s) {
+  LoopParams p = base_params(c, cls, K, KM, ldk, T);
+  p.queries = d_queries;
+  if (prec == WMD_PREC_BF16_K) return dispatch_loop<__nv_bfloat16>(cls, p, c->sched[cls].n_items, nq, s);
+  return dispatch_loop<float>(cls, p, c->sched[cls].n_items, nq, s);
 }
 
 }  // namespace wmd

@@ -102,6 +102,18 @@ cudaError_t launch_cdist_tc(const wmd_corpus* c, const int32_t* q_ids, const flo
                             int VR, float lambda, wmd_precision prec, void* K, void* KM, int ldk,
                             int kcol0, float* r_out, int* err, cudaStream_t s);
 bool make_vecs_tensor_map(wmd_corpus* c);
+void release_batch_state(const wmd_corpus* c);  // serve.cu: cached batch buffers and graphs
+// One query of a batched loop launch: its padded weights r, output row, first
+// column of its block in the word-major K / K .* M, and its number of words.
+struct QueryDesc {
+  const float* r;
+  double* out;
+  int kcol0;
+  int v_r;
+};
+cudaError_t launch_loop_batch(const wmd_corpus* c, int cls, const void* K, const void* KM,
+                              int ldk, const QueryDesc* d_queries, int nq, int T,
+                              wmd_precision prec, cudaStream_t s);
 cudaError_t launch_loop(const wmd_corpus* c, int cls, const void* K, const void* KM, int ldk,
                         int kcol0, const float* r, int v_r, int T, wmd_precision prec,
                         double* out, cudaStream_t s);

@@ -44,6 +44,17 @@ class WMDError(RuntimeError):
         self.status = status
 
 
+class ServerOptions(C.Structure):
+    _fields_ = [("max_batch", C.c_int32), ("slots", C.c_int32), ("mem_budget", C.c_size_t),
+                ("max_pending", C.c_int64)]
+
+
+class ServerStats(C.Structure):
+    _fields_ = [("submitted", C.c_int64), ("completed", C.c_int64), ("cancelled", C.c_int64),
+                ("batches", C.c_int64), ("max_batch_seen", C.c_int64), ("pending", C.c_int64),
+                ("in_flight_batches", C.c_int64)]
+
+
 class CorpusInfo(C.Structure):
     _fields_ = [("V", C.c_int64), ("d", C.c_int32), ("N", C.c_int64), ("nnz", C.c_int64),
                 ("U", C.c_int64), ("device", C.c_int32), ("device_bytes", C.c_size_t)]
@@ -69,6 +80,13 @@ _SIGS = {
                                    C.c_size_t, _P, _P]),
     "wmd_query_device_noalloc": (C.c_int, [_P, _P, _P, C.c_int32, C.c_float, C.c_int32, C.c_int,
                                            _P, _P]),
+    "wmd_query_batch": (C.c_int, [_P, C.c_int32, _P, _P, _P, _P, C.c_int32, C.c_int, _P]),
+    "wmd_server_create": (C.c_int, [_P, _P, _P]),
+    "wmd_serve_submit": (C.c_int, [_P, _P, _P, C.c_int32, C.c_float, C.c_int32, C.c_int, _P]),
+    "wmd_serve_poll": (C.c_int, [_P, C.c_uint64, _P, C.c_int64]),
+    "wmd_serve_cancel": (C.c_int, [_P, C.c_uint64]),
+    "wmd_server_get_stats": (C.c_int, [_P, _P]),
+    "wmd_server_destroy": (None, [_P]),
 }
 
 
@@ -188,6 +206,23 @@ class Corpus:
                                int(prec), _ptr(out)))
         return out
 
+    def query_batch(self, queries, lam, max_iter: int, prec: int = PREC_FP32) -> np.ndarray:
+        """``wmd_query_batch``: ``queries`` is a list of (ids, weights); ``lam``
+        one value or one per query.  Returns an (nq, N) float64 array."""
+        nq = len(queries)
+        lens = [len(np.atleast_1d(q[0])) for q in queries]
+        q_ptr = np.zeros(nq + 1, np.int64)
+        np.cumsum(lens, out=q_ptr[1:])
+        ids = np.ascontiguousarray(np.concatenate([np.asarray(q[0], np.int32).ravel() for q in queries])
+                                   if nq else np.zeros(0, np.int32), dtype=np.int32)
+        w = np.ascontiguousarray(np.concatenate([np.asarray(q[1], np.float32).ravel() for q in queries])
+                                 if nq else np.zeros(0, np.float32), dtype=np.float32)
+        lams = np.ascontiguousarray(np.broadcast_to(np.asarray(lam, np.float32), (nq,)), np.float32)
+        out = np.empty((nq, self.N), np.float64)
+        _check(lib().wmd_query_batch(self._h, nq, _ptr(q_ptr), _ptr(ids), _ptr(w), _ptr(lams),
+                                     int(max_iter), int(prec), _ptr(out) if out.size else None))
+        return out
+
     # -------------------------------------------------------------- device path
     def workspace_bytes(self, v_r: int, prec: int = PREC_FP32) -> int:
         return int(lib().wmd_workspace_bytes(self._h, int(v_r), int(prec)))
@@ -240,3 +275,49 @@ class DeviceQuery:
         self.corpus.query_device(self.ids, self.w, self.v_r, lam, max_iter, self.prec, self.ws,
                                  self.ws_bytes, self.out, stream)
         return self.out
+
+
+class Server:
+    """``wmd_server``: continuous batching of queries against a corpus."""
+
+    def __init__(self, corpus: Corpus, max_batch: int = 64, slots: int = 2,
+                 mem_budget: int = 8 << 30, max_pending: int = 65536):
+        opt = ServerOptions(int(max_batch), int(slots), int(mem_budget), int(max_pending))
+        h = C.c_void_p()
+        _check(lib().wmd_server_create(corpus.handle, C.byref(opt), C.byref(h)))
+        self._h = h
+        self.corpus = corpus
+
+    def submit(self, q_ids, q_w, lam: float, max_iter: int, prec: int = PREC_FP32) -> int:
+        ids = np.ascontiguousarray(q_ids, dtype=np.int32)
+        w = np.ascontiguousarray(q_w, dtype=np.float32)
+        t = C.c_uint64(0)
+        _check(lib().wmd_serve_submit(self._h, _ptr(ids), _ptr(w), ids.size, float(lam),
+                                      int(max_iter), int(prec), C.byref(t)))
+        return int(t.value)
+
+    def poll(self, ticket: int, timeout_us: int = 0, out: np.ndarray | None = None) -> np.ndarray:
+        if out is None:
+            out = np.empty(self.corpus.N, np.float64)
+        _check(lib().wmd_serve_poll(self._h, C.c_uint64(ticket), _ptr(out) if out.size else None,
+                                    int(timeout_us)))
+        return out
+
+    def cancel(self, ticket: int):
+        _check(lib().wmd_serve_cancel(self._h, C.c_uint64(ticket)))
+
+    def stats(self) -> dict:
+        st = ServerStats()
+        _check(lib().wmd_server_get_stats(self._h, C.byref(st)))
+        return {k: getattr(st, k) for k, _ in ServerStats._fields_}
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().wmd_server_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
