@@ -48,6 +48,9 @@ def parse():
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="paper")
     ap.add_argument("--prec", choices=["fp32", "bf16"], default="fp32")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-systems", action="store_true",
+                    help="skip the batched and served measurements")
+    ap.add_argument("--serve-requests", type=int, default=300)
     return ap.parse_args()
 
 
@@ -194,6 +197,128 @@ def run_reference(args, w):
     }))
 
 
+# ------------------------------------------------------------------ batched and served
+def bench_batched(wmd, device, reps=2):
+    """256 queries of v_r ~ U[5,128] against N=20000 documents: one at a time
+    through wmd_query versus one wmd_query_batch call (graph replayed)."""
+    wb = synth.BATCHED
+    vecs, c, qs = synth.make_workload(wb)
+    corpus = wmd.Corpus.from_synth(vecs, c, device=device)
+    out = np.empty(c.N, np.float64)
+    for q in qs[:4]:
+        corpus.query(q[0], q[1], wb.lam, wb.max_iter, out=out)
+    t0 = time.perf_counter()
+    for q in qs:
+        corpus.query(q[0], q[1], wb.lam, wb.max_iter, out=out)
+    t_single = time.perf_counter() - t0
+    corpus.query_batch(qs, wb.lam, wb.max_iter)  # first call runs eagerly and captures
+    times = []
+    for _ in range(reps):
+        t0 = time.perf_counter()
+        res = corpus.query_batch(qs, wb.lam, wb.max_iter)
+        times.append(time.perf_counter() - t0)
+    t_batch = min(times)
+    assert np.array_equal(res[-1], out), "batched and single results differ"
+    units = len(qs) * c.N
+    corpus.close()
+    return {"workload": (f"{wb.name}: V={wb.V} d={wb.d} N={wb.N} docs of {wb.doc_lo}-{wb.doc_hi} "
+                         f"words, {len(qs)} queries v_r U[{wb.vr_lo},{wb.vr_hi}], lambda={wb.lam:g}, "
+                         f"max_iter={wb.max_iter}"),
+            "one_at_a_time": {"value": units / t_single, "unit": UNIT, "seconds": t_single},
+            "batched": {"value": units / t_batch, "unit": UNIT, "seconds": t_batch,
+                        "path": "wmd_query_batch (captured CUDA graph replay)"},
+            "speedup": t_single / t_batch}
+
+
+def bench_serving(wmd, device, n_requests=300, seed=11):
+    """Poisson arrivals (v_r ~ U[5,200]) against the paper-shaped corpus:
+    latency p50/p99 and throughput of the continuous-batching server at rates
+    below its measured capacity, and the one-query-at-a-time capacity."""
+    import threading as th
+    w = synth.PAPER
+    vecs, c, _ = synth.make_workload(w)
+    corpus = wmd.Corpus.from_synth(vecs, c, device=device)
+    rng = np.random.default_rng(seed)
+    qs = [synth.make_query(w.V, int(rng.integers(5, 201)), 50_000 + i) for i in range(64)]
+    out = np.empty(c.N, np.float64)
+    for q in qs[:4]:
+        corpus.query(q[0], q[1], w.lam, w.max_iter, out=out)
+    t0 = time.perf_counter()
+    for q in qs:
+        corpus.query(q[0], q[1], w.lam, w.max_iter, out=out)
+    single_qps = len(qs) / (time.perf_counter() - t0)
+
+    srv = wmd.Server(corpus, max_batch=32, slots=3, mem_budget=24 << 30)
+    try:
+        # capacity: a closed burst of requests
+        t0 = time.perf_counter()
+        ts = [srv.submit(q[0], q[1], w.lam, w.max_iter) for q in qs * 2]
+        for t in ts:
+            srv.poll(t, timeout_us=60_000_000, out=out)
+        capacity = len(ts) / (time.perf_counter() - t0)
+        rates = []
+        for frac in (0.5, 0.9):
+            rate = frac * capacity
+            arrivals = np.cumsum(rng.exponential(1.0 / rate, n_requests))
+            sub_t, done_t, tickets = {}, {}, []
+            lock = th.Lock()
+            finished = th.Event()
+
+            def submitter():
+                start = time.perf_counter()
+                for k, a in enumerate(arrivals):
+                    delay = start + a - time.perf_counter()
+                    if delay > 0:
+                        time.sleep(delay)
+                    q = qs[k % len(qs)]
+                    tk = srv.submit(q[0], q[1], w.lam, w.max_iter)
+                    with lock:
+                        sub_t[tk] = time.perf_counter()
+                        tickets.append(tk)
+                finished.set()
+
+            th_sub = th.Thread(target=submitter)
+            t_start = time.perf_counter()
+            th_sub.start()
+            pending = []
+            taken = 0
+            buf = np.empty(c.N, np.float64)
+            while True:
+                with lock:
+                    pending.extend(tickets[taken:])
+                    taken = len(tickets)
+                    all_in = finished.is_set() and taken == len(tickets)
+                if all_in and not pending:
+                    break
+                for tk in list(pending):
+                    try:
+                        srv.poll(tk, timeout_us=0, out=buf)
+                    except wmd.WMDError as e:
+                        if e.status == wmd.WMD_ERR_NOT_READY:
+                            continue
+                        raise
+                    done_t[tk] = time.perf_counter()
+                    pending.remove(tk)
+                time.sleep(0.0002)
+            th_sub.join()
+            lat = np.array([done_t[t] - sub_t[t] for t in done_t]) * 1e3
+            rates.append({"offered_qps": rate, "fraction_of_capacity": frac,
+                          "achieved_qps": len(done_t) / (max(done_t.values()) - t_start),
+                          "p50_ms": float(np.percentile(lat, 50)),
+                          "p99_ms": float(np.percentile(lat, 99)),
+                          "requests": len(lat)})
+        stats = srv.stats()
+    finally:
+        srv.close()
+        corpus.close()
+    return {"workload": (f"serving against {w.name} corpus: queries v_r U[5,200], lambda={w.lam:g}, "
+                         f"max_iter={w.max_iter}, Poisson arrivals, {n_requests} requests per rate"),
+            "one_at_a_time_qps": single_qps, "capacity_qps": capacity,
+            "capacity_wmds_per_s": capacity * c.N, "one_at_a_time_wmds_per_s": single_qps * c.N,
+            "rates": rates, "server": {"max_batch": 32, "slots": 3, "batches": stats["batches"],
+                                       "max_batch_seen": stats["max_batch_seen"]}}
+
+
 # ------------------------------------------------------------------ ours
 def run_ours(args, w):
     import torch
@@ -327,6 +452,9 @@ def run_ours(args, w):
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(w, vecs, c, q_ids, q_w)
+    if rank == 0 and not args.no_systems:
+        out["batched"] = bench_batched(wmd, local_rank)
+        out["serving"] = bench_serving(wmd, local_rank, args.serve_requests)
     if rank == 0:
         print(json.dumps(out))
     corpus.close()
