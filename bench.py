@@ -59,6 +59,21 @@ def dist_env():
             int(os.environ.get("WORLD_SIZE", 1)))
 
 
+def replica_throughput(step_ms: float, units_per_rank: int, world: int, group=None):
+    """Whole-job throughput of independent replicas: every rank processed
+    `units_per_rank` units; the job takes as long as the slowest rank.
+    Returns (value, max step ms over ranks)."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(step_ms)], dtype=torch.float64)
+    if world > 1:
+        if dist.get_backend(group) == "nccl":
+            t = t.cuda()
+        dist.all_reduce(t, op=dist.ReduceOp.MAX, group=group)
+    worst = float(t.item())
+    return world * units_per_rank / (worst * 1e-3), worst
+
+
 def workload_name(w):
     return (f"{w.name}: V={w.V} d={w.d} N={w.N} docs of {w.doc_lo}-{w.doc_hi} Zipf(1.1) words, "
             f"v_r={w.vr_lo}, lambda={w.lam:g}, max_iter={w.max_iter}")
@@ -376,11 +391,7 @@ def run_ours(args, w):
     cdist_ms = sum(a.elapsed_time(b) for a, b, _ in ev) / args.steps
     loop_ms = sum(b.elapsed_time(cc) for _, b, cc in ev) / args.steps
     step_ms = sum(a.elapsed_time(cc) for a, _, cc in ev) / args.steps
-    t = torch.tensor([step_ms], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    step_ms_max = float(t.item())
-    value = world * c.N / (step_ms_max * 1e-3)
+    value, step_ms_max = replica_throughput(step_ms, c.N, world)
 
     # end to end through the public host API: pinned query in, WMD[N] out
     h_ids = torch.from_numpy(np.ascontiguousarray(q_ids)).pin_memory()
@@ -397,10 +408,7 @@ def run_ours(args, w):
         corpus.query(ids_np, w_np, w.lam, w.max_iter, prec, out=out_np)
         e2e_t.append(time.perf_counter() - t0)
     e2e_ms = statistics.mean(e2e_t) * 1e3
-    te = torch.tensor([e2e_ms], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(te, op=dist.ReduceOp.MAX)
-    e2e_value = world * c.N / (float(te.item()) * 1e-3)
+    e2e_value, _ = replica_throughput(e2e_ms, c.N, world)
     dev_out = dq.out[: c.N].cpu().numpy()
     assert np.array_equal(dev_out, out_np), "device and host paths disagree"
 
