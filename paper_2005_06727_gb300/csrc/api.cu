@@ -50,6 +50,7 @@ void free_corpus_device(wmd_corpus* c) {
   cudaFree(c->doc_words);
   cudaFree(c->doc_vals);
   cudaFree(c->order);
+  cudaFree(c->slots);
   cudaFree(c->d_err);
   for (auto& s : c->sched) cudaFree(s.d_items);
   cudaFree(c->ws);
@@ -96,12 +97,10 @@ wmd_status cuda_error(cudaError_t e, const char* what) {
 WsLayout ws_layout(const wmd_corpus* c, int VR, wmd_precision prec) {
   WsLayout L;
   size_t o = 0;
-  L.r_off = o;    o = align_up(o + (size_t)VR * sizeof(float), 256);
+  L.r_off = o;    o = align_up(o + (size_t)(VR + 1) * sizeof(float), 256);
   const size_t kelem = prec == WMD_PREC_BF16_K ? 2 : 4;
   const size_t kbytes = align_up((size_t)std::max<int64_t>(c->U, 1) * VR * kelem, 256);
   L.k_off = o;
-  o += kbytes;
-  L.km_off = o;
   o += kbytes;
   L.total = o;
   return L;
@@ -239,6 +238,12 @@ wmd_status wmd_corpus_load(const float* vecs, int64_t V, int32_t d, const int64_
   if (e == cudaSuccess) e = upload(&c->doc_vals, dvals.data(), dvals.size(), &bytes);
   if (e == cudaSuccess) e = upload(&c->order, order.data(), order.size(), &bytes);
   if (e == cudaSuccess) {
+    std::vector<SlotInfo> slots(N);
+    for (int64_t i = 0; i < N; ++i)
+      slots[i] = SlotInfo{dptr[order[i]], (int32_t)(dptr[order[i] + 1] - dptr[order[i]]), order[i]};
+    e = upload(&c->slots, slots.data(), slots.size(), &bytes);
+  }
+  if (e == cudaSuccess) {
     const int zero = 0;
     e = upload(&c->d_err, &zero, 1, &bytes);
   }
@@ -327,8 +332,8 @@ wmd_status wmd_build_kernel_matrix(wmd_corpus* c, const int32_t* d_q_ids, const 
   char* ws = static_cast<char*>(d_ws);
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   float* r = reinterpret_cast<float*>(ws + L.r_off);
-  WMD_CUDA_TRY(launch_cdist(c, d_q_ids, d_q_w, v_r, VR, lambda, prec, ws + L.k_off,
-                            ws + L.km_off, VR, 0, r, s));
+  WMD_CUDA_TRY(launch_cdist(c, d_q_ids, d_q_w, v_r, VR, lambda, prec, ws + L.k_off, VR, 0, r,
+                            r + VR, s));
   return WMD_OK;
 }
 
@@ -344,8 +349,7 @@ wmd_status wmd_sinkhorn_loop(wmd_corpus* c, int32_t v_r, int32_t max_iter, wmd_p
   const WsLayout L = ws_layout(c, VR, prec);
   char* ws = static_cast<char*>(d_ws);
   const float* r = reinterpret_cast<const float*>(ws + L.r_off);
-  WMD_CUDA_TRY(launch_loop(c, cls, ws + L.k_off, ws + L.km_off, VR, 0, r, v_r, max_iter, prec,
-                           d_out,
+  WMD_CUDA_TRY(launch_loop(c, cls, ws + L.k_off, VR, 0, r, r + VR, v_r, max_iter, prec, d_out,
                            static_cast<cudaStream_t>(stream)));
   return WMD_OK;
 }

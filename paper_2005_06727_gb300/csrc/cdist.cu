@@ -7,10 +7,8 @@
 //
 // Output layout is word-major: K[w * ldk + kcol0 + i] for active word row w
 // and query column i (the "on the fly transpose" of Sec. 3: the v_r values a
-// document word needs are contiguous).  The same kernel writes K .* M (the
-// KM matrix of the paper's Python, used by the final reduction) in the same
-// layout.  Columns i >= v_r are written as 0.  A query word equal to the
-// vocabulary word gets M = 0 exactly (K = 1, KM = 0).
+// document word needs are contiguous).  Columns i >= v_r are written as 0.
+// A query word equal to the vocabulary word gets M = 0 exactly (K = 1).
 #include <algorithm>
 
 #include "wmd_internal.h"
@@ -36,8 +34,8 @@ template <int VRB, typename KT>
 __global__ void __launch_bounds__(256) cdist_kernel(
     const float* __restrict__ vecs, int ldv, const float* __restrict__ norms, int64_t U,
     const int32_t* __restrict__ perm, int64_t V, const int32_t* __restrict__ q_ids,
-    const float* __restrict__ q_w, int v_r, int VR, float lambda, KT* __restrict__ K,
-    KT* __restrict__ KM, int ldk, int kcol0, float* __restrict__ r_out) {
+    const float* __restrict__ q_w, int v_r, int VR, float lambda, KT* __restrict__ K, int ldk,
+    int kcol0, float* __restrict__ r_out, float* __restrict__ lam_out) {
   constexpr int TC = VRB / 8;
   constexpr int BStride = VRB + 4;
   __shared__ __align__(16) float As[kSlab][kAStride];
@@ -74,6 +72,7 @@ __global__ void __launch_bounds__(256) cdist_kernel(
   if (r_out && blockIdx.x == 0) {
     for (int i = tid + c0; i < c0 + VRB; i += 256) r_out[i] = i < v_r ? q_w[i] : 0.f;
   }
+  if (lam_out && blockIdx.x == 0 && blockIdx.y == 0 && tid == 0) *lam_out = lambda;
   __syncthreads();
 
   float acc[4][TC];
@@ -178,77 +177,70 @@ __global__ void __launch_bounds__(256) cdist_kernel(
     const int64_t w = w0 + 4 * wg + a;
     if (w >= U) continue;
     const float nw = norms[w];
-    KT outk[TC], outkm[TC];
+    KT outk[TC];
 #pragma unroll
     for (int q = 0; q < TC; ++q) {
       const int col = c0 + TC * cg + q;
-      float kv, kmv;
+      float kv;
       if (col < v_r) {
         if (qrw[q] == (int)w) {
           kv = 1.f;
-          kmv = 0.f;
         } else if (qrw[q] == -2) {
-          kv = kmv = __int_as_float(0x7fc00000);  // id outside [0, V): NaN column
+          kv = __int_as_float(0x7fc00000);  // id outside [0, V): NaN column
         } else {
           const float m2 = (nw + qnv[q]) - 2.f * acc[a][q];
-          const float m = sqrtf(fmaxf(m2, 0.f));
-          kv = expf(-lambda * m);
-          kmv = kv * m;
+          kv = expf(-lambda * sqrtf(fmaxf(m2, 0.f)));
         }
       } else {
-        kv = kmv = 0.f;
+        kv = 0.f;
       }
       outk[q] = to_k<KT>(kv);
-      outkm[q] = to_k<KT>(kmv);
     }
     const size_t o = (size_t)w * ldk + kcol0 + c0 + TC * cg;
 #pragma unroll
-    for (int q = 0; q < TC; ++q) {
-      K[o + q] = outk[q];
-      KM[o + q] = outkm[q];
-    }
+    for (int q = 0; q < TC; ++q) K[o + q] = outk[q];
   }
 }
 
 template <int VRB, typename KT>
 cudaError_t launch_cdist_t(const wmd_corpus* c, const int32_t* q_ids, const float* q_w, int v_r,
-                           int VR, float lambda, KT* K, KT* KM, int ldk, int kcol0, float* r_out,
+                           int VR, float lambda, KT* K, int ldk, int kcol0, float* r_out, float* lam_out,
                            cudaStream_t s) {
   // at least one CTA row so that r_out is written even without active words
   const int64_t tiles = std::max<int64_t>((c->U + kTileW - 1) / kTileW, 1);
   dim3 grid((unsigned)tiles, (unsigned)(VR / VRB));
   cdist_kernel<VRB, KT><<<grid, 256, 0, s>>>(c->vecs, c->ldv, c->norms, c->U, c->perm, c->V,
-                                            q_ids, q_w, v_r, VR, lambda, K, KM, ldk, kcol0, r_out);
+                                            q_ids, q_w, v_r, VR, lambda, K, ldk, kcol0, r_out, lam_out);
   return cudaGetLastError();
 }
 
 template <typename KT>
 cudaError_t dispatch_cdist(const wmd_corpus* c, const int32_t* q_ids, const float* q_w, int v_r,
-                           int VR, float lambda, KT* K, KT* KM, int ldk, int kcol0, float* r_out,
+                           int VR, float lambda, KT* K, int ldk, int kcol0, float* r_out, float* lam_out,
                            cudaStream_t s) {
   switch (VR) {
-    case 8: return launch_cdist_t<8, KT>(c, q_ids, q_w, v_r, VR, lambda, K, KM, ldk, kcol0, r_out, s);
-    case 16: return launch_cdist_t<16, KT>(c, q_ids, q_w, v_r, VR, lambda, K, KM, ldk, kcol0, r_out, s);
-    case 32: return launch_cdist_t<32, KT>(c, q_ids, q_w, v_r, VR, lambda, K, KM, ldk, kcol0, r_out, s);
-    default: return launch_cdist_t<64, KT>(c, q_ids, q_w, v_r, VR, lambda, K, KM, ldk, kcol0, r_out, s);
+    case 8: return launch_cdist_t<8, KT>(c, q_ids, q_w, v_r, VR, lambda, K, ldk, kcol0, r_out, lam_out, s);
+    case 16: return launch_cdist_t<16, KT>(c, q_ids, q_w, v_r, VR, lambda, K, ldk, kcol0, r_out, lam_out, s);
+    case 32: return launch_cdist_t<32, KT>(c, q_ids, q_w, v_r, VR, lambda, K, ldk, kcol0, r_out, lam_out, s);
+    default: return launch_cdist_t<64, KT>(c, q_ids, q_w, v_r, VR, lambda, K, ldk, kcol0, r_out, lam_out, s);
   }
 }
 
 }  // namespace
 
 cudaError_t launch_cdist(const wmd_corpus* c, const int32_t* q_ids, const float* q_w, int v_r,
-                         int VR, float lambda, wmd_precision prec, void* K, void* KM, int ldk,
-                         int kcol0, float* r_out, cudaStream_t s) {
+                         int VR, float lambda, wmd_precision prec, void* K, int ldk, int kcol0,
+                         float* r_out, float* lam_out, cudaStream_t s) {
   // tensor cores (cdist_tc.cu) when the query fits their resident tile
-  cudaError_t e = launch_cdist_tc(c, q_ids, q_w, v_r, VR, lambda, prec, K, KM, ldk, kcol0, r_out,
-                                  c->d_err, s);
+  cudaError_t e = launch_cdist_tc(c, q_ids, q_w, v_r, VR, lambda, prec, K, ldk, kcol0, r_out,
+                                  lam_out, c->d_err, s);
   if (e != cudaErrorNotSupported) return e;
   if (prec == WMD_PREC_BF16_K)
     return dispatch_cdist<__nv_bfloat16>(c, q_ids, q_w, v_r, VR, lambda,
-                                         static_cast<__nv_bfloat16*>(K),
-                                         static_cast<__nv_bfloat16*>(KM), ldk, kcol0, r_out, s);
-  return dispatch_cdist<float>(c, q_ids, q_w, v_r, VR, lambda, static_cast<float*>(K),
-                               static_cast<float*>(KM), ldk, kcol0, r_out, s);
+                                         static_cast<__nv_bfloat16*>(K), ldk, kcol0, r_out,
+                                         lam_out, s);
+  return dispatch_cdist<float>(c, q_ids, q_w, v_r, VR, lambda, static_cast<float*>(K), ldk,
+                               kcol0, r_out, lam_out, s);
 }
 
 }  // namespace wmd

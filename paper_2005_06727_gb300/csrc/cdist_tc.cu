@@ -1,4 +1,4 @@
-// K1 on the 5th-generation tensor cores: cdist + K = exp(-lambda M) + K .* M.
+// K1 on the 5th-generation tensor cores: cdist + K = exp(-lambda M).
 //
 // Sec. 5 of the paper turns the Euclidean distance into a matrix-multiply-like
 // kernel, m^2(i, w) = |e_i|^2 + |e_w|^2 - 2 e_i . e_w, so that the v_r x V
@@ -14,7 +14,7 @@
 //   warp 8        TMA producer: 128 x 32 float32 k-blocks of vecs, 128B-swizzled
 //   warps 4..7    converters: split each landed k-block into hi and lo parts
 //   warp 9        MMA issuer (one thread) and TMEM owner
-//   warps 0..3    epilogue: TMEM -> registers, m, K, K .* M, word-major stores
+//   warps 0..3    epilogue: TMEM -> registers, m, K, word-major stores
 // The query side (B, N x d) is gathered once per CTA into shared memory, split
 // into hi/lo parts and kept resident.  The hi part of A is the landed float32
 // tile itself (the tensor core reads the tf32 bits of each operand).  Accumulators are double buffered in
@@ -53,10 +53,10 @@ struct Params {
   int VR;
   float lambda;
   void* K;
-  void* KM;
   int ldk;
   int kcol0;
   float* r_out;
+  float* lam_out;
   int num_tiles;
   int KB;
   int* err;
@@ -345,6 +345,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       qrow_s[bt] = row;
     }
     if (p.r_out && blockIdx.x == 0 && bt < p.VR) p.r_out[bt] = bt < p.v_r ? p.q_w[bt] : 0.f;
+    if (p.lam_out && blockIdx.x == 0 && bt == 0) *p.lam_out = p.lambda;
     asm volatile("bar.sync 1, %0;" ::"r"(kBT) : "memory");
     const int total = N * KB * 8;
     for (int base = bt; base < total; base += kBT * 12) {
@@ -542,26 +543,18 @@ __global__ void __launch_bounds__(kThreads, 1)
       mbar_arrive(&tempty[ab]);
 
       if (w < p.U) {
-        // m^2 = |a|^2 + |b|^2 - 2 a.b (clamped), K = exp(-lambda m), K .* M;
-        // the query's own word is exactly m = 0; padding columns are 0 and an
-        // id outside [0, V) gives NaN
-        float kv[N], kmv[N];
+        // m^2 = |a|^2 + |b|^2 - 2 a.b (clamped), K = exp(-lambda m); the
+        // query's own word is exactly m = 0 (K = 1); padding columns are 0 and
+        // an id outside [0, V) gives NaN
+        float kv[N];
 #pragma unroll
         for (int j = 0; j < N; ++j) {
-          const float m = sqrtf(fmaxf((nw + qn_s[j]) - 2.f * acc[j], 0.f));
-          const float e = expf(-p.lambda * m);
+          const float e = expf(-p.lambda * sqrtf(fmaxf((nw + qn_s[j]) - 2.f * acc[j], 0.f)));
           const int qr = qrow_s[j];
-          const bool own = qr == (int)w;
-          float k = own ? 1.f : e;
-          float km = own ? 0.f : e * m;
-          k = qr == -2 ? __int_as_float(0x7fc00000) : k;
-          km = qr == -2 ? __int_as_float(0x7fc00000) : km;
+          const float k = qr == (int)w ? 1.f : (qr == -2 ? __int_as_float(0x7fc00000) : e);
           kv[j] = j < p.v_r ? k : 0.f;
-          kmv[j] = j < p.v_r ? km : 0.f;
         }
-        const size_t o = (size_t)w * p.ldk + p.kcol0;
-        store_row<N>(static_cast<KT*>(p.K) + o, kv, N < p.VR ? N : p.VR);
-        store_row<N>(static_cast<KT*>(p.KM) + o, kmv, N < p.VR ? N : p.VR);
+        store_row<N>(static_cast<KT*>(p.K) + (size_t)w * p.ldk + p.kcol0, kv, N < p.VR ? N : p.VR);
       }
     }
   }
@@ -643,8 +636,8 @@ bool make_vecs_tensor_map(wmd_corpus* c) {
 // Tensor-core path when the query fits one N <= 64 tile and B stays resident
 // in shared memory; returns cudaErrorNotSupported otherwise.
 cudaError_t launch_cdist_tc(const wmd_corpus* c, const int32_t* q_ids, const float* q_w, int v_r,
-                            int VR, float lambda, wmd_precision prec, void* K, void* KM, int ldk,
-                            int kcol0, float* r_out, int* err, cudaStream_t s) {
+                            int VR, float lambda, wmd_precision prec, void* K, int ldk, int kcol0,
+                            float* r_out, float* lam_out, int* err, cudaStream_t s) {
   if (!c->tmap_ok || VR > 64 || c->U == 0) return cudaErrorNotSupported;
   tc::Params p;
   p.vecs = c->vecs;
@@ -659,10 +652,10 @@ cudaError_t launch_cdist_tc(const wmd_corpus* c, const int32_t* q_ids, const flo
   p.VR = VR;
   p.lambda = lambda;
   p.K = K;
-  p.KM = KM;
   p.ldk = ldk;
   p.kcol0 = kcol0;
   p.r_out = r_out;
+  p.lam_out = lam_out;
   p.num_tiles = (int)((c->U + tc::kM - 1) / tc::kM);
   p.KB = (c->ldv + tc::kKB - 1) / tc::kKB;
   p.err = err;

@@ -18,8 +18,8 @@
 
 namespace {
 
-// 16 MiB: enough for K and K .* M of a 30-word query against ~65,000 active
-// vocabulary words in float32 (the paper-shaped corpus has 53,151).
+// 16 MiB: enough for K of a 30-word query against ~130,000 active vocabulary
+// words in float32 (the paper-shaped corpus has 53,151).
 constexpr size_t kWmdScratchBytes = size_t(16) << 20;
 
 __device__ __align__(256) unsigned char g_wmd_scratch[kWmdScratchBytes];
@@ -60,7 +60,7 @@ extern "C" wmd_status wmd_query_device_noalloc(wmd_corpus* corpus, const int32_t
       g_scratch_ptr[corpus->device] = scratch;
     }
   }
-  // The kernels overwrite every byte of the scratch they read (r, K, K .* M),
+  // The kernels overwrite every byte of the scratch they read (r, lambda, K),
   // so nothing has to be cleared between calls.
   return wmd_query_device(corpus, d_q_ids, d_q_w, v_r, lambda, max_iter, prec, scratch,
                           kWmdScratchBytes, d_out, stream);

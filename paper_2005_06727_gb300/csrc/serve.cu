@@ -2,7 +2,7 @@
 // corpus (the paper answers one query at a time, Sec. 3 and Sec. 4; running
 // several is the same computation repeated per query).
 //
-// A batch lays every query's block of K and K .* M side by side in one
+// A batch lays every query's block of K side by side in one
 // word-major matrix (row w holds the VR_q columns of query q at offset col0_q),
 // runs one cdist launch per query (tensor cores where they apply) and then ONE
 // fused-loop launch per query-width class that covers every (query, document)
@@ -60,9 +60,9 @@ struct Req {
 
 size_t k_elem(wmd_precision prec) { return prec == WMD_PREC_BF16_K ? 2 : 4; }
 
-// Device bytes one query adds to a batch (its K and K .* M columns, r, output).
+// Device bytes one query adds to a batch (its K columns, r, output).
 size_t request_bytes(const wmd_corpus* c, int VR, wmd_precision prec) {
-  return 2 * (size_t)std::max<int64_t>(c->U, 1) * VR * k_elem(prec) + VR * 4 +
+  return (size_t)std::max<int64_t>(c->U, 1) * VR * k_elem(prec) + VR * 4 +
          (size_t)std::max<int64_t>(c->N, 1) * 8 + 64;
 }
 
@@ -75,7 +75,7 @@ struct Slot {
   size_t ids_cap = 0, w_cap = 0;
   QueryDesc* d_desc = nullptr;
   size_t desc_cap = 0;
-  char* d_ws = nullptr;  // r_all | K_all | KM_all
+  char* d_ws = nullptr;  // r_all | K_all
   size_t ws_cap = 0;
   double* d_out = nullptr;
   size_t out_cap = 0;
@@ -129,7 +129,7 @@ struct Layout {
   std::vector<int> col0;
   int ldk = 0;
   size_t words = 0;
-  size_t r_off = 0, k_off = 0, km_off = 0, ws_bytes = 0;
+  size_t r_off = 0, k_off = 0, ws_bytes = 0;
   std::vector<int> desc_of;        // query -> index in the descriptor table
   int cls_begin[kNumClasses + 1];  // descriptor ranges per class
 };
@@ -147,8 +147,7 @@ Layout plan(const wmd_corpus* c, const std::vector<const Req*>& qs, wmd_precisio
   L.r_off = 0;
   L.k_off = round_up((size_t)L.ldk * 4, 256);
   const size_t kb = round_up((size_t)std::max<int64_t>(c->U, 1) * L.ldk * k_elem(prec), 256);
-  L.km_off = L.k_off + kb;
-  L.ws_bytes = L.km_off + kb;
+  L.ws_bytes = L.k_off + kb;
   // descriptors grouped by width class
   L.desc_of.assign(qs.size(), 0);
   int n = 0;
@@ -195,6 +194,7 @@ wmd_status enqueue_batch(wmd_corpus* c, Slot& s, const std::vector<const Req*>& 
     d.out = s.d_out + q * N1;
     d.kcol0 = L.col0[q];
     d.v_r = qs[q]->v_r;
+    d.lambda = qs[q]->lambda;
   }
   cudaStream_t st = s.stream;
   WMD_CUDA_TRY(cudaMemcpyAsync(s.d_ids, s.h_ids, L.words * sizeof(int32_t), cudaMemcpyHostToDevice, st));
@@ -202,13 +202,13 @@ wmd_status enqueue_batch(wmd_corpus* c, Slot& s, const std::vector<const Req*>& 
   WMD_CUDA_TRY(cudaMemcpyAsync(s.d_desc, s.h_desc, nq * sizeof(QueryDesc), cudaMemcpyHostToDevice, st));
   for (size_t q = 0; q < nq; ++q)
     WMD_CUDA_TRY(launch_cdist(c, s.d_ids + word_off[q], s.d_w + word_off[q], qs[q]->v_r, qs[q]->VR,
-                              qs[q]->lambda, prec, ws + L.k_off, ws + L.km_off, L.ldk, L.col0[q],
-                              r_all + L.col0[q], st));
+                              qs[q]->lambda, prec, ws + L.k_off, L.ldk, L.col0[q],
+                              r_all + L.col0[q], nullptr, st));
   for (int cls = 0; cls < kNumClasses; ++cls) {
     const int n = L.cls_begin[cls + 1] - L.cls_begin[cls];
     if (n)
-      WMD_CUDA_TRY(launch_loop_batch(c, cls, ws + L.k_off, ws + L.km_off, L.ldk,
-                                     s.d_desc + L.cls_begin[cls], n, T, prec, st));
+      WMD_CUDA_TRY(launch_loop_batch(c, cls, ws + L.k_off, L.ldk, s.d_desc + L.cls_begin[cls], n, T,
+                                     prec, st));
   }
   if (c->N > 0)
     WMD_CUDA_TRY(cudaMemcpyAsync(s.h_out, s.d_out, nq * N1 * sizeof(double), cudaMemcpyDeviceToHost, st));

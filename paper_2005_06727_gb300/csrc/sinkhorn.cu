@@ -20,8 +20,11 @@
 // Column j of lane pi is c(j) = (j / 4) * 4 PI + 4 pi + j % 4, so one float4
 // load per 4 columns reads 16 PI contiguous bytes per row group.
 //
-// The final step reads K .* M (written next to K by the cdist kernel) for the
-// document's words once.
+// K .* M for the final step is recovered from the K block already in
+// registers: M = -ln(K) / lambda, exact for K = 1 (the query's own word) and
+// within a few float32 ulps of m while K is a normal float (the cdist kernel
+// computed K = exp(-lambda m) in float32, so -ln K returns lambda m up to the
+// rounding of that product and of expf).
 #include "wmd_internal.h"
 
 namespace wmd {
@@ -32,14 +35,14 @@ struct LoopParams {
   const int32_t* doc_words;
   const float* doc_vals;
   const void* K;
-  const void* KM;
   int ldk;
   int kcol0;
   const float* r;
+  const float* lam;  // lambda of the single query (written by the cdist kernel)
   int v_r;
   int T;
   const LoopItem* items;
-  const int32_t* order;
+  const SlotInfo* slots;
   double* out;
   const int* err;  // set by a cdist kernel that gave up waiting: results are NaN
   const QueryDesc* queries;  // blockIdx.y selects the query; NULL: the fields above
@@ -74,6 +77,12 @@ __device__ __forceinline__ void team_barrier(int id, int nthreads) {
   asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
 }
 
+// K[w,i] (-ln K[w,i]) = lambda K[w,i] M[w,i]; 0 where K underflowed to a
+// subnormal or zero.
+__device__ __forceinline__ float k_times_neg_logk(float k) {
+  return k >= 1.17549435e-38f ? -k * __logf(k) : 0.f;
+}
+
 // Hardware reciprocal (PTX rcp.approx, about 1 ulp); operands here are never
 // zero: padding rows and columns are seeded so that their sums stay positive.
 __device__ __forceinline__ float fast_rcp(float x) {
@@ -93,7 +102,7 @@ struct TeamCtx {
   int lane;
   int pi;
   int pw;
-  QueryDesc q;  // the query this CTA works for
+  QueryDesc q;  // the query this CTA works for (q.lambda resolved)
   int rpw_res;  // rows per warp when the document is register resident
   int nch;      // chunks this warp handles
   float* red;   // [2][4][VR] partial x of every warp of the CTA
@@ -110,20 +119,20 @@ __device__ __forceinline__ void solve(const LoopParams& p, const TeamCtx& t) {
   constexpr int C2 = C / 2;
   constexpr int PW = 32 / PI;
   const KT* Kb = static_cast<const KT*>(p.K);
-  const KT* KMb = static_cast<const KT*>(p.KM);
 
-  // query weights and the initial u = 1 / x = v_r for my columns; x0 seeds
-  // the SpMM sums of padding columns with 1 so that 1/x stays finite there
-  // (their r is 0, so u = r / x = 0 and K = 0 keeps them out of every sum)
-  float2 rr[C2], u[C2], x0[C2];
+  // query weights and the initial u = 1 / x = v_r for my columns; one lane
+  // per column seeds the SpMM sums of padding columns with 1 so that 1/x stays
+  // finite there (their r is 0, so u = r / x = 0, and K = 0 keeps them out of
+  // every sum); bit 2q+h of `seed` marks those columns
+  float2 rr[C2], u[C2];
+  uint32_t seed = 0;
 #pragma unroll
   for (int q = 0; q < C2; ++q) {
     const int col = (q >> 1) * 4 * PI + 4 * t.pi + 2 * (q & 1);
     const bool l0 = col < t.q.v_r, l1 = col + 1 < t.q.v_r;
     rr[q] = make_float2(l0 ? t.q.r[col] : 0.f, l1 ? t.q.r[col + 1] : 0.f);
     u[q] = make_float2(l0 ? (float)t.q.v_r : 0.f, l1 ? (float)t.q.v_r : 0.f);
-    const bool seed = t.pw == 0 && t.kw == 0;
-    x0[q] = make_float2(l0 || !seed ? 0.f : 1.f, l1 || !seed ? 0.f : 1.f);
+    if (t.pw == 0 && t.kw == 0) seed |= (l0 ? 0u : 1u) << (2 * q) | (l1 ? 0u : 1u) << (2 * q + 1);
   }
 
   float2 kt[R][C2];
@@ -164,7 +173,8 @@ __device__ __forceinline__ void solve(const LoopParams& p, const TeamCtx& t) {
     const bool last = it == p.T;
     float2 xp[C2];
 #pragma unroll
-    for (int q = 0; q < C2; ++q) xp[q] = x0[q];
+    for (int q = 0; q < C2; ++q)
+      xp[q] = make_float2((seed >> (2 * q)) & 1u ? 1.f : 0.f, (seed >> (2 * q + 1)) & 1u ? 1.f : 0.f);
 
     for (int m = 0; m < t.nch; ++m) {
       if (RELOAD) load_chunk(m);
@@ -196,21 +206,18 @@ __device__ __forceinline__ void solve(const LoopParams& p, const TeamCtx& t) {
           for (int q = 0; q < C2; ++q) xp[q] = __ffma2_rn(kt[rI][q], vv, xp[q]);
         }
       } else {
-        // final reduction: sum_w v_w sum_i u_i (K .* M)[w, i]; a lane's few
-        // terms are summed in float32, lanes and warps in float64
-        int start, len;
-        chunk(m, start, len);
+        // final reduction: sum_w v_w sum_i u_i K[w, i] (-ln K[w, i]) (= lambda
+        // times the WMD); a lane's few terms are summed in float32, lanes and
+        // warps in float64
 #pragma unroll
         for (int rI = 0; rI < R; ++rI) {
-          const int row = rI * PW + t.pw;
-          if (row < len) {
-            float2 km[C2];
-            load_krow<KT, C, PI>(KMb, p.doc_words[t.beg + start + row], p.ldk, t.q.kcol0, t.pi, km);
-            float2 a = make_float2(0.f, 0.f);
+          float tt = 0.f;
 #pragma unroll
-            for (int q = 0; q < C2; ++q) a = __ffma2_rn(km[q], u[q], a);
-            wacc = fmaf(v[rI], a.x + a.y, wacc);
+          for (int q = 0; q < C2; ++q) {
+            tt = fmaf(u[q].x, k_times_neg_logk(kt[rI][q].x), tt);
+            tt = fmaf(u[q].y, k_times_neg_logk(kt[rI][q].y), tt);
           }
+          wacc = fmaf(v[rI], tt, wacc);
         }
       }
     }
@@ -264,10 +271,10 @@ __device__ __forceinline__ void solve(const LoopParams& p, const TeamCtx& t) {
     if (t.kw == 0 && t.lane == 0) {
       double acc = 0.0;
       for (int k2 = 0; k2 < t.W; ++k2) acc += t.wred[t.team * t.W + k2];
-      t.q.out[t.doc] = acc;
+      t.q.out[t.doc] = acc / (double)t.q.lambda;
     }
   } else if (t.lane == 0) {
-    t.q.out[t.doc] = wsum;
+    t.q.out[t.doc] = wsum / (double)t.q.lambda;
   }
 }
 
@@ -291,6 +298,7 @@ __global__ void __launch_bounds__(128, MINB) sinkhorn_fused_kernel(LoopParams p)
     t.q.out = p.out;
     t.q.kcol0 = p.kcol0;
     t.q.v_r = p.v_r;
+    t.q.lambda = *p.lam;
   }
   t.warp = threadIdx.x >> 5;
   t.lane = threadIdx.x & 31;
@@ -303,9 +311,10 @@ __global__ void __launch_bounds__(128, MINB) sinkhorn_fused_kernel(LoopParams p)
   const int slot = item.begin + t.team;
   if (t.team >= 4 / t.W || slot >= item.end) return;  // whole team leaves together
 
-  t.doc = p.order[slot];
-  t.beg = p.doc_ptr[t.doc];
-  t.n = (int)(p.doc_ptr[t.doc + 1] - t.beg);
+  const SlotInfo si = p.slots[slot];
+  t.doc = si.doc;
+  t.beg = si.beg;
+  t.n = si.n;
   if (*p.err) {
     if (t.kw == 0 && t.lane == 0) t.q.out[t.doc] = __longlong_as_double(0x7ff8000000000000ll);
     return;
@@ -384,43 +393,43 @@ int rows_per_warp(int cls) {
   }
 }
 
-static LoopParams base_params(const wmd_corpus* c, int cls, const void* K, const void* KM,
-                              int ldk, int T) {
+static LoopParams base_params(const wmd_corpus* c, int cls, const void* K, int ldk, int T) {
   LoopParams p;
   p.doc_ptr = c->doc_ptr;
   p.doc_words = c->doc_words;
   p.doc_vals = c->doc_vals;
   p.K = K;
-  p.KM = KM;
   p.ldk = ldk;
   p.kcol0 = 0;
   p.r = nullptr;
+  p.lam = nullptr;
   p.v_r = 0;
   p.T = T;
   p.items = c->sched[cls].d_items;
-  p.order = c->order;
+  p.slots = c->slots;
   p.out = nullptr;
   p.err = c->d_err;
   p.queries = nullptr;
   return p;
 }
 
-cudaError_t launch_loop(const wmd_corpus* c, int cls, const void* K, const void* KM, int ldk,
-                        int kcol0, const float* r, int v_r, int T, wmd_precision prec,
+cudaError_t launch_loop(const wmd_corpus* c, int cls, const void* K, int ldk, int kcol0,
+                        const float* r, const float* lam, int v_r, int T, wmd_precision prec,
                         double* out, cudaStream_t s) {
-  LoopParams p = base_params(c, cls, K, KM, ldk, T);
+  LoopParams p = base_params(c, cls, K, ldk, T);
   p.kcol0 = kcol0;
   p.r = r;
+  p.lam = lam;
   p.v_r = v_r;
   p.out = out;
   if (prec == WMD_PREC_BF16_K) return dispatch_loop<__nv_bfloat16>(cls, p, c->sched[cls].n_items, 1, s);
   return dispatch_loop<float>(cls, p, c->sched[cls].n_items, 1, s);
 }
 
-cudaError_t launch_loop_batch(const wmd_corpus* c, int cls, const void* K, const void* KM,
-                              int ldk, const QueryDesc* d_queries, int nq, int T,
-                              wmd_precision prec, cudaStream_t s) {
-  LoopParams p = base_params(c, cls, K, KM, ldk, T);
+cudaError_t launch_loop_batch(const wmd_corpus* c, int cls, const void* K, int ldk,
+                              const QueryDesc* d_queries, int nq, int T, wmd_precision prec,
+                              cudaStream_t s) {
+  LoopParams p = base_params(c, cls, K, ldk, T);
   p.queries = d_queries;
   if (prec == WMD_PREC_BF16_K) return dispatch_loop<__nv_bfloat16>(cls, p, c->sched[cls].n_items, nq, s);
   return dispatch_loop<float>(cls, p, c->sched[cls].n_items, nq, s);

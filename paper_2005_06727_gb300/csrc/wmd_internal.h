@@ -48,6 +48,14 @@ struct LoopItem {
   int32_t pad;
 };
 
+// Where one slot of the length-sorted document order lives in the
+// document-major CSR (one 16-byte load at team start).
+struct SlotInfo {
+  int64_t beg;
+  int32_t n;
+  int32_t doc;
+};
+
 struct Schedule {
   LoopItem* d_items = nullptr;
   int32_t n_items = 0;
@@ -68,6 +76,7 @@ struct wmd_corpus {
   int32_t* doc_words = nullptr;// nnz, device rows (< U) sorted within a doc
   float* doc_vals = nullptr;   // nnz
   int32_t* order = nullptr;    // N, documents by decreasing length
+  wmd::SlotInfo* slots = nullptr;  // N, {beg, n, doc} of order[i]
   wmd::Schedule sched[wmd::kNumClasses];
   size_t device_bytes = 0;
   int num_sms = 0;
@@ -88,19 +97,19 @@ struct wmd_corpus {
 namespace wmd {
 
 // Workspace carve-up for one query of class VR: the padded query weights r
-// (VR floats) and the word-major K and K .* M (U x VR each).
+// (VR floats) followed by lambda, and the word-major K (U x VR).
 struct WsLayout {
-  size_t r_off, k_off, km_off, total;
+  size_t r_off, k_off, total;
 };
 WsLayout ws_layout(const wmd_corpus* c, int VR, wmd_precision prec);
 
 // Kernel launchers (cdist.cu / sinkhorn.cu).
 cudaError_t launch_cdist(const wmd_corpus* c, const int32_t* q_ids, const float* q_w, int v_r,
-                         int VR, float lambda, wmd_precision prec, void* K, void* KM, int ldk,
-                         int kcol0, float* r_out, cudaStream_t s);
+                         int VR, float lambda, wmd_precision prec, void* K, int ldk, int kcol0,
+                         float* r_out, float* lam_out, cudaStream_t s);
 cudaError_t launch_cdist_tc(const wmd_corpus* c, const int32_t* q_ids, const float* q_w, int v_r,
-                            int VR, float lambda, wmd_precision prec, void* K, void* KM, int ldk,
-                            int kcol0, float* r_out, int* err, cudaStream_t s);
+                            int VR, float lambda, wmd_precision prec, void* K, int ldk, int kcol0,
+                            float* r_out, float* lam_out, int* err, cudaStream_t s);
 bool make_vecs_tensor_map(wmd_corpus* c);
 void release_batch_state(const wmd_corpus* c);  // serve.cu: cached batch buffers and graphs
 // One query of a batched loop launch: its padded weights r, output row, first
@@ -110,12 +119,13 @@ struct QueryDesc {
   double* out;
   int kcol0;
   int v_r;
+  float lambda;
 };
-cudaError_t launch_loop_batch(const wmd_corpus* c, int cls, const void* K, const void* KM,
-                              int ldk, const QueryDesc* d_queries, int nq, int T,
-                              wmd_precision prec, cudaStream_t s);
-cudaError_t launch_loop(const wmd_corpus* c, int cls, const void* K, const void* KM, int ldk,
-                        int kcol0, const float* r, int v_r, int T, wmd_precision prec,
+cudaError_t launch_loop_batch(const wmd_corpus* c, int cls, const void* K, int ldk,
+                              const QueryDesc* d_queries, int nq, int T, wmd_precision prec,
+                              cudaStream_t s);
+cudaError_t launch_loop(const wmd_corpus* c, int cls, const void* K, int ldk, int kcol0,
+                        const float* r, const float* lam, int v_r, int T, wmd_precision prec,
                         double* out, cudaStream_t s);
 
 }  // namespace wmd

@@ -255,25 +255,25 @@ def _active_words(c):
 
 
 def _workspace_k(wmd, corpus, dq, VR, prec):
-    """K and K .* M (U x VR) read back from the workspace after the cdist stage."""
+    """Padded weights r, lambda and K (U x VR) read back from the workspace
+    after the cdist stage."""
     import torch
     U = corpus.U
     esz = 2 if prec == wmd.PREC_BF16_K else 4
-    k_off = 256 if VR * 4 <= 256 else (VR * 4 + 255) // 256 * 256
-    kbytes = (U * VR * esz + 255) // 256 * 256
+    k_off = ((VR + 1) * 4 + 255) // 256 * 256
     raw = dq.ws.cpu()
+    r_lam = raw[: (VR + 1) * 4].view(torch.float32).numpy()
     dt = torch.bfloat16 if esz == 2 else torch.float32
     K = raw[k_off:k_off + U * VR * esz].view(dt).float().numpy().reshape(U, VR)
-    KM = raw[k_off + kbytes:k_off + kbytes + U * VR * esz].view(dt).float().numpy().reshape(U, VR)
-    return K, KM
+    return r_lam[:VR], float(r_lam[VR]), K
 
 
 @pytest.mark.parametrize("kernel", ["tc", "simt"])
 @pytest.mark.parametrize("v_r", [5, 16, 30, 64, 100])
 def test_cdist_kernel_matrix_elementwise(wmd, monkeypatch, kernel, v_r):
-    """K = exp(-lambda M) and K .* M against the oracle's FP64 distances, for
-    the tensor-core (3xTF32) and the CUDA-core kernel; the query's own words
-    give K = 1 and K .* M = 0 exactly."""
+    """K = exp(-lambda M) against the oracle's FP64 distances, for the
+    tensor-core (3xTF32) and the CUDA-core kernel; the query's own words give
+    K = 1 exactly; padding columns are 0; r and lambda land next to K."""
     import torch
     if kernel == "simt":
         monkeypatch.setenv("WMD_CDIST_KERNEL", "simt")
@@ -295,16 +295,18 @@ def test_cdist_kernel_matrix_elementwise(wmd, monkeypatch, kernel, v_r):
         VR = 8
         while VR < v_r:
             VR *= 2
-        K, KM = _workspace_k(wmd, corpus, dq, VR, prec)
+        r, lam_ws, K = _workspace_k(wmd, corpus, dq, VR, prec)
+        assert lam_ws == np.float32(lam)
+        np.testing.assert_array_equal(r[:v_r], dq.w.cpu().numpy())
+        assert np.all(r[v_r:] == 0)
         words = _active_words(c)
         M = orc.cdist(vecs, q_ids, words).T                    # U x v_r
         Kw = np.exp(-lam * M)
         np.testing.assert_allclose(K[:, :v_r], Kw, rtol=rtol, atol=0)
-        np.testing.assert_allclose(KM[:, :v_r], Kw * M, rtol=rtol, atol=1e-30)
-        assert np.all(K[:, v_r:] == 0) and np.all(KM[:, v_r:] == 0)
+        assert np.all(K[:, v_r:] == 0)
         own = np.isin(words, q_ids)
         rows, cols = np.nonzero(words[:, None] == q_ids[None, :])
-        assert np.all(K[rows, cols] == 1.0) and np.all(KM[rows, cols] == 0.0)
+        assert np.all(K[rows, cols] == 1.0)
         assert own.sum() == len(rows)
 
 

@@ -56,12 +56,12 @@ def test_noalloc_entry_point_matches_workspace_entry_point():
             assert np.all(np.isfinite(out.cpu().numpy()))
 
     # more scratch than the built-in array holds is refused, not truncated
-    big_ids, big_w = synth.make_query(w.V, 64, 77)
+    big_ids, big_w = synth.make_query(w.V, 128, 77)
     ids = torch.from_numpy(big_ids).to(dev)
     wts = torch.from_numpy(big_w).to(dev)
-    assert corpus.workspace_bytes(64) > 16 << 20
+    assert corpus.workspace_bytes(128) > 16 << 20
     out = torch.empty(c.N, dtype=torch.float64, device=dev)
     with pytest.raises(wmd.WMDError) as e:
-        wmd.query_device_noalloc(corpus, ids, wts, 64, w.lam, w.max_iter, wmd.PREC_FP32, out)
+        wmd.query_device_noalloc(corpus, ids, wts, 128, w.lam, w.max_iter, wmd.PREC_FP32, out)
     assert e.value.status == wmd.WMD_ERR_UNSUPPORTED
     corpus.close()
