@@ -217,6 +217,10 @@ def bench_batched(wmd, device, reps=2):
     wb = synth.BATCHED
     vecs, c, qs = synth.make_workload(wb)
     corpus = wmd.Corpus.from_synth(vecs, c, device=device)
+    for vr in (8, 16, 32, 64, 128):  # autotune every width class the batch uses
+        q = next((q for q in qs if (len(q[0]) <= vr and len(q[0]) > vr // 2)), None)
+        if q is not None:
+            corpus.autotune(q[0], q[1], wb.lam, wb.max_iter)
     out = np.empty(c.N, np.float64)
     for q in qs[:4]:
         corpus.query(q[0], q[1], wb.lam, wb.max_iter, out=out)
@@ -253,6 +257,10 @@ def bench_serving(wmd, device, n_requests=300, seed=11):
     corpus = wmd.Corpus.from_synth(vecs, c, device=device)
     rng = np.random.default_rng(seed)
     qs = [synth.make_query(w.V, int(rng.integers(5, 201)), 50_000 + i) for i in range(64)]
+    for vr in (8, 16, 32, 64, 128, 256):
+        q = next((q for q in qs if (len(q[0]) <= vr and len(q[0]) > vr // 2)), None)
+        if q is not None:
+            corpus.autotune(q[0], q[1], w.lam, w.max_iter)
     out = np.empty(c.N, np.float64)
     for q in qs[:4]:
         corpus.query(q[0], q[1], w.lam, w.max_iter, out=out)
@@ -351,6 +359,8 @@ def run_ours(args, w):
     vecs, c, qs = synth.make_workload(w)
     q_ids, q_w = qs[0]
     corpus = wmd.Corpus.from_synth(vecs, c, device=local_rank)
+    # setup (untimed): the autotuner picks the fused-loop tile variant
+    loop_variant = corpus.autotune(q_ids, q_w, w.lam, w.max_iter, prec)
     dq = wmd.DeviceQuery(corpus, q_ids, q_w, prec)
     v_r = dq.v_r
     stream = torch.cuda.current_stream(dev)
@@ -446,6 +456,7 @@ def run_ours(args, w):
         "scaling": "weak", "vs_baseline": None, "dtype": "f32" if prec == wmd.PREC_FP32 else "bf16-K/f32",
         "data": "synthetic (seeded Zipf(1.1) corpus, N(0,1/d) embeddings)",
         "config": {"workload": workload_name(w), "v_r": v_r, "nnz": c.nnz, "active_words": U,
+                   "loop_variant": loop_variant,
                    "l2": "flushed between steps (512 MiB write)",
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(v_r * 8),

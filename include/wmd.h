@@ -176,6 +176,26 @@ wmd_status wmd_query_device(wmd_corpus* corpus, const int32_t* d_q_ids,
                             size_t ws_bytes, double* d_out, void* stream);
 
 /* ---------------------------------------------------------------------------
+ * Tile variants of the fused loop and their autotuner.  Every query width
+ * class (v_r rounded up to 8, 16, 32, 64, 128 or 256) has one or more
+ * register-tile shapes for the fused SDDMM/SpMM loop (same arithmetic, same
+ * results within rounding); they trade work per cross-lane reduction against
+ * resident warps.  wmd_loop_variant_count: how many exist for queries of v_r
+ * words.  wmd_set_loop_variant: use `variant` for v_r's class and `prec` on
+ * this corpus (all later calls; not thread-safe against running queries).
+ * wmd_autotune: synchronous; builds K for the given query (host buffers, as
+ * wmd_query), times every variant of its class on this corpus with CUDA
+ * events, keeps the fastest for that class and precision and writes its
+ * index to *chosen (may be NULL).  Allocates a temporary workspace.
+ * ------------------------------------------------------------------------- */
+int32_t wmd_loop_variant_count(int32_t v_r);
+wmd_status wmd_set_loop_variant(wmd_corpus* corpus, int32_t v_r, wmd_precision prec,
+                                int32_t variant);
+wmd_status wmd_autotune(wmd_corpus* corpus, const int32_t* q_ids, const float* q_w,
+                        int32_t n_q, float lambda, int32_t max_iter, wmd_precision prec,
+                        int32_t* chosen);
+
+/* ---------------------------------------------------------------------------
  * Batched queries (many queries of uneven v_r, one resident corpus).  The
  * paper computes one query against many documents (Sec. 3); a batch is that
  * computation for every query, with each query's K block laid out next to the

@@ -52,7 +52,8 @@ void free_corpus_device(wmd_corpus* c) {
   cudaFree(c->order);
   cudaFree(c->slots);
   cudaFree(c->d_err);
-  for (auto& s : c->sched) cudaFree(s.d_items);
+  for (auto& sc : c->sched)
+    for (auto& s : sc) cudaFree(s.d_items);
   cudaFree(c->ws);
   cudaFree(c->d_qids);
   cudaFree(c->d_qw);
@@ -256,29 +257,31 @@ wmd_status wmd_corpus_load(const float* vecs, int64_t V, int32_t d, const int64_
     c->tmap_ok = !simt && make_vecs_tensor_map(c);
   }
 
-  // per query-width class: team size per document and CTA work items
+  // per query-width class and tile variant: team size per document and CTA
+  // work items (a CTA's 4/W teams take consecutive documents of one team size)
   for (int cls = 0; cls < kNumClasses && e == cudaSuccess; ++cls) {
-    const int64_t rpw = rows_per_warp(cls);
-    std::vector<LoopItem> items;
-    int64_t i = 0;
-    while (i < N) {
-      const int64_t n = dptr[order[i] + 1] - dptr[order[i]];
-      const int W = n <= rpw ? 1 : (n <= 2 * rpw ? 2 : 4);
-      const int per = 4 / W;
-      // the run of documents with the same team size (lengths are sorted)
-      int64_t j = i;
-      while (j < N) {
-        const int64_t m = dptr[order[j] + 1] - dptr[order[j]];
-        const int Wm = m <= rpw ? 1 : (m <= 2 * rpw ? 2 : 4);
-        if (Wm != W) break;
-        ++j;
+    for (int var = 0; var < kClassVariants[cls] && e == cudaSuccess; ++var) {
+      const int64_t rpw = rows_per_warp(cls, var);
+      std::vector<LoopItem> items;
+      int64_t i = 0;
+      while (i < N) {
+        const int64_t n = dptr[order[i] + 1] - dptr[order[i]];
+        const int W = n <= rpw ? 1 : (n <= 2 * rpw ? 2 : 4);
+        const int per = 4 / W;
+        int64_t j = i;
+        while (j < N) {
+          const int64_t m = dptr[order[j] + 1] - dptr[order[j]];
+          const int Wm = m <= rpw ? 1 : (m <= 2 * rpw ? 2 : 4);
+          if (Wm != W) break;
+          ++j;
+        }
+        for (int64_t b = i; b < j; b += per)
+          items.push_back(LoopItem{W, (int32_t)b, (int32_t)std::min<int64_t>(b + per, j), 0});
+        i = j;
       }
-      for (int64_t b = i; b < j; b += per)
-        items.push_back(LoopItem{W, (int32_t)b, (int32_t)std::min<int64_t>(b + per, j), 0});
-      i = j;
+      c->sched[cls][var].n_items = (int32_t)items.size();
+      e = upload(&c->sched[cls][var].d_items, items.data(), items.size(), &bytes);
     }
-    c->sched[cls].n_items = (int32_t)items.size();
-    e = upload(&c->sched[cls].d_items, items.data(), items.size(), &bytes);
   }
   c->device_bytes = bytes;
   if (e != cudaSuccess) {
@@ -362,6 +365,90 @@ wmd_status wmd_query_device(wmd_corpus* c, const int32_t* d_q_ids, const float* 
   st = wmd_build_kernel_matrix(c, d_q_ids, d_q_w, v_r, lambda, prec, d_ws, ws_bytes, stream);
   if (st != WMD_OK) return st;
   return wmd_sinkhorn_loop(c, v_r, max_iter, prec, d_ws, ws_bytes, d_out, stream);
+}
+
+int32_t wmd_loop_variant_count(int32_t v_r) {
+  const int cls = vr_class(v_r);
+  return v_r > 0 && cls >= 0 ? kClassVariants[cls] : 0;
+}
+
+wmd_status wmd_set_loop_variant(wmd_corpus* c, int32_t v_r, wmd_precision prec, int32_t variant) {
+  if (!c) return set_error(WMD_ERR_INVALID_ARG, "corpus is NULL");
+  const int cls = v_r > 0 ? vr_class(v_r) : -1;
+  if (cls < 0) return set_error(WMD_ERR_INVALID_ARG, "v_r out of range");
+  if (prec != WMD_PREC_FP32 && prec != WMD_PREC_BF16_K)
+    return set_error(WMD_ERR_INVALID_ARG, "unknown precision");
+  if (variant < 0 || variant >= kClassVariants[cls])
+    return set_error(WMD_ERR_INVALID_ARG, "no such variant for this query width");
+  c->loop_variant[cls][prec == WMD_PREC_BF16_K] = variant;
+  return WMD_OK;
+}
+
+wmd_status wmd_autotune(wmd_corpus* c, const int32_t* q_ids, const float* q_w, int32_t n_q,
+                        float lambda, int32_t max_iter, wmd_precision prec, int32_t* chosen) {
+  if (!c) return set_error(WMD_ERR_INVALID_ARG, "corpus is NULL");
+  std::vector<int32_t> ids(std::max(n_q, 1));
+  std::vector<float> w(std::max(n_q, 1));
+  int32_t v_r = 0;
+  wmd_status st = wmd_compact_query(q_ids, q_w, n_q, c->V, ids.data(), w.data(), &v_r);
+  if (st != WMD_OK) return st;
+  if ((st = check_query_args(c, v_r, lambda, max_iter)) != WMD_OK) return st;
+  if (prec != WMD_PREC_FP32 && prec != WMD_PREC_BF16_K)
+    return set_error(WMD_ERR_INVALID_ARG, "unknown precision");
+  const int cls = vr_class(v_r);
+  DeviceGuard g(c->device);
+  const size_t ws_bytes = wmd_workspace_bytes(c, v_r, prec);
+  void* ws = nullptr;
+  int32_t* d_ids = nullptr;
+  float* d_w = nullptr;
+  double* d_out = nullptr;
+  cudaStream_t s = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  int best = 0;
+  float best_ms = 0.f;
+  cudaError_t e = cudaMalloc(&ws, ws_bytes);
+  if (e == cudaSuccess) e = cudaMalloc(&d_ids, v_r * sizeof(int32_t));
+  if (e == cudaSuccess) e = cudaMalloc(&d_w, v_r * sizeof(float));
+  if (e == cudaSuccess) e = cudaMalloc(&d_out, std::max<int64_t>(c->N, 1) * sizeof(double));
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaEventCreate(&e0);
+  if (e == cudaSuccess) e = cudaEventCreate(&e1);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(d_ids, ids.data(), v_r * sizeof(int32_t), cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(d_w, w.data(), v_r * sizeof(float), cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) {
+    st = wmd_build_kernel_matrix(c, d_ids, d_w, v_r, lambda, prec, ws, ws_bytes, s);
+    const int keep = c->loop_variant[cls][prec == WMD_PREC_BF16_K];
+    for (int var = 0; var < kClassVariants[cls] && st == WMD_OK && e == cudaSuccess; ++var) {
+      c->loop_variant[cls][prec == WMD_PREC_BF16_K] = var;
+      for (int k = 0; k < 2 && st == WMD_OK; ++k)
+        st = wmd_sinkhorn_loop(c, v_r, max_iter, prec, ws, ws_bytes, d_out, s);
+      if (st != WMD_OK) break;
+      e = cudaEventRecord(e0, s);
+      for (int k = 0; k < 5 && st == WMD_OK; ++k)
+        st = wmd_sinkhorn_loop(c, v_r, max_iter, prec, ws, ws_bytes, d_out, s);
+      if (e == cudaSuccess) e = cudaEventRecord(e1, s);
+      if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+      float ms = 0.f;
+      if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+      if (e == cudaSuccess && (var == 0 || ms < best_ms)) {
+        best_ms = ms;
+        best = var;
+      }
+    }
+    c->loop_variant[cls][prec == WMD_PREC_BF16_K] = (st == WMD_OK && e == cudaSuccess) ? best : keep;
+  }
+  if (s) cudaStreamSynchronize(s);
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  if (s) cudaStreamDestroy(s);
+  cudaFree(ws);
+  cudaFree(d_ids);
+  cudaFree(d_w);
+  cudaFree(d_out);
+  if (e != cudaSuccess) return cuda_error(e, "autotune");
+  if (st != WMD_OK) return st;
+  if (chosen) *chosen = best;
+  return WMD_OK;
 }
 
 wmd_status wmd_query(wmd_corpus* c, const int32_t* q_ids, const float* q_w, int32_t n_q,

@@ -349,19 +349,24 @@ __global__ void __launch_bounds__(128, MINB) sinkhorn_fused_kernel(LoopParams p)
   }
 }
 
-// Per-class tile shapes: {VR, PI, RMAX, CTAs per SM}; RMAX * (VR / PI) floats
-// of K per lane (96 or 128 registers).
-template <int CLS> struct ClassCfg;
-template <> struct ClassCfg<0> { static constexpr int VR = 8, PI = 2, RMAX = 24, MINB = 2; };
-template <> struct ClassCfg<1> { static constexpr int VR = 16, PI = 4, RMAX = 24, MINB = 3; };
-template <> struct ClassCfg<2> { static constexpr int VR = 32, PI = 4, RMAX = 12, MINB = 3; };
-template <> struct ClassCfg<3> { static constexpr int VR = 64, PI = 8, RMAX = 12, MINB = 3; };
-template <> struct ClassCfg<4> { static constexpr int VR = 128, PI = 8, RMAX = 8, MINB = 2; };
-template <> struct ClassCfg<5> { static constexpr int VR = 256, PI = 16, RMAX = 8, MINB = 2; };
+// Tile variants per width class: {VR, PI, RMAX, CTAs per SM}.  RMAX * (VR /
+// PI) floats of K per lane; the variants trade register tile size (work per
+// cross-lane reduction) against resident warps (latency hiding).  The
+// autotuner (wmd_autotune) picks one per class and precision by timing.
+template <int CLS, int V> struct Var;
+template <> struct Var<0, 0> { static constexpr int VR = 8, PI = 2, RMAX = 24, MINB = 2; };
+template <> struct Var<1, 0> { static constexpr int VR = 16, PI = 4, RMAX = 24, MINB = 3; };
+template <> struct Var<2, 0> { static constexpr int VR = 32, PI = 4, RMAX = 12, MINB = 3; };
+template <> struct Var<2, 1> { static constexpr int VR = 32, PI = 4, RMAX = 8, MINB = 4; };
+template <> struct Var<3, 0> { static constexpr int VR = 64, PI = 8, RMAX = 12, MINB = 3; };
+template <> struct Var<3, 1> { static constexpr int VR = 64, PI = 8, RMAX = 8, MINB = 4; };
+template <> struct Var<4, 0> { static constexpr int VR = 128, PI = 8, RMAX = 8, MINB = 2; };
+template <> struct Var<4, 1> { static constexpr int VR = 128, PI = 16, RMAX = 12, MINB = 2; };
+template <> struct Var<5, 0> { static constexpr int VR = 256, PI = 16, RMAX = 8, MINB = 2; };
 
-template <int CLS, typename KT>
-cudaError_t launch_cls(const LoopParams& p, int n_items, int nq, cudaStream_t s) {
-  using Cf = ClassCfg<CLS>;
+template <int CLS, int V, typename KT>
+cudaError_t launch_var(const LoopParams& p, int n_items, int nq, cudaStream_t s) {
+  using Cf = Var<CLS, V>;
   if (n_items == 0 || nq == 0) return cudaSuccess;
   dim3 grid((unsigned)n_items, (unsigned)nq);
   sinkhorn_fused_kernel<Cf::VR, Cf::PI, Cf::RMAX, Cf::MINB, KT><<<grid, 128, 0, s>>>(p);
@@ -369,31 +374,36 @@ cudaError_t launch_cls(const LoopParams& p, int n_items, int nq, cudaStream_t s)
 }
 
 template <typename KT>
-cudaError_t dispatch_loop(int cls, const LoopParams& p, int n_items, int nq, cudaStream_t s) {
+cudaError_t dispatch_loop(int cls, int var, const LoopParams& p, int n_items, int nq,
+                          cudaStream_t s) {
   switch (cls) {
-    case 0: return launch_cls<0, KT>(p, n_items, nq, s);
-    case 1: return launch_cls<1, KT>(p, n_items, nq, s);
-    case 2: return launch_cls<2, KT>(p, n_items, nq, s);
-    case 3: return launch_cls<3, KT>(p, n_items, nq, s);
-    case 4: return launch_cls<4, KT>(p, n_items, nq, s);
-    default: return launch_cls<5, KT>(p, n_items, nq, s);
+    case 0: return launch_var<0, 0, KT>(p, n_items, nq, s);
+    case 1: return launch_var<1, 0, KT>(p, n_items, nq, s);
+    case 2: return var ? launch_var<2, 1, KT>(p, n_items, nq, s) : launch_var<2, 0, KT>(p, n_items, nq, s);
+    case 3: return var ? launch_var<3, 1, KT>(p, n_items, nq, s) : launch_var<3, 0, KT>(p, n_items, nq, s);
+    case 4: return var ? launch_var<4, 1, KT>(p, n_items, nq, s) : launch_var<4, 0, KT>(p, n_items, nq, s);
+    default: return launch_var<5, 0, KT>(p, n_items, nq, s);
   }
 }
+
+template <int CLS, int V>
+constexpr int rpw() { return (32 / Var<CLS, V>::PI) * Var<CLS, V>::RMAX; }
 
 }  // namespace
 
-int rows_per_warp(int cls) {
+int rows_per_warp(int cls, int var) {
   switch (cls) {
-    case 0: return (32 / ClassCfg<0>::PI) * ClassCfg<0>::RMAX;
-    case 1: return (32 / ClassCfg<1>::PI) * ClassCfg<1>::RMAX;
-    case 2: return (32 / ClassCfg<2>::PI) * ClassCfg<2>::RMAX;
-    case 3: return (32 / ClassCfg<3>::PI) * ClassCfg<3>::RMAX;
-    case 4: return (32 / ClassCfg<4>::PI) * ClassCfg<4>::RMAX;
-    default: return (32 / ClassCfg<5>::PI) * ClassCfg<5>::RMAX;
+    case 0: return rpw<0, 0>();
+    case 1: return rpw<1, 0>();
+    case 2: return var ? rpw<2, 1>() : rpw<2, 0>();
+    case 3: return var ? rpw<3, 1>() : rpw<3, 0>();
+    case 4: return var ? rpw<4, 1>() : rpw<4, 0>();
+    default: return rpw<5, 0>();
   }
 }
 
-static LoopParams base_params(const wmd_corpus* c, int cls, const void* K, int ldk, int T) {
+static LoopParams base_params(const wmd_corpus* c, int cls, int var, const void* K, int ldk,
+                              int T) {
   LoopParams p;
   p.doc_ptr = c->doc_ptr;
   p.doc_words = c->doc_words;
@@ -405,7 +415,7 @@ static LoopParams base_params(const wmd_corpus* c, int cls, const void* K, int l
   p.lam = nullptr;
   p.v_r = 0;
   p.T = T;
-  p.items = c->sched[cls].d_items;
+  p.items = c->sched[cls][var].d_items;
   p.slots = c->slots;
   p.out = nullptr;
   p.err = c->d_err;
@@ -416,23 +426,27 @@ static LoopParams base_params(const wmd_corpus* c, int cls, const void* K, int l
 cudaError_t launch_loop(const wmd_corpus* c, int cls, const void* K, int ldk, int kcol0,
                         const float* r, const float* lam, int v_r, int T, wmd_precision prec,
                         double* out, cudaStream_t s) {
-  LoopParams p = base_params(c, cls, K, ldk, T);
+  const int var = c->loop_variant[cls][prec == WMD_PREC_BF16_K];
+  LoopParams p = base_params(c, cls, var, K, ldk, T);
   p.kcol0 = kcol0;
   p.r = r;
   p.lam = lam;
   p.v_r = v_r;
   p.out = out;
-  if (prec == WMD_PREC_BF16_K) return dispatch_loop<__nv_bfloat16>(cls, p, c->sched[cls].n_items, 1, s);
-  return dispatch_loop<float>(cls, p, c->sched[cls].n_items, 1, s);
+  const int n_items = c->sched[cls][var].n_items;
+  if (prec == WMD_PREC_BF16_K) return dispatch_loop<__nv_bfloat16>(cls, var, p, n_items, 1, s);
+  return dispatch_loop<float>(cls, var, p, n_items, 1, s);
 }
 
 cudaError_t launch_loop_batch(const wmd_corpus* c, int cls, const void* K, int ldk,
                               const QueryDesc* d_queries, int nq, int T, wmd_precision prec,
                               cudaStream_t s) {
-  LoopParams p = base_params(c, cls, K, ldk, T);
+  const int var = c->loop_variant[cls][prec == WMD_PREC_BF16_K];
+  LoopParams p = base_params(c, cls, var, K, ldk, T);
   p.queries = d_queries;
-  if (prec == WMD_PREC_BF16_K) return dispatch_loop<__nv_bfloat16>(cls, p, c->sched[cls].n_items, nq, s);
-  return dispatch_loop<float>(cls, p, c->sched[cls].n_items, nq, s);
+  const int n_items = c->sched[cls][var].n_items;
+  if (prec == WMD_PREC_BF16_K) return dispatch_loop<__nv_bfloat16>(cls, var, p, n_items, nq, s);
+  return dispatch_loop<float>(cls, var, p, n_items, nq, s);
 }
 
 }  // namespace wmd

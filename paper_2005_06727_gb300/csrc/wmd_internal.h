@@ -34,9 +34,11 @@ inline int vr_class(int v_r) {
   return -1;
 }
 
-// Rows one warp keeps in registers for a class (lanes-per-row-group x rows
-// per lane); must match the kernel configurations in sinkhorn.cu.
-int rows_per_warp(int cls);
+// Fused-loop tile variants per class (sinkhorn.cu) and the rows one warp of
+// variant `var` keeps in registers (row groups x rows per lane).
+constexpr int kMaxVariants = 2;
+constexpr int kClassVariants[kNumClasses] = {1, 1, 2, 2, 2, 1};
+int rows_per_warp(int cls, int var);
 
 // One CTA work item of the fused loop: a team size W (warps per document),
 // and the range [begin, end) of the length-sorted document order that the
@@ -77,7 +79,8 @@ struct wmd_corpus {
   float* doc_vals = nullptr;   // nnz
   int32_t* order = nullptr;    // N, documents by decreasing length
   wmd::SlotInfo* slots = nullptr;  // N, {beg, n, doc} of order[i]
-  wmd::Schedule sched[wmd::kNumClasses];
+  wmd::Schedule sched[wmd::kNumClasses][wmd::kMaxVariants];
+  int loop_variant[wmd::kNumClasses][2] = {};  // chosen variant per class and precision
   size_t device_bytes = 0;
   int num_sms = 0;
   int* d_err = nullptr;        // device-side timeout flag (sticky); also read by wmd_query

@@ -81,6 +81,9 @@ _SIGS = {
     "wmd_query_device_noalloc": (C.c_int, [_P, _P, _P, C.c_int32, C.c_float, C.c_int32, C.c_int,
                                            _P, _P]),
     "wmd_query_batch": (C.c_int, [_P, C.c_int32, _P, _P, _P, _P, C.c_int32, C.c_int, _P]),
+    "wmd_loop_variant_count": (C.c_int32, [C.c_int32]),
+    "wmd_set_loop_variant": (C.c_int, [_P, C.c_int32, C.c_int, C.c_int32]),
+    "wmd_autotune": (C.c_int, [_P, _P, _P, C.c_int32, C.c_float, C.c_int32, C.c_int, _P]),
     "wmd_server_create": (C.c_int, [_P, _P, _P]),
     "wmd_serve_submit": (C.c_int, [_P, _P, _P, C.c_int32, C.c_float, C.c_int32, C.c_int, _P]),
     "wmd_serve_poll": (C.c_int, [_P, C.c_uint64, _P, C.c_int64]),
@@ -122,6 +125,11 @@ def _check(st: int):
 
 def _ptr(a: np.ndarray):
     return a.ctypes.data_as(C.c_void_p) if a.size else None
+
+
+def loop_variant_count(v_r: int) -> int:
+    """``wmd_loop_variant_count``."""
+    return int(lib().wmd_loop_variant_count(int(v_r)))
 
 
 def compact_query(q_ids, q_w, V: int):
@@ -205,6 +213,19 @@ class Corpus:
         _check(lib().wmd_query(self._h, _ptr(ids), _ptr(w), ids.size, float(lam), int(max_iter),
                                int(prec), _ptr(out)))
         return out
+
+    def set_loop_variant(self, v_r: int, variant: int, prec: int = PREC_FP32):
+        """``wmd_set_loop_variant``."""
+        _check(lib().wmd_set_loop_variant(self._h, int(v_r), int(prec), int(variant)))
+
+    def autotune(self, q_ids, q_w, lam: float, max_iter: int, prec: int = PREC_FP32) -> int:
+        """``wmd_autotune``: returns the chosen fused-loop variant."""
+        ids = np.ascontiguousarray(q_ids, dtype=np.int32)
+        w = np.ascontiguousarray(q_w, dtype=np.float32)
+        chosen = C.c_int32(-1)
+        _check(lib().wmd_autotune(self._h, _ptr(ids), _ptr(w), ids.size, float(lam), int(max_iter),
+                                  int(prec), C.byref(chosen)))
+        return int(chosen.value)
 
     def query_batch(self, queries, lam, max_iter: int, prec: int = PREC_FP32) -> np.ndarray:
         """``wmd_query_batch``: ``queries`` is a list of (ids, weights); ``lam``

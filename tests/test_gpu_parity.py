@@ -325,3 +325,37 @@ def test_paper_shaped_with_both_cdist_kernels(wmd, monkeypatch, kernel):
     want = oracle(vecs, c, q_ids, q_w, w.lam, w.max_iter, docs=docs)
     got = corpus.query(q_ids, q_w, w.lam, w.max_iter)
     assert_parity(got[docs], want, FP32_RTOL, f"paper-shaped fp32 {kernel}")
+
+
+# ---------------------------------------------------------------- fused-loop tile variants
+@pytest.mark.parametrize("v_r", [6, 16, 30, 64, 100, 200])
+def test_every_loop_variant_matches_oracle(wmd, v_r):
+    """Each register-tile variant of each width class gives the oracle's
+    values (documents long enough for teams of 1, 2 and 4 warps and for the
+    chunked path), and the autotuner picks one of them."""
+    V = 4000
+    vecs = synth.make_vecs(V, 300, 500 + v_r)
+    rng = np.random.default_rng(v_r)
+    lengths = [1, 7, 20, 40, 48, 64, 65, 96, 97, 130, 192, 193, 260, 400]
+    docs = []
+    for n in lengths:
+        ids = np.sort(rng.choice(V, n, replace=False)).astype(np.int32)
+        wts = rng.random(n) + 0.05
+        docs.append((ids, (wts / wts.sum()).astype(np.float32)))
+    c = synth.corpus_from_docs(V, docs)
+    q_ids, q_w = synth.make_query(V, v_r, 600 + v_r)
+    corpus = wmd.Corpus.from_synth(vecs, c)
+    want = oracle(vecs, c, q_ids, q_w, 10.0, 15)
+    n_var = wmd.loop_variant_count(v_r)
+    assert n_var >= 1
+    for var in range(n_var):
+        corpus.set_loop_variant(v_r, var)
+        assert_parity(corpus.query(q_ids, q_w, 10.0, 15), want, FP32_RTOL, f"v_r={v_r} variant {var}")
+        corpus.set_loop_variant(v_r, var, wmd.PREC_BF16_K)
+        assert_parity(corpus.query(q_ids, q_w, 10.0, 15, wmd.PREC_BF16_K), want, BF16_RTOL,
+                      f"bf16 v_r={v_r} variant {var}")
+    chosen = corpus.autotune(q_ids, q_w, 10.0, 15)
+    assert 0 <= chosen < n_var
+    assert_parity(corpus.query(q_ids, q_w, 10.0, 15), want, FP32_RTOL, "after autotune")
+    with pytest.raises(wmd.WMDError):
+        corpus.set_loop_variant(v_r, n_var)
