@@ -56,8 +56,8 @@ void free_corpus_device(wmd_corpus* c) {
     for (auto& s : sc) cudaFree(s.d_items);
   cudaFree(c->ws);
   cudaFree(c->d_qids);
-  cudaFree(c->d_qw);
   cudaFree(c->d_out);
+  cudaFreeHost(c->h_stage);
   if (c->stream) cudaStreamDestroy(c->stream);
 }
 
@@ -455,18 +455,30 @@ wmd_status wmd_query(wmd_corpus* c, const int32_t* q_ids, const float* q_w, int3
                      float lambda, int32_t max_iter, wmd_precision prec, double* out_wmd) {
   if (!c) return set_error(WMD_ERR_INVALID_ARG, "corpus is NULL");
   if (!out_wmd && c->N > 0) return set_error(WMD_ERR_INVALID_ARG, "out_wmd is NULL");
-  std::vector<int32_t> ids(std::max(n_q, 0));
-  std::vector<float> w(std::max(n_q, 0));
+  if (n_q > WMD_MAX_VR) {
+    // compaction may still bring it under the limit: use a temporary
+    std::vector<int32_t> ids(n_q);
+    std::vector<float> w(n_q);
+    int32_t v_r = 0;
+    wmd_status st = wmd_compact_query(q_ids, q_w, n_q, c->V, ids.data(), w.data(), &v_r);
+    if (st != WMD_OK) return st;
+    return wmd_query(c, ids.data(), w.data(), v_r, lambda, max_iter, prec, out_wmd);
+  }
+  std::lock_guard<std::mutex> lock(c->mu);
+  DeviceGuard g(c->device);
+  if (!c->stream) WMD_CUDA_TRY(cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking));
+  if (!c->h_stage)
+    WMD_CUDA_TRY(cudaMallocHost(&c->h_stage, (2 * WMD_MAX_VR + 4) * sizeof(int32_t)));
+  // compact straight into the pinned staging block: ids, then weights
+  int32_t* h_ids = c->h_stage;
+  float* h_w = reinterpret_cast<float*>(c->h_stage + WMD_MAX_VR);
+  int32_t* h_err = c->h_stage + 2 * WMD_MAX_VR;
   int32_t v_r = 0;
-  wmd_status st = wmd_compact_query(q_ids, q_w, n_q, c->V, ids.data(), w.data(), &v_r);
+  wmd_status st = wmd_compact_query(q_ids, q_w, n_q, c->V, h_ids, h_w, &v_r);
   if (st != WMD_OK) return st;
   if ((st = check_query_args(c, v_r, lambda, max_iter)) != WMD_OK) return st;
   if (prec != WMD_PREC_FP32 && prec != WMD_PREC_BF16_K)
     return set_error(WMD_ERR_INVALID_ARG, "unknown precision");
-
-  std::lock_guard<std::mutex> lock(c->mu);
-  DeviceGuard g(c->device);
-  if (!c->stream) WMD_CUDA_TRY(cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking));
   const size_t need = wmd_workspace_bytes(c, v_r, prec);
   if (c->ws_bytes < need) {
     cudaFree(c->ws);
@@ -476,13 +488,16 @@ wmd_status wmd_query(wmd_corpus* c, const int32_t* q_ids, const float* q_w, int3
     c->ws_bytes = need;
   }
   if (!c->d_qids) {
-    WMD_CUDA_TRY(cudaMalloc(&c->d_qids, WMD_MAX_VR * sizeof(int32_t)));
-    WMD_CUDA_TRY(cudaMalloc(&c->d_qw, WMD_MAX_VR * sizeof(float)));
+    WMD_CUDA_TRY(cudaMalloc(&c->d_qids, 2 * WMD_MAX_VR * sizeof(int32_t)));
+    c->d_qw = reinterpret_cast<float*>(c->d_qids + WMD_MAX_VR);
     WMD_CUDA_TRY(cudaMalloc(&c->d_out, (std::max<int64_t>(c->N, 1) + 1) * sizeof(double)));
   }
-  WMD_CUDA_TRY(cudaMemcpyAsync(c->d_qids, ids.data(), v_r * sizeof(int32_t), cudaMemcpyHostToDevice, c->stream));
-  WMD_CUDA_TRY(cudaMemcpyAsync(c->d_qw, w.data(), v_r * sizeof(float), cudaMemcpyHostToDevice, c->stream));
-  st = wmd_query_device(c, c->d_qids, c->d_qw, v_r, lambda, max_iter, prec, c->ws, c->ws_bytes,
+  // one copy for ids and weights (the staging block is contiguous)
+  if (v_r < WMD_MAX_VR) std::memmove(h_ids + v_r, h_w, v_r * sizeof(float));
+  WMD_CUDA_TRY(cudaMemcpyAsync(c->d_qids, h_ids, 2 * v_r * sizeof(int32_t), cudaMemcpyHostToDevice,
+                               c->stream));
+  float* d_w = reinterpret_cast<float*>(c->d_qids + v_r);
+  st = wmd_query_device(c, c->d_qids, d_w, v_r, lambda, max_iter, prec, c->ws, c->ws_bytes,
                         c->d_out, c->stream);
   if (st != WMD_OK) {
     cudaStreamSynchronize(c->stream);
@@ -490,9 +505,9 @@ wmd_status wmd_query(wmd_corpus* c, const int32_t* q_ids, const float* q_w, int3
   }
   if (c->N > 0)
     WMD_CUDA_TRY(cudaMemcpyAsync(out_wmd, c->d_out, c->N * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
-  int err = 0;
-  WMD_CUDA_TRY(cudaMemcpyAsync(&err, c->d_err, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  WMD_CUDA_TRY(cudaMemcpyAsync(h_err, c->d_err, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
   WMD_CUDA_TRY(cudaStreamSynchronize(c->stream));
+  const int err = *h_err;
   if (err) {
     static const char* roles[] = {"?", "producer (stage free)", "converter (tile landed)",
                                   "MMA (accumulator free)", "MMA (tile landed or converted)",

@@ -92,8 +92,9 @@ struct wmd_corpus {
   cudaStream_t stream = nullptr;
   void* ws = nullptr;
   size_t ws_bytes = 0;
-  int32_t* d_qids = nullptr;
-  float* d_qw = nullptr;
+  int32_t* d_qids = nullptr;   // WMD_MAX_VR ids followed by WMD_MAX_VR weights
+  float* d_qw = nullptr;       // = d_qids + WMD_MAX_VR
+  int32_t* h_stage = nullptr;  // pinned: ids, weights, error word
   double* d_out = nullptr;     // N doubles followed by one int error word (host path)
 };
 
