@@ -262,19 +262,21 @@ wmd_status wmd_corpus_load(const float* vecs, int64_t V, int32_t d, const int64_
   for (int cls = 0; cls < kNumClasses && e == cudaSuccess; ++cls) {
     for (int var = 0; var < kClassVariants[cls] && e == cudaSuccess; ++var) {
       const int64_t rpw = rows_per_warp(cls, var);
+      const int nw = warps_per_cta(cls, var);
+      // the smallest team that keeps the document resident, else the widest
+      auto team = [&](int64_t n) {
+        int W = 1;
+        while (W < nw && n > W * rpw) W *= 2;
+        return W;
+      };
       std::vector<LoopItem> items;
       int64_t i = 0;
       while (i < N) {
         const int64_t n = dptr[order[i] + 1] - dptr[order[i]];
-        const int W = n <= rpw ? 1 : (n <= 2 * rpw ? 2 : 4);
-        const int per = 4 / W;
+        const int W = team(n);
+        const int per = nw / W;
         int64_t j = i;
-        while (j < N) {
-          const int64_t m = dptr[order[j] + 1] - dptr[order[j]];
-          const int Wm = m <= rpw ? 1 : (m <= 2 * rpw ? 2 : 4);
-          if (Wm != W) break;
-          ++j;
-        }
+        while (j < N && team(dptr[order[j] + 1] - dptr[order[j]]) == W) ++j;
         for (int64_t b = i; b < j; b += per)
           items.push_back(LoopItem{W, (int32_t)b, (int32_t)std::min<int64_t>(b + per, j), 0});
         i = j;

@@ -105,8 +105,9 @@ struct TeamCtx {
   QueryDesc q;  // the query this CTA works for (q.lambda resolved)
   int rpw_res;  // rows per warp when the document is register resident
   int nch;      // chunks this warp handles
-  float* red;   // [2][4][VR] partial x of every warp of the CTA
-  double* wred; // [4] partial WMD of every warp of the CTA
+  float* red;   // [2][NW][VR] partial x of every warp of the CTA
+  double* wred; // [NW] partial WMD of every warp of the CTA
+  int nw;       // warps in the CTA
 };
 
 // The whole solve of one document by one team, with R rows per lane known at
@@ -235,7 +236,7 @@ __device__ __forceinline__ void solve(const LoopParams& p, const TeamCtx& t) {
       }
       // ... and over the warps of the team (fixed order, so deterministic)
       if (t.W > 1) {
-        float* red = t.red + buf * 4 * VR;
+        float* red = t.red + buf * t.nw * VR;
         if (t.pw == 0) {
 #pragma unroll
           for (int q = 0; q < C2; ++q) {
@@ -278,8 +279,8 @@ __device__ __forceinline__ void solve(const LoopParams& p, const TeamCtx& t) {
   }
 }
 
-template <int VR, int PI, int RMAX, int MINB, typename KT>
-__global__ void __launch_bounds__(128, MINB) sinkhorn_fused_kernel(LoopParams p) {
+template <int VR, int PI, int RMAX, int MINB, int NW, typename KT>
+__global__ void __launch_bounds__(NW * 32, MINB) sinkhorn_fused_kernel(LoopParams p) {
   constexpr int C = VR / PI;
   constexpr int PW = 32 / PI;
   constexpr int RPW = PW * RMAX;
@@ -287,8 +288,8 @@ __global__ void __launch_bounds__(128, MINB) sinkhorn_fused_kernel(LoopParams p)
   static_assert(C % 4 == 0, "columns per lane must be a multiple of 4");
   static_assert(RMAX % 4 == 0, "RMAX must split into 4 steps");
 
-  __shared__ __align__(16) float red[2 * 4 * VR];
-  __shared__ double wred[4];
+  __shared__ __align__(16) float red[2 * NW * VR];
+  __shared__ double wred[NW];
 
   TeamCtx t;
   if (p.queries) {
@@ -309,7 +310,7 @@ __global__ void __launch_bounds__(128, MINB) sinkhorn_fused_kernel(LoopParams p)
   t.team = t.warp / t.W;
   t.kw = t.warp - t.team * t.W;
   const int slot = item.begin + t.team;
-  if (t.team >= 4 / t.W || slot >= item.end) return;  // whole team leaves together
+  if (t.team >= NW / t.W || slot >= item.end) return;  // whole team leaves together
 
   const SlotInfo si = p.slots[slot];
   t.doc = si.doc;
@@ -326,6 +327,7 @@ __global__ void __launch_bounds__(128, MINB) sinkhorn_fused_kernel(LoopParams p)
   }
   t.red = red;
   t.wred = wred;
+  t.nw = NW;
 
   if (t.n <= t.W * RPW) {
     // register resident: one chunk of rpw_res rows per warp
@@ -349,27 +351,30 @@ __global__ void __launch_bounds__(128, MINB) sinkhorn_fused_kernel(LoopParams p)
   }
 }
 
-// Tile variants per width class: {VR, PI, RMAX, CTAs per SM}.  RMAX * (VR /
-// PI) floats of K per lane; the variants trade register tile size (work per
-// cross-lane reduction) against resident warps (latency hiding).  The
-// autotuner (wmd_autotune) picks one per class and precision by timing.
+// Tile variants per width class: {VR, PI, RMAX, CTAs per SM, warps per CTA}.
+// RMAX * (VR / PI) floats of K per lane; the variants trade register tile
+// size (work per cross-lane reduction) against resident warps (latency
+// hiding), and wide queries use 8-warp CTAs so that a team of up to 8 warps
+// keeps a long document's K block resident.  The autotuner (wmd_autotune)
+// picks one per class and precision by timing.
 template <int CLS, int V> struct Var;
-template <> struct Var<0, 0> { static constexpr int VR = 8, PI = 2, RMAX = 24, MINB = 2; };
-template <> struct Var<1, 0> { static constexpr int VR = 16, PI = 4, RMAX = 24, MINB = 3; };
-template <> struct Var<2, 0> { static constexpr int VR = 32, PI = 4, RMAX = 12, MINB = 3; };
-template <> struct Var<2, 1> { static constexpr int VR = 32, PI = 4, RMAX = 8, MINB = 4; };
-template <> struct Var<3, 0> { static constexpr int VR = 64, PI = 8, RMAX = 12, MINB = 3; };
-template <> struct Var<3, 1> { static constexpr int VR = 64, PI = 8, RMAX = 8, MINB = 4; };
-template <> struct Var<4, 0> { static constexpr int VR = 128, PI = 8, RMAX = 8, MINB = 2; };
-template <> struct Var<4, 1> { static constexpr int VR = 128, PI = 16, RMAX = 12, MINB = 2; };
-template <> struct Var<5, 0> { static constexpr int VR = 256, PI = 16, RMAX = 8, MINB = 2; };
+template <> struct Var<0, 0> { static constexpr int VR = 8, PI = 2, RMAX = 24, MINB = 2, NW = 4; };
+template <> struct Var<1, 0> { static constexpr int VR = 16, PI = 4, RMAX = 24, MINB = 3, NW = 4; };
+template <> struct Var<2, 0> { static constexpr int VR = 32, PI = 4, RMAX = 12, MINB = 3, NW = 4; };
+template <> struct Var<2, 1> { static constexpr int VR = 32, PI = 4, RMAX = 8, MINB = 4, NW = 4; };
+template <> struct Var<3, 0> { static constexpr int VR = 64, PI = 8, RMAX = 12, MINB = 3, NW = 4; };
+template <> struct Var<3, 1> { static constexpr int VR = 64, PI = 8, RMAX = 8, MINB = 4, NW = 4; };
+template <> struct Var<4, 0> { static constexpr int VR = 128, PI = 8, RMAX = 8, MINB = 1, NW = 8; };
+template <> struct Var<4, 1> { static constexpr int VR = 128, PI = 8, RMAX = 8, MINB = 2, NW = 4; };
+template <> struct Var<5, 0> { static constexpr int VR = 256, PI = 16, RMAX = 8, MINB = 1, NW = 8; };
+template <> struct Var<5, 1> { static constexpr int VR = 256, PI = 16, RMAX = 8, MINB = 2, NW = 4; };
 
 template <int CLS, int V, typename KT>
 cudaError_t launch_var(const LoopParams& p, int n_items, int nq, cudaStream_t s) {
   using Cf = Var<CLS, V>;
   if (n_items == 0 || nq == 0) return cudaSuccess;
   dim3 grid((unsigned)n_items, (unsigned)nq);
-  sinkhorn_fused_kernel<Cf::VR, Cf::PI, Cf::RMAX, Cf::MINB, KT><<<grid, 128, 0, s>>>(p);
+  sinkhorn_fused_kernel<Cf::VR, Cf::PI, Cf::RMAX, Cf::MINB, Cf::NW, KT><<<grid, Cf::NW * 32, 0, s>>>(p);
   return cudaGetLastError();
 }
 
@@ -382,7 +387,7 @@ cudaError_t dispatch_loop(int cls, int var, const LoopParams& p, int n_items, in
     case 2: return var ? launch_var<2, 1, KT>(p, n_items, nq, s) : launch_var<2, 0, KT>(p, n_items, nq, s);
     case 3: return var ? launch_var<3, 1, KT>(p, n_items, nq, s) : launch_var<3, 0, KT>(p, n_items, nq, s);
     case 4: return var ? launch_var<4, 1, KT>(p, n_items, nq, s) : launch_var<4, 0, KT>(p, n_items, nq, s);
-    default: return launch_var<5, 0, KT>(p, n_items, nq, s);
+    default: return var ? launch_var<5, 1, KT>(p, n_items, nq, s) : launch_var<5, 0, KT>(p, n_items, nq, s);
   }
 }
 
@@ -398,7 +403,15 @@ int rows_per_warp(int cls, int var) {
     case 2: return var ? rpw<2, 1>() : rpw<2, 0>();
     case 3: return var ? rpw<3, 1>() : rpw<3, 0>();
     case 4: return var ? rpw<4, 1>() : rpw<4, 0>();
-    default: return rpw<5, 0>();
+    default: return var ? rpw<5, 1>() : rpw<5, 0>();
+  }
+}
+
+int warps_per_cta(int cls, int var) {
+  switch (cls) {
+    case 4: return var ? Var<4, 1>::NW : Var<4, 0>::NW;
+    case 5: return var ? Var<5, 1>::NW : Var<5, 0>::NW;
+    default: return 4;
   }
 }
 

@@ -37,12 +37,13 @@ inline int vr_class(int v_r) {
 // Fused-loop tile variants per class (sinkhorn.cu) and the rows one warp of
 // variant `var` keeps in registers (row groups x rows per lane).
 constexpr int kMaxVariants = 2;
-constexpr int kClassVariants[kNumClasses] = {1, 1, 2, 2, 2, 1};
+constexpr int kClassVariants[kNumClasses] = {1, 1, 2, 2, 2, 2};
 int rows_per_warp(int cls, int var);
+int warps_per_cta(int cls, int var);  // 4 or 8
 
 // One CTA work item of the fused loop: a team size W (warps per document),
 // and the range [begin, end) of the length-sorted document order that the
-// CTA's 4/W teams take, one document each.
+// CTA's NW/W teams take, one document each (NW = warps per CTA).
 struct LoopItem {
   int32_t W;
   int32_t begin;
