@@ -83,6 +83,13 @@ __device__ __forceinline__ float k_times_neg_logk(float k) {
   return k >= 1.17549435e-38f ? -k * __logf(k) : 0.f;
 }
 
+// Knuth's TwoSum: s + e == a + b exactly (s = fl(a + b)).
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = a + b;
+  const float bb = s - a;
+  e = (a - (s - bb)) + (b - bb);
+}
+
 // Hardware reciprocal (PTX rcp.approx, about 1 ulp); operands here are never
 // zero: padding rows and columns are seeded so that their sums stay positive.
 __device__ __forceinline__ float fast_rcp(float x) {
@@ -262,10 +269,20 @@ __device__ __forceinline__ void solve(const LoopParams& p, const TeamCtx& t) {
     }
   }
 
-  // WMD_j: sum over the lanes of the warp, then over the team's warps
-  double wsum = (double)wacc;
+  // WMD_j: sum over the lanes of the warp in double-float (hi + lo pairs
+  // combined with TwoSum, as accurate as float64 for these 32 terms and
+  // without the GPU's slow float64 pipe), then over the team's warps in
+  // float64
+  float hi = wacc, lo = 0.f;
 #pragma unroll
-  for (int off = 1; off < 32; off <<= 1) wsum += __shfl_xor_sync(0xffffffffu, wsum, off);
+  for (int off = 1; off < 32; off <<= 1) {
+    const float h2 = __shfl_xor_sync(0xffffffffu, hi, off);
+    const float l2 = __shfl_xor_sync(0xffffffffu, lo, off);
+    float sh, se;
+    two_sum(hi, h2, sh, se);
+    two_sum(sh, se + (lo + l2), hi, lo);
+  }
+  const double wsum = (double)hi + (double)lo;
   if (t.W > 1) {
     if (t.lane == 0) t.wred[t.warp] = wsum;
     team_barrier(1 + t.team, 32 * t.W);
