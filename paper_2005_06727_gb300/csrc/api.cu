@@ -58,6 +58,10 @@ void free_corpus_device(wmd_corpus* c) {
   cudaFree(c->d_qids);
   cudaFree(c->d_out);
   cudaFreeHost(c->h_stage);
+  cudaFreeHost(c->h_out);
+  for (auto& g : c->qgraphs)
+    if (g.exec) cudaGraphExecDestroy(g.exec);
+  c->qgraphs.clear();
   if (c->stream) cudaStreamDestroy(c->stream);
 }
 
@@ -483,6 +487,11 @@ wmd_status wmd_query(wmd_corpus* c, const int32_t* q_ids, const float* q_w, int3
     return set_error(WMD_ERR_INVALID_ARG, "unknown precision");
   const size_t need = wmd_workspace_bytes(c, v_r, prec);
   if (c->ws_bytes < need) {
+    // a new workspace invalidates the captured sequences that point into it
+    cudaStreamSynchronize(c->stream);
+    for (auto& g2 : c->qgraphs)
+      if (g2.exec) cudaGraphExecDestroy(g2.exec);
+    c->qgraphs.clear();
     cudaFree(c->ws);
     c->ws = nullptr;
     c->ws_bytes = 0;
@@ -493,22 +502,76 @@ wmd_status wmd_query(wmd_corpus* c, const int32_t* q_ids, const float* q_w, int3
     WMD_CUDA_TRY(cudaMalloc(&c->d_qids, 2 * WMD_MAX_VR * sizeof(int32_t)));
     c->d_qw = reinterpret_cast<float*>(c->d_qids + WMD_MAX_VR);
     WMD_CUDA_TRY(cudaMalloc(&c->d_out, (std::max<int64_t>(c->N, 1) + 1) * sizeof(double)));
+    WMD_CUDA_TRY(cudaMallocHost(&c->h_out, std::max<int64_t>(c->N, 1) * sizeof(double)));
   }
   // one copy for ids and weights (the staging block is contiguous)
   if (v_r < WMD_MAX_VR) std::memmove(h_ids + v_r, h_w, v_r * sizeof(float));
-  WMD_CUDA_TRY(cudaMemcpyAsync(c->d_qids, h_ids, 2 * v_r * sizeof(int32_t), cudaMemcpyHostToDevice,
-                               c->stream));
   float* d_w = reinterpret_cast<float*>(c->d_qids + v_r);
-  st = wmd_query_device(c, c->d_qids, d_w, v_r, lambda, max_iter, prec, c->ws, c->ws_bytes,
-                        c->d_out, c->stream);
-  if (st != WMD_OK) {
-    cudaStreamSynchronize(c->stream);
-    return st;
+
+  // the whole sequence (H2D, cdist, loop, D2H of results and error word)
+  // runs eagerly on the first use of a query shape and from a captured CUDA
+  // graph from the second use on
+  const int cls = vr_class(v_r);
+  const int variant = c->loop_variant[cls][prec == WMD_PREC_BF16_K];
+  auto enqueue = [&]() -> wmd_status {
+    WMD_CUDA_TRY(cudaMemcpyAsync(c->d_qids, h_ids, 2 * v_r * sizeof(int32_t),
+                                 cudaMemcpyHostToDevice, c->stream));
+    wmd_status s2 = wmd_query_device(c, c->d_qids, d_w, v_r, lambda, max_iter, prec, c->ws,
+                                     c->ws_bytes, c->d_out, c->stream);
+    if (s2 != WMD_OK) return s2;
+    if (c->N > 0)
+      WMD_CUDA_TRY(cudaMemcpyAsync(c->h_out, c->d_out, c->N * sizeof(double),
+                                   cudaMemcpyDeviceToHost, c->stream));
+    WMD_CUDA_TRY(cudaMemcpyAsync(h_err, c->d_err, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    return WMD_OK;
+  };
+  wmd_corpus::QueryGraph* qg = nullptr;
+  for (auto& g2 : c->qgraphs)
+    if (g2.v_r == v_r && g2.T == max_iter && g2.prec == (int)prec && g2.variant == variant &&
+        g2.lambda == lambda)
+      qg = &g2;
+  if (!qg) {
+    if (c->qgraphs.size() >= 8) {
+      auto oldest = std::min_element(c->qgraphs.begin(), c->qgraphs.end(),
+                                     [](const wmd_corpus::QueryGraph& a, const wmd_corpus::QueryGraph& b) {
+                                       return a.last < b.last;
+                                     });
+      if (oldest->exec) cudaGraphExecDestroy(oldest->exec);
+      c->qgraphs.erase(oldest);
+    }
+    c->qgraphs.push_back(wmd_corpus::QueryGraph{v_r, max_iter, (int)prec, variant, lambda, 0, nullptr, 0});
+    qg = &c->qgraphs.back();
   }
-  if (c->N > 0)
-    WMD_CUDA_TRY(cudaMemcpyAsync(out_wmd, c->d_out, c->N * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
-  WMD_CUDA_TRY(cudaMemcpyAsync(h_err, c->d_err, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  qg->last = ++c->qtick;
+  if (qg->exec) {
+    WMD_CUDA_TRY(cudaGraphLaunch(qg->exec, c->stream));
+  } else if (qg->uses >= 1) {
+    cudaGraph_t graph = nullptr;
+    WMD_CUDA_TRY(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+    st = enqueue();
+    cudaError_t e = cudaStreamEndCapture(c->stream, &graph);
+    if (st != WMD_OK) {
+      if (graph) cudaGraphDestroy(graph);
+      return st;
+    }
+    if (e != cudaSuccess) return cuda_error(e, "cudaStreamEndCapture");
+    e = cudaGraphInstantiate(&qg->exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) {
+      qg->exec = nullptr;
+      return cuda_error(e, "cudaGraphInstantiate");
+    }
+    WMD_CUDA_TRY(cudaGraphLaunch(qg->exec, c->stream));
+  } else {
+    st = enqueue();
+    if (st != WMD_OK) {
+      cudaStreamSynchronize(c->stream);
+      return st;
+    }
+  }
+  qg->uses += 1;
   WMD_CUDA_TRY(cudaStreamSynchronize(c->stream));
+  if (c->N > 0) std::memcpy(out_wmd, c->h_out, c->N * sizeof(double));
   const int err = *h_err;
   if (err) {
     static const char* roles[] = {"?", "producer (stage free)", "converter (tile landed)",

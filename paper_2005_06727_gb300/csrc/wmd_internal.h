@@ -97,6 +97,17 @@ struct wmd_corpus {
   float* d_qw = nullptr;       // = d_qids + WMD_MAX_VR
   int32_t* h_stage = nullptr;  // pinned: ids, weights, error word
   double* d_out = nullptr;     // N doubles followed by one int error word (host path)
+  double* h_out = nullptr;     // pinned N doubles (host path, graph replay)
+  // captured host-path sequences, keyed by query shape (second use onwards)
+  struct QueryGraph {
+    int v_r, T, prec, variant;
+    float lambda;
+    int uses;
+    cudaGraphExec_t exec;
+    uint64_t last;
+  };
+  std::vector<QueryGraph> qgraphs;
+  uint64_t qtick = 0;
 };
 
 namespace wmd {
