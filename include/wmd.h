@@ -85,7 +85,7 @@ const char* wmd_last_error(void);
 const char* wmd_version(void);
 
 /* ---------------------------------------------------------------------------
- * Query compaction (Algorithm 1, first line: I = (r > 0)).  Host only, no GPU.
+ * Query compaction (Algorithm 1, the selection I = (r > 0)).  Host only, no GPU.
  * q_ids[n_q], q_w[n_q]: the sparse query r as (word id, weight) pairs, host.
  * Entries with weight 0 are dropped; the kept pairs are written, in input
  * order, to out_ids / out_w (host, capacity n_q each) and their count to
@@ -146,17 +146,18 @@ wmd_status wmd_query(wmd_corpus* corpus, const int32_t* q_ids, const float* q_w,
  * never read outside the corpus for an out-of-range id: its column of K
  * becomes NaN and so does every result, but uniqueness is not re-checked.
  * d_ws: device workspace of at least wmd_workspace_bytes(...) bytes, 256-byte
- * aligned; it holds r, K and K .* M between the two stages.
+ * aligned; it holds r, lambda and K between the two stages.
  * d_out: device array of N doubles.
  *
  * wmd_build_kernel_matrix (Sec. 2 distance, Sec. 5 GEMM-type cdist,
- * Algorithm 1 line K = exp(-lambda M)): K[w, i] and (K .* M)[w, i] for every
- * active word w (a word that occurs in some document), word-major (the "on
- * the fly transpose" of Sec. 3), plus the padded weights r, into d_ws.
+ * Algorithm 1's K = exp(-lambda M)): K[w, i] for every active word w (a word
+ * that occurs in some document), word-major (the "on the fly transpose" of
+ * Sec. 3), plus the padded weights r and lambda, into d_ws.
  * wmd_sinkhorn_loop (Algorithm 1 loop and final reduction; the fused
  * SDDMM_SpMM kernel of Sec. 3): max_iter iterations plus the final reduction
- * for all N documents, reading K, K .* M and r from the workspace that
- * wmd_build_kernel_matrix filled (same v_r and precision).
+ * for all N documents, reading K, r and lambda from the workspace that
+ * wmd_build_kernel_matrix filled (same v_r and precision); K .* M of the
+ * final step is recovered from K as K (-ln K) / lambda.
  * wmd_query_device: both stages.
  * ------------------------------------------------------------------------- */
 size_t wmd_workspace_bytes(const wmd_corpus* corpus, int32_t v_r, wmd_precision prec);

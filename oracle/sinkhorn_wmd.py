@@ -40,7 +40,7 @@ import scipy.sparse as sp
 
 
 # --------------------------------------------------------------------------
-# Algorithm 1, first line: I = (r > 0)
+# Algorithm 1, query selection: I = (r > 0)
 # --------------------------------------------------------------------------
 def select_nonzero(q_ids, q_w):
     """Keep the query words with positive weight (Algorithm 1: I = (r > 0)).

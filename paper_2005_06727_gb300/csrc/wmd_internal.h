@@ -129,7 +129,7 @@ cudaError_t launch_cdist_tc(const wmd_corpus* c, const int32_t* q_ids, const flo
 bool make_vecs_tensor_map(wmd_corpus* c);
 void release_batch_state(const wmd_corpus* c);  // serve.cu: cached batch buffers and graphs
 // One query of a batched loop launch: its padded weights r, output row, first
-// column of its block in the word-major K / K .* M, and its number of words.
+// column of its block in the word-major K, and its number of words.
 struct QueryDesc {
   const float* r;
   double* out;
