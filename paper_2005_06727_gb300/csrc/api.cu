@@ -7,7 +7,10 @@
 #include <cstdlib>
 #include <cstring>
 #include <numeric>
+#include <thread>
 #include <vector>
+
+#include <cuda_fp16.h>
 
 #include "wmd_internal.h"
 
@@ -45,6 +48,9 @@ cudaError_t upload(T** dst, const T* src, size_t count, size_t* bytes) {
 void free_corpus_device(wmd_corpus* c) {
   cudaFree(c->vecs);
   cudaFree(c->norms);
+  cudaFree(c->vecs_hi);
+  cudaFree(c->vecs_lo);
+  cudaFree(c->rscale);
   cudaFree(c->perm);
   cudaFree(c->doc_ptr);
   cudaFree(c->doc_words);
@@ -211,6 +217,41 @@ wmd_status wmd_corpus_load(const float* vecs, int64_t V, int32_t d, const int64_
     hn[perm[w]] = (float)s;
   }
 
+  // fp16 pair of every row for the tensor-core cdist: scale the row by 2^e so
+  // that its largest magnitude lies in [2^14, 2^15) (exact), hi = fp16(x),
+  // lo = fp16((x - hi) * 2^11) (x - hi is exact in float32); the dropped part
+  // is below 2^-22 of the row's largest entry.  Host arithmetic only, so the
+  // pair is the same on every machine.
+  std::vector<uint16_t> hhi((size_t)V * c->ldv, 0), hlo((size_t)V * c->ldv, 0);
+  std::vector<float> hrs(V, 1.f);
+  auto split_rows = [&](int64_t r0, int64_t r1) {
+    for (int64_t r = r0; r < r1; ++r) {
+      const float* x = hv.data() + (size_t)r * c->ldv;
+      float mx = 0.f;
+      for (int k = 0; k < d; ++k) mx = std::max(mx, std::fabs(x[k]));
+      int ex = 0;
+      if (mx > 0.f) std::frexp(mx, &ex);  // mx < 2^ex
+      const int e = std::min(120, std::max(-120, 15 - ex));
+      hrs[r] = std::ldexp(1.f, -e);
+      for (int k = 0; k < d; ++k) {
+        const float xs = std::ldexp(x[k], e);
+        const __half h = __float2half_rn(xs);
+        const float rem = (xs - __half2float(h)) * 2048.f;
+        const __half l = __float2half_rn(rem);
+        hhi[(size_t)r * c->ldv + k] = __half_as_ushort(h);
+        hlo[(size_t)r * c->ldv + k] = __half_as_ushort(l);
+      }
+    }
+  };
+  {
+    const int64_t nt = std::max<int64_t>(
+        1, std::min<int64_t>({16, (int64_t)std::thread::hardware_concurrency(), V / 4096 + 1}));
+    std::vector<std::thread> pool;
+    for (int64_t t = 1; t < nt; ++t) pool.emplace_back(split_rows, V * t / nt, V * (t + 1) / nt);
+    split_rows(0, V / nt);
+    for (auto& th : pool) th.join();
+  }
+
   // document-major copy of c (CSR of c^T), words as device rows
   std::vector<int64_t> dptr(N + 1, 0);
   for (int64_t e = 0; e < nnz; ++e) dptr[doc_idx[e] + 1]++;
@@ -237,6 +278,9 @@ wmd_status wmd_corpus_load(const float* vecs, int64_t V, int32_t d, const int64_
   size_t bytes = 0;
   if (e == cudaSuccess) e = upload(&c->vecs, hv.data(), hv.size(), &bytes);
   if (e == cudaSuccess) e = upload(&c->norms, hn.data(), hn.size(), &bytes);
+  if (e == cudaSuccess) e = upload(&c->vecs_hi, hhi.data(), hhi.size(), &bytes);
+  if (e == cudaSuccess) e = upload(&c->vecs_lo, hlo.data(), hlo.size(), &bytes);
+  if (e == cudaSuccess) e = upload(&c->rscale, hrs.data(), hrs.size(), &bytes);
   if (e == cudaSuccess) e = upload(&c->perm, perm.data(), perm.size(), &bytes);
   if (e == cudaSuccess) e = upload(&c->doc_ptr, dptr.data(), dptr.size(), &bytes);
   if (e == cudaSuccess) e = upload(&c->doc_words, dwords.data(), dwords.size(), &bytes);

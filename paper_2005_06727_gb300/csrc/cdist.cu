@@ -231,19 +231,20 @@ cudaError_t dispatch_cdist(const wmd_corpus* c, const int32_t* q_ids, const floa
 cudaError_t launch_cdist(const wmd_corpus* c, const int32_t* q_ids, const float* q_w, int v_r,
                          int VR, float lambda, wmd_precision prec, void* K, int ldk, int kcol0,
                          float* r_out, float* lam_out, cudaStream_t s) {
-  // tensor cores (cdist_tc.cu): the query's columns in slices of at most 64
-  // (the width of the resident query operand); every slice streams the
+  // tensor cores (cdist_tc.cu): the query's columns in slices as wide as the
+  // resident query operand allows (128 at most); every slice streams the
   // active vocabulary once
   cudaError_t e = cudaErrorNotSupported;
-  if (VR <= 64) {
+  const int width = cdist_tc_max_width(c);
+  if (width >= VR || (width > 0 && VR <= 16)) {
     e = launch_cdist_tc(c, q_ids, q_w, v_r, VR, lambda, prec, K, ldk, kcol0, r_out, lam_out,
                         c->d_err, s);
-  } else {
+  } else if (width > 0) {
     const size_t esz = prec == WMD_PREC_BF16_K ? 2 : 4;
-    for (int j0 = 0; j0 < VR; j0 += 64) {
-      const int vr_slice = std::max(0, std::min(64, v_r - j0));
+    for (int j0 = 0; j0 < VR; j0 += width) {
+      const int vr_slice = std::max(0, std::min(width, v_r - j0));
       // a slice past the last query word still writes its zero padding
-      e = launch_cdist_tc(c, q_ids + std::min(j0, v_r), q_w + std::min(j0, v_r), vr_slice, 64,
+      e = launch_cdist_tc(c, q_ids + std::min(j0, v_r), q_w + std::min(j0, v_r), vr_slice, width,
                           lambda, prec, static_cast<char*>(K) + (size_t)j0 * esz, ldk, kcol0,
                           r_out ? r_out + j0 : nullptr, j0 == 0 ? lam_out : nullptr, c->d_err, s);
       if (e != cudaSuccess) break;

@@ -4,20 +4,29 @@
 // kernel, m^2(i, w) = |e_i|^2 + |e_w|^2 - 2 e_i . e_w, so that the v_r x V
 // block of M comes out of one GEMM of the query rows (v_r x d) against the
 // vocabulary (V x d), and the same kernel also emits K (Algorithm 1).  Here
-// that GEMM runs on tcgen05 with float32 accuracy from TF32 inputs
-// (3xTF32: a = a_hi + a_lo, a.b ~ a_hi.b_hi + a_hi.b_lo + a_lo.b_hi, dropping
-// only a_lo.b_lo, which is 2^-20 relative), accumulating in TMEM.  B is kept
-// as one 2N-row operand [B_hi; B_lo], so a_hi.b_hi and a_hi.b_lo come out of
-// a single N = 2N MMA that reads the A tile once; a_lo.b_hi is a second MMA.
+// that GEMM runs on tcgen05 (kind::f16, float32 accumulation in TMEM) with
+// float32 accuracy from an fp16 pair per operand, prepared once when the
+// corpus is loaded: every row is scaled by a power of two 2^e so that its
+// largest entry lies in [2^14, 2^15), and x = hi + lo 2^-11 with hi = fp16(x)
+// and lo = fp16((x - hi) 2^11).  Then
+//   a . b = 2^-(e_a + e_b) (a_hi . b_hi + 2^-11 (a_hi . b_lo + a_lo . b_hi))
+// up to the dropped a_lo . b_lo term (2^-22 relative).  B (the query side)
+// is kept as one 2N-row operand [B_hi; B_lo], so a_hi . b_hi and a_hi . b_lo
+// come out of a single N = 2N MMA; a_lo . b_hi is a second MMA that
+// accumulates into the a_hi . b_lo columns, so the large term and the two
+// small ones are summed apart.  Both halves of the vocabulary tile arrive by
+// TMA in their final form: no conversion pass touches shared memory.
 //
 // One persistent CTA per SM walks 128-row tiles of the active vocabulary:
-//   warp 8        TMA producer: 128 x 32 float32 k-blocks of vecs, 128B-swizzled
-//   warps 4..7    converters: split each landed k-block into hi and lo parts
+//   warp 8        TMA producer: 128 x 64 fp16 k-blocks of vecs_hi and vecs_lo
+//                 (128B-swizzled), into an S-stage ring in shared memory
 //   warp 9        MMA issuer (one thread) and TMEM owner
-//   warps 0..3    epilogue: TMEM -> registers, m, K, word-major stores
-// The query side (B, N x d) is gathered once per CTA into shared memory, split
-// into hi/lo parts and kept resident.  The hi part of A is the landed float32
-// tile itself (the tensor core reads the tf32 bits of each operand).  Accumulators are double buffered in
+//   warps 0..7    epilogue (two warps per TMEM lane quarter, half the columns
+//                 each): TMEM -> registers, m, K, word-major stores
+// The query side (B, N x d) is gathered once per CTA by the epilogue and MMA
+// warps into shared memory and kept resident; the producer primes a few
+// stages and holds the rest of the stream until those gathers are in flight,
+// so that they do not queue behind it.  Accumulators are double buffered in
 // TMEM so the epilogue of tile t overlaps the MMAs of tile t+1.  Every wait is
 // bounded: on a timeout the CTA raises a flag, drains what it issued, frees
 // its TMEM and returns.
@@ -35,13 +44,19 @@ namespace wmd {
 namespace tc {
 
 constexpr int kM = 128;                   // vocabulary rows per tile (MMA M)
-constexpr int kKB = 32;                   // float32 elements per 128-byte k-block
-constexpr int kStageBytes = kM * kKB * 4; // one k-block of the A tile
+constexpr int kKB = 64;                   // fp16 elements per 128-byte k-block
+constexpr int kHalfBytes = kM * 128;      // one k-block of the hi (or lo) tile
+constexpr int kStageBytes = 2 * kHalfBytes;
 constexpr int kThreads = 320;             // 10 warps
+constexpr int kBuildThreads = 288;        // warps 0..7 and 9 gather the query operand
+constexpr int kPrime = 2;                 // stages issued before the query gathers
 constexpr long long kWaitCycles = 4000000000ll;  // ~2 s at 2 GHz
+constexpr float kLoScale = 1.f / 2048.f;  // 2^-11
 
 struct Params {
-  const float* vecs;
+  const uint16_t* vhi;  // fp16 pair of the (permuted) vocabulary rows, V x ldv
+  const uint16_t* vlo;
+  const float* rscale;  // 2^-e per row
   int ldv;
   const float* norms;
   int64_t U;
@@ -59,6 +74,7 @@ struct Params {
   float* lam_out;
   int num_tiles;
   int KB;
+  int S;  // stages of the A ring
   int* err;
 };
 
@@ -161,14 +177,15 @@ __device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
                : "memory");
 }
 
-// D[tmem] (+)= A[smem] * B[smem]^T, A: 128 x 8 tf32, B: N x 8 tf32, both K-major.
-__device__ __forceinline__ void mma_tf32(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc,
-                                         uint32_t idesc, uint32_t accumulate) {
+// D[tmem] (+)= A[smem] * B[smem]^T, A: 128 x 16 fp16, B: N x 16 fp16, both
+// K-major, float32 accumulation.
+__device__ __forceinline__ void mma_f16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc,
+                                        uint32_t idesc, uint32_t accumulate) {
   asm volatile(
       "{\n"
       " .reg .pred p;\n"
       " setp.ne.b32 p, %4, 0;\n"
-      " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n"
       "}\n" ::"r"(d_tmem),
       "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
       : "memory");
@@ -194,15 +211,27 @@ __device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
   return d;
 }
 
-// Instruction descriptor for kind::tf32: D float32, A and B tf32, both
-// K-major, shape M x N.
-__host__ __device__ constexpr uint32_t idesc_tf32(int M, int N) {
-  return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(N >> 3) << 17) |
-         ((uint32_t)(M >> 4) << 24);
+// Instruction descriptor for kind::f16: D float32, A and B fp16 (format 0),
+// both K-major, shape M x N.
+__host__ __device__ constexpr uint32_t idesc_f16(int M, int N) {
+  return (1u << 4) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
 
 template <int NC>
 __device__ __forceinline__ void tmem_load(uint32_t taddr, float* v);
+
+template <>
+__device__ __forceinline__ void tmem_load<8>(uint32_t taddr, float* v) {
+  uint32_t r[8];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
+}
 
 template <>
 __device__ __forceinline__ void tmem_load<16>(uint32_t taddr, float* v) {
@@ -237,25 +266,18 @@ __device__ __forceinline__ void tmem_load<32>(uint32_t taddr, float* v) {
   for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
 
-// TMEM columns per tile buffer: 2N for a_hi.[b_hi | b_lo] and N for
-// a_lo.b_hi; two buffers, rounded up to a power of two.
-template <int N>
-__host__ __device__ constexpr int tmem_cols() {
-  return 6 * N <= 32 ? 32 : (6 * N <= 64 ? 64 : (6 * N <= 128 ? 128 : (6 * N <= 256 ? 256 : 512)));
-}
-
-// Stores the first n (a multiple of 4, n <= N) values of a row.
-template <int N>
-__device__ __forceinline__ void store_row(float* dst, const float (&v)[N], int n) {
+// Stores the first n (a multiple of 4, n <= CH) values of a row chunk.
+template <int CH>
+__device__ __forceinline__ void store_chunk(float* dst, const float (&v)[CH], int n) {
 #pragma unroll
-  for (int j = 0; j < N; j += 4)
+  for (int j = 0; j < CH; j += 4)
     if (j < n) *reinterpret_cast<float4*>(dst + j) = make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]);
 }
 
-template <int N>
-__device__ __forceinline__ void store_row(__nv_bfloat16* dst, const float (&v)[N], int n) {
+template <int CH>
+__device__ __forceinline__ void store_chunk(__nv_bfloat16* dst, const float (&v)[CH], int n) {
 #pragma unroll
-  for (int j = 0; j < N; j += 4) {
+  for (int j = 0; j < CH; j += 4) {
     if (j < n) {
       __nv_bfloat162 a = __floats2bfloat162_rn(v[j], v[j + 1]);
       __nv_bfloat162 b = __floats2bfloat162_rn(v[j + 2], v[j + 3]);
@@ -268,36 +290,43 @@ __device__ __forceinline__ void store_row(__nv_bfloat16* dst, const float (&v)[N
 }
 
 // ------------------------------------------------------------------ kernel
-// N: query columns of the tile (MMA N); S: TMA stages of A; LS: slots of the
-// lo-part ring (the hi part is the landed float32 tile itself: the tensor
-// core reads only the tf32 bits of each operand, and lo = a - tf32(a)).
-template <int N, int S, int LS, typename KT>
+// N: query columns of the tile (B holds 2N rows, the MMAs are N = 2N and N).
+template <int N>
+__host__ __device__ constexpr int tmem_cols() {
+  return 4 * N;  // two buffers of [a.b_hi-part | cross terms]
+}
+
+template <int N, typename KT>
 __global__ void __launch_bounds__(kThreads, 1)
-    cdist_tc_kernel(const __grid_constant__ CUtensorMap tmap_a, const Params p) {
-  constexpr uint32_t kIdesc2 = idesc_tf32(kM, 2 * N);  // a_hi . [b_hi | b_lo]
-  constexpr uint32_t kIdesc = idesc_tf32(kM, N);       // a_lo . b_hi
+    cdist_tc_kernel(const __grid_constant__ CUtensorMap tmap_hi,
+                    const __grid_constant__ CUtensorMap tmap_lo, const Params p) {
+  constexpr uint32_t kIdesc2 = idesc_f16(kM, 2 * N);  // a_hi . [b_hi | b_lo]
+  constexpr uint32_t kIdesc = idesc_f16(kM, N);       // a_lo . b_hi
   constexpr int kCols = tmem_cols<N>();
-  static_assert(LS < S, "the lo ring must be shorter than the stage ring");
+  static_assert(kCols >= 32 && kCols <= 512 && (kCols & (kCols - 1)) == 0, "TMEM allocation");
+  constexpr int kHalfN = N / 2;                       // columns per epilogue warp
+  constexpr int CH = kHalfN < 32 ? kHalfN : 32;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
 
   const int KB = p.KB;
+  const int S = p.S;
   const int bblock = 2 * N * 128;               // bytes of one [B_hi; B_lo] k-block
   uint8_t* Bcat = smem;
-  uint8_t* Abuf = Bcat + KB * bblock;           // S stages of landed float32 tiles
-  uint8_t* Lbuf = Abuf + S * kStageBytes;       // LS slots of lo parts
-  uint64_t* bars = reinterpret_cast<uint64_t*>(Lbuf + LS * kStageBytes);
+  uint8_t* Abuf = Bcat + KB * bblock;           // S stages: hi tile, then lo tile
+  uint64_t* bars = reinterpret_cast<uint64_t*>(Abuf + S * kStageBytes);
   uint64_t* full = bars;
-  uint64_t* conv = full + S;
-  uint64_t* empty = conv + S;
+  uint64_t* empty = full + S;
   uint64_t* tfull = empty + S;
   uint64_t* tempty = tfull + 2;
   uint64_t* drain = tempty + 2;
   int32_t* qrow_s = reinterpret_cast<int32_t*>(drain + 1);
   float* qn_s = reinterpret_cast<float*>(qrow_s + N);
-  uint32_t* tmem_base_s = reinterpret_cast<uint32_t*>(qn_s + N);
+  float* qrs_s = qn_s + N;
+  uint32_t* tmem_base_s = reinterpret_cast<uint32_t*>(qrs_s + N);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_base_s + 1);
   int* consumed_s = const_cast<int*>(abort_flag) + 1;
+  volatile int* issued_s = consumed_s + 1;      // gathering warps whose loads are in flight
 
   const int tid = threadIdx.x;
   const int warp = tid >> 5;
@@ -308,16 +337,16 @@ __global__ void __launch_bounds__(kThreads, 1)
   if (tid == 0) {
     for (int s = 0; s < S; ++s) {
       mbar_init(&full[s], 1);
-      mbar_init(&conv[s], 128);
       mbar_init(&empty[s], 1);
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(&tfull[b], 1);
-      mbar_init(&tempty[b], 128);
+      mbar_init(&tempty[b], 256);
     }
     mbar_init(drain, 1);
     *abort_flag = 0;
     *consumed_s = 0;
+    *issued_s = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     fence_async_smem();
   }
@@ -330,12 +359,13 @@ __global__ void __launch_bounds__(kThreads, 1)
 
   if (warp != 8) {
     // ---------------------------------------------------------------- B, all but the producer
-    // query columns (device row, norm), the padded weights, then the resident
-    // B = query rows split into tf32 hi and lo parts in the 128B-swizzled
-    // K-major layout (chunk c of row n lands at chunk c ^ (n % 8)); every
-    // thread issues all its loads before its first store
-    constexpr int kBT = kThreads - 32;
+    // query columns (device row, norm, inverse scale), the padded weights,
+    // then the resident B = the query rows' fp16 pairs in the 128B-swizzled
+    // K-major layout (chunk c of row n lands at chunk c ^ (n % 8)): hi rows
+    // 0..N-1, lo rows N..2N-1 of every k-block; every thread issues all its
+    // loads before its first store
     const int bt = tid < 256 ? tid : tid - 32;  // 0 .. 287
+    float qn = 0.f, qrs = 0.f;
     if (bt < N) {
       int row = -1;
       if (bt < p.v_r) {
@@ -343,67 +373,92 @@ __global__ void __launch_bounds__(kThreads, 1)
         row = (id >= 0 && id < p.V) ? p.perm[id] : -2;
       }
       qrow_s[bt] = row;
+      // these two loads stay in flight behind the B loads below
+      if (row >= 0) {
+        qn = __ldg(p.norms + row);
+        qrs = __ldg(p.rscale + row);
+      } else if (row == -2) {
+        qn = __int_as_float(0x7fc00000);
+      }
     }
     if (p.r_out && blockIdx.x == 0 && bt < p.VR) p.r_out[bt] = bt < p.v_r ? p.q_w[bt] : 0.f;
     if (p.lam_out && blockIdx.x == 0 && bt == 0) *p.lam_out = p.lambda;
-    asm volatile("bar.sync 1, %0;" ::"r"(kBT) : "memory");
-    const int total = N * KB * 8;
-    for (int base = bt; base < total; base += kBT * 12) {
-      float4 v[12];
+    asm volatile("bar.sync 1, %0;" ::"r"(kBuildThreads) : "memory");
+    constexpr int kBatch = 16;
+    const int per_row = KB * 8;                 // 16-byte chunks of one row's hi (or lo) part
+    const int total = 2 * N * per_row;
+    bool first = true;
+    for (int base = bt; base < total; base += kBuildThreads * kBatch) {
+      uint4 v[kBatch];
 #pragma unroll
-      for (int j = 0; j < 12; ++j) {
-        const int idx = base + j * kBT;
-        v[j] = make_float4(0.f, 0.f, 0.f, 0.f);
+      for (int j = 0; j < kBatch; ++j) {
+        const int idx = base + j * kBuildThreads;
+        v[j] = make_uint4(0u, 0u, 0u, 0u);
         if (idx < total) {
-          const int n = idx / (KB * 8);
-          const int rem = idx - n * KB * 8;
-          const int k = (rem >> 3) * kKB + (rem & 7) * 4;
+          const int nn = idx / per_row;           // 0..2N-1: hi rows, then lo rows
+          const int n = nn < N ? nn : nn - N;
+          const int rem = idx - nn * per_row;
+          const int k = (rem >> 3) * kKB + (rem & 7) * 8;
           const int row = qrow_s[n];
+          const uint16_t* src = nn < N ? p.vhi : p.vlo;
           if (row >= 0 && k < p.ldv)
-            v[j] = __ldg(reinterpret_cast<const float4*>(p.vecs + (size_t)row * p.ldv + k));
-          else if (row == -2)
-            v[j] = make_float4(__int_as_float(0x7fc00000), 0.f, 0.f, 0.f);
+            v[j] = __ldg(reinterpret_cast<const uint4*>(src + (size_t)row * p.ldv + k));
         }
       }
+      if (first) {
+        // the producer may stream the vocabulary now: these loads are ahead of it
+        asm volatile("" ::: "memory");
+        if (lane == 0) atomicAdd(const_cast<int*>(issued_s), 1);
+        first = false;
+      }
 #pragma unroll
-      for (int j = 0; j < 12; ++j) {
-        const int idx = base + j * kBT;
+      for (int j = 0; j < kBatch; ++j) {
+        const int idx = base + j * kBuildThreads;
         if (idx < total) {
-          const int n = idx / (KB * 8);
-          const int rem = idx - n * KB * 8;
+          const int nn = idx / per_row;
+          const int rem = idx - nn * per_row;
           const int kb = rem >> 3;
           const int ch = rem & 7;
-          float4 hi;
-          hi.x = __uint_as_float(__float_as_uint(v[j].x) & 0xFFFFE000u);
-          hi.y = __uint_as_float(__float_as_uint(v[j].y) & 0xFFFFE000u);
-          hi.z = __uint_as_float(__float_as_uint(v[j].z) & 0xFFFFE000u);
-          hi.w = __uint_as_float(__float_as_uint(v[j].w) & 0xFFFFE000u);
-          const float4 lo = make_float4(v[j].x - hi.x, v[j].y - hi.y, v[j].z - hi.z, v[j].w - hi.w);
-          const int nl = n + N;  // row of the lo part in the 2N-row operand
-          *reinterpret_cast<float4*>(Bcat + kb * bblock + n * 128 + ((ch ^ (n & 7)) << 4)) = hi;
-          *reinterpret_cast<float4*>(Bcat + kb * bblock + nl * 128 + ((ch ^ (nl & 7)) << 4)) = lo;
+          *reinterpret_cast<uint4*>(Bcat + kb * bblock + nn * 128 + ((ch ^ (nn & 7)) << 4)) = v[j];
         }
       }
     }
-    // norms of the query words (off the load chain of B)
+    if (first && lane == 0) atomicAdd(const_cast<int*>(issued_s), 1);
     if (bt < N) {
-      const int row = qrow_s[bt];
-      qn_s[bt] = row >= 0 ? p.norms[row] : (row == -2 ? __int_as_float(0x7fc00000) : 0.f);
+      qn_s[bt] = qn;
+      qrs_s[bt] = qrs;
     }
     fence_async_smem();
-    asm volatile("bar.sync 1, %0;" ::"r"(kBT) : "memory");  // B resident for everyone
+    asm volatile("bar.sync 1, %0;" ::"r"(kBuildThreads) : "memory");  // B resident for everyone
     if (tid == 0) TC_TRACE(5, 1);
   }
 
   if (warp == 8) {
     // ---------------------------------------------------------------- producer
     if (lane == 0) {
-      asm volatile("prefetch.tensormap [%0];" ::"l"(&tmap_a) : "memory");
+      asm volatile("prefetch.tensormap [%0];" ::"l"(&tmap_hi) : "memory");
+      asm volatile("prefetch.tensormap [%0];" ::"l"(&tmap_lo) : "memory");
       int it = 0;
       bool ok = true;
       for (int lt = 0; lt < nlt && ok; ++lt) {
         const int w0 = ((int)blockIdx.x + lt * (int)gridDim.x) * kM;
         for (int kb = 0; kb < KB; ++kb, ++it) {
+          if (it == kPrime) {
+            // hold the stream until every gathering warp has its loads in flight
+            const long long t0 = clock64();
+            while (*issued_s < kBuildThreads / 32) {
+              if (*abort_flag) {
+                ok = false;
+                break;
+              }
+              if (clock64() - t0 > kWaitCycles) {
+                atomicCAS(const_cast<int*>(abort_flag), 0, 0x40000000 | (7 << 24));
+                ok = false;
+                break;
+              }
+            }
+            if (!ok) break;
+          }
           const int s = it % S;
           const uint32_t ph = (uint32_t)(it / S) & 1u;
           if (!mbar_wait(&empty[s], ph ^ 1u, abort_flag, 1, it)) {
@@ -411,7 +466,8 @@ __global__ void __launch_bounds__(kThreads, 1)
             break;
           }
           mbar_expect_tx(&full[s], kStageBytes);
-          tma_load_2d(Abuf + s * kStageBytes, &tmap_a, &full[s], kb * kKB, w0);
+          tma_load_2d(Abuf + s * kStageBytes, &tmap_hi, &full[s], kb * kKB, w0);
+          tma_load_2d(Abuf + s * kStageBytes + kHalfBytes, &tmap_lo, &full[s], kb * kKB, w0);
           TC_TRACE(0, it);
         }
       }
@@ -424,47 +480,6 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
       }
     }
-  } else if (warp >= 4 && warp < 8) {
-    // ---------------------------------------------------------------- converters
-    // lo = a - tf32(a) of every landed tile, into ring slot it % LS once the
-    // MMAs that read that slot (iteration it - LS) have completed
-    const int ct = tid - 128;
-    int it = 0;
-    bool ok = true;
-    for (int lt = 0; lt < nlt && ok; ++lt) {
-      for (int kb = 0; kb < KB; ++kb, ++it) {
-        const int s = it % S;
-        const uint32_t ph = (uint32_t)(it / S) & 1u;
-        if (!mbar_wait(&full[s], ph, abort_flag, 2, it)) {
-          ok = false;
-          break;
-        }
-        if (ct == 0) TC_TRACE(1, it);
-        if (it >= LS) {
-          const int j = it - LS;
-          if (!mbar_wait(&empty[j % S], (uint32_t)(j / S) & 1u, abort_flag, 6, it)) {
-            ok = false;
-            break;
-          }
-        }
-        const float4* A4 = reinterpret_cast<const float4*>(Abuf + s * kStageBytes);
-        float4* L4 = reinterpret_cast<float4*>(Lbuf + (it % LS) * kStageBytes);
-        float4 v[kStageBytes / 16 / 128];
-#pragma unroll
-        for (int j = 0; j < kStageBytes / 16 / 128; ++j) v[j] = A4[ct + 128 * j];
-#pragma unroll
-        for (int j = 0; j < kStageBytes / 16 / 128; ++j) {
-          const float4 a = v[j];
-          L4[ct + 128 * j] = make_float4(a.x - __uint_as_float(__float_as_uint(a.x) & 0xFFFFE000u),
-                                         a.y - __uint_as_float(__float_as_uint(a.y) & 0xFFFFE000u),
-                                         a.z - __uint_as_float(__float_as_uint(a.z) & 0xFFFFE000u),
-                                         a.w - __uint_as_float(__float_as_uint(a.w) & 0xFFFFE000u));
-        }
-        fence_async_smem();
-        mbar_arrive(&conv[s]);
-        if (ct == 0) *consumed_s = it + 1;
-      }
-    }
   } else if (warp == 9) {
     // ---------------------------------------------------------------- MMA issuer
     if (lane == 0) {
@@ -472,40 +487,31 @@ __global__ void __launch_bounds__(kThreads, 1)
       bool ok = true;
       for (int lt = 0; lt < nlt && ok; ++lt) {
         const int ab = lt & 1;
-        const uint32_t aph = (uint32_t)(lt >> 1) & 1u;
-        if (!mbar_wait(&tempty[ab], aph ^ 1u, abort_flag, 3, lt)) break;
+        const uint32_t tph = (uint32_t)(lt >> 1) & 1u;
+        if (!mbar_wait(&tempty[ab], tph ^ 1u, abort_flag, 3, lt)) break;
         tc_fence_after();
-        const uint32_t d_tmem = tmem_base + (uint32_t)(ab * 3 * N);
+        // columns [0, N): a_hi . b_hi; [N, 2N): a_hi . b_lo + a_lo . b_hi (scaled 2^11)
+        const uint32_t d_tmem = tmem_base + (uint32_t)(ab * 2 * N);
         for (int kb = 0; kb < KB; ++kb, ++it) {
           const int s = it % S;
           const uint32_t ph = (uint32_t)(it / S) & 1u;
           const uint32_t a_hi = smem_u32(Abuf + s * kStageBytes);
-          const uint32_t a_lo = smem_u32(Lbuf + (it % LS) * kStageBytes);
+          const uint32_t a_lo = a_hi + kHalfBytes;
           const uint32_t b_cat = smem_u32(Bcat + kb * bblock);  // rows 0..N-1 are b_hi
-          // a_hi . [b_hi | b_lo] as soon as the tile lands ...
           if (!mbar_wait(&full[s], ph, abort_flag, 4, it)) {
-            ok = false;
-            break;
-          }
-          tc_fence_after();
-#pragma unroll
-          for (int ks = 0; ks < kKB / 8; ++ks) {
-            const uint32_t o = ks * 32;  // 8 tf32 = 32 bytes along K
-            mma_tf32(d_tmem, sw128_desc(a_hi + o), sw128_desc(b_cat + o), kIdesc2, (kb | ks) != 0);
-          }
-          // ... a_lo . b_hi once the converters wrote the lo part
-          if (!mbar_wait(&conv[s], ph, abort_flag, 4, it)) {
             ok = false;
             break;
           }
           TC_TRACE(2, it);
           tc_fence_after();
 #pragma unroll
-          for (int ks = 0; ks < kKB / 8; ++ks) {
-            const uint32_t o = ks * 32;
-            mma_tf32(d_tmem + 2 * N, sw128_desc(a_lo + o), sw128_desc(b_cat + o), kIdesc, (kb | ks) != 0);
+          for (int ks = 0; ks < kKB / 16; ++ks) {
+            const uint32_t o = ks * 32;  // 16 fp16 = 32 bytes along K
+            mma_f16(d_tmem, sw128_desc(a_hi + o), sw128_desc(b_cat + o), kIdesc2, (kb | ks) != 0);
+            mma_f16(d_tmem + N, sw128_desc(a_lo + o), sw128_desc(b_cat + o), kIdesc, 1);
           }
           mma_commit(&empty[s]);
+          if (ok) *consumed_s = it + 1;
         }
         if (ok) mma_commit(&tfull[ab]);
       }
@@ -517,44 +523,49 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
   } else {
     // ---------------------------------------------------------------- epilogue
-    const int row_in_tile = warp * 32 + lane;
-    float acc[N];
+    // warp w reads TMEM lanes 32 (w % 4) .. + 31 (its rows) and the columns
+    // [kHalfN (w / 4), kHalfN (w / 4 + 1)) of both accumulator parts
+    const int q = warp & 3;
+    const int c0 = (warp >> 2) * kHalfN;
+    const int row_in_tile = q * 32 + lane;
+    const int ncols = min(N, p.VR);             // columns this launch owns in K
     for (int lt = 0; lt < nlt; ++lt) {
       const int ab = lt & 1;
-      const uint32_t aph = (uint32_t)(lt >> 1) & 1u;
+      const uint32_t tph = (uint32_t)(lt >> 1) & 1u;
       const int64_t w = (int64_t)((int)blockIdx.x + lt * (int)gridDim.x) * kM + row_in_tile;
-      const float nw = w < p.U ? p.norms[w] : 0.f;  // issued before the wait
-      if (!mbar_wait(&tfull[ab], aph, abort_flag, 5, lt)) break;
+      const bool live = w < p.U;
+      const float nw = live ? p.norms[w] : 0.f;  // issued before the wait
+      const float rsw = live ? p.rscale[w] : 0.f;
+      if (!mbar_wait(&tfull[ab], tph, abort_flag, 5, lt)) break;
       if (tid == 0) TC_TRACE(3, lt);
       tc_fence_after();
-      // a.b = a_hi.b_hi (columns 0..N-1) + a_hi.b_lo (N..2N-1) + a_lo.b_hi (2N..3N-1)
-      const uint32_t taddr = tmem_base + ((uint32_t)(warp * 32) << 16) + (uint32_t)(ab * 3 * N);
-      constexpr int CH = N < 32 ? N : 32;
+      const uint32_t taddr = tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(ab * 2 * N);
 #pragma unroll
-      for (int c = 0; c < N; c += CH) {
-        float t1[CH], t2[CH];
-        tmem_load<CH>(taddr + c, acc + c);
-        tmem_load<CH>(taddr + N + c, t1);
-        tmem_load<CH>(taddr + 2 * N + c, t2);
-#pragma unroll
-        for (int j = 0; j < CH; ++j) acc[c + j] = (t2[j] + t1[j]) + acc[c + j];
-      }
-      tc_fence_before();
-      mbar_arrive(&tempty[ab]);
-
-      if (w < p.U) {
-        // m^2 = |a|^2 + |b|^2 - 2 a.b (clamped), K = exp(-lambda m); the
-        // query's own word is exactly m = 0 (K = 1); padding columns are 0 and
-        // an id outside [0, V) gives NaN
-        float kv[N];
-#pragma unroll
-        for (int j = 0; j < N; ++j) {
-          const float e = expf(-p.lambda * sqrtf(fmaxf((nw + qn_s[j]) - 2.f * acc[j], 0.f)));
-          const int qr = qrow_s[j];
-          const float k = qr == (int)w ? 1.f : (qr == -2 ? __int_as_float(0x7fc00000) : e);
-          kv[j] = j < p.v_r ? k : 0.f;
+      for (int cc = 0; cc < kHalfN; cc += CH) {
+        const int c = c0 + cc;
+        float big[CH], small[CH];
+        tmem_load<CH>(taddr + c, big);
+        tmem_load<CH>(taddr + N + c, small);
+        if (cc + CH == kHalfN) {
+          tc_fence_before();
+          mbar_arrive(&tempty[ab]);
         }
-        store_row<N>(static_cast<KT*>(p.K) + (size_t)w * p.ldk + p.kcol0, kv, N < p.VR ? N : p.VR);
+        if (live && c < ncols) {
+          // a.b = 2^-(e_w + e_q) (big + 2^-11 small); m^2 = |a|^2 + |b|^2 - 2 a.b
+          // (clamped), K = exp(-lambda m); the query's own word is exactly
+          // m = 0 (K = 1); padding columns are 0 and an id outside [0, V) gives NaN
+          float kv[CH];
+#pragma unroll
+          for (int j = 0; j < CH; ++j) {
+            const int col = c + j;
+            const float dot = (fmaf(small[j], kLoScale, big[j]) * rsw) * qrs_s[col];
+            const float e = expf(-p.lambda * sqrtf(fmaxf((nw + qn_s[col]) - 2.f * dot, 0.f)));
+            const int qr = qrow_s[col];
+            const float k = qr == (int)w ? 1.f : (qr == -2 ? __int_as_float(0x7fc00000) : e);
+            kv[j] = col < p.v_r ? k : 0.f;
+          }
+          store_chunk<CH>(static_cast<KT*>(p.K) + (size_t)w * p.ldk + p.kcol0 + c, kv, ncols - c);
+        }
       }
     }
   }
@@ -570,10 +581,21 @@ __global__ void __launch_bounds__(kThreads, 1)
   if (tid == 0 && *abort_flag) atomicCAS(p.err, 0, *abort_flag);
 }
 
-template <int N, int S, int LS>
-size_t smem_bytes(int KB) {
-  return 1024 + 2 * (size_t)KB * N * 128 + (size_t)(S + LS) * kStageBytes + (3 * S + 5) * 8 +
-         N * 8 + 16;
+// Shared memory of one CTA for S stages.
+template <int N>
+size_t smem_bytes(int KB, int S) {
+  return 1024 + 2 * (size_t)KB * N * 128 + (size_t)S * kStageBytes + (2 * S + 5) * 8 + N * 12 + 16;
+}
+
+constexpr size_t kSmemLimit = 232448;
+constexpr int kMaxStages = 6;
+
+// Stages that fit next to the resident B for this width (0 if fewer than 2).
+template <int N>
+int stages_for(int KB) {
+  int S = kMaxStages;
+  while (S >= 2 && smem_bytes<N>(KB, S) > kSmemLimit) --S;
+  return S >= 2 ? S : 0;
 }
 
 PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
@@ -591,9 +613,11 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
   return fn;
 }
 
-template <int N, int S, int LS, typename KT>
-cudaError_t launch_t(const wmd_corpus* c, const Params& p, cudaStream_t s) {
-  const size_t bytes = smem_bytes<N, S, LS>(p.KB);
+template <int N, typename KT>
+cudaError_t launch_t(const wmd_corpus* c, Params p, cudaStream_t s) {
+  p.S = stages_for<N>(p.KB);
+  if (p.S == 0) return cudaErrorNotSupported;
+  const size_t bytes = smem_bytes<N>(p.KB, p.S);
   // the shared-memory limit is raised once per device and size (never inside
   // a stream capture: the first launch of a shape always runs eagerly)
   static std::mutex mu;
@@ -602,45 +626,63 @@ cudaError_t launch_t(const wmd_corpus* c, const Params& p, cudaStream_t s) {
     std::lock_guard<std::mutex> lock(mu);
     const int dev = c->device < 64 ? c->device : 63;
     if (set_bytes[dev] < bytes) {
-      cudaError_t e = cudaFuncSetAttribute(cdist_tc_kernel<N, S, LS, KT>,
+      cudaError_t e = cudaFuncSetAttribute(cdist_tc_kernel<N, KT>,
                                            cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
       if (e != cudaSuccess) return e;
       set_bytes[dev] = bytes;
     }
   }
   const int grid = std::max(1, std::min(p.num_tiles, c->num_sms));
-  const CUtensorMap* map = reinterpret_cast<const CUtensorMap*>(c->tmap_vecs);
-  cdist_tc_kernel<N, S, LS, KT><<<grid, kThreads, bytes, s>>>(*map, p);
+  const CUtensorMap* mh = reinterpret_cast<const CUtensorMap*>(c->tmap_hi);
+  const CUtensorMap* ml = reinterpret_cast<const CUtensorMap*>(c->tmap_lo);
+  cdist_tc_kernel<N, KT><<<grid, kThreads, bytes, s>>>(*mh, *ml, p);
   return cudaGetLastError();
 }
+
+int num_kblocks(const wmd_corpus* c) { return (c->ldv + kKB - 1) / kKB; }
 
 }  // namespace tc
 
 bool make_vecs_tensor_map(wmd_corpus* c) {
   auto fn = tc::encode_fn();
   if (!fn) return false;
-  static_assert(sizeof(CUtensorMap) <= sizeof(c->tmap_vecs), "tensor map storage");
-  CUtensorMap map;
+  static_assert(sizeof(CUtensorMap) <= sizeof(c->tmap_hi), "tensor map storage");
   cuuint64_t dims[2] = {(cuuint64_t)c->ldv, (cuuint64_t)c->V};
-  cuuint64_t strides[1] = {(cuuint64_t)c->ldv * sizeof(float)};
+  cuuint64_t strides[1] = {(cuuint64_t)c->ldv * sizeof(uint16_t)};
   cuuint32_t box[2] = {tc::kKB, tc::kM};
   cuuint32_t estr[2] = {1, 1};
-  CUresult r = fn(&map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, c->vecs, dims, strides, box, estr,
-                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
-                  CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-  if (r != CUDA_SUCCESS) return false;
-  std::memcpy(c->tmap_vecs, &map, sizeof(map));
+  for (int part = 0; part < 2; ++part) {
+    CUtensorMap map;
+    CUresult r = fn(&map, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2, part ? c->vecs_lo : c->vecs_hi,
+                    dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                    CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return false;
+    std::memcpy(part ? c->tmap_lo : c->tmap_hi, &map, sizeof(map));
+  }
   return true;
 }
 
-// Tensor-core path when the query fits one N <= 64 tile and B stays resident
-// in shared memory; returns cudaErrorNotSupported otherwise.
+int cdist_tc_max_width(const wmd_corpus* c) {
+  if (!c->tmap_ok || c->U == 0) return 0;
+  const int KB = tc::num_kblocks(c);
+  if (tc::stages_for<128>(KB)) return 128;
+  if (tc::stages_for<64>(KB)) return 64;
+  if (tc::stages_for<32>(KB)) return 32;
+  if (tc::stages_for<16>(KB)) return 16;
+  return 0;
+}
+
+// Tensor-core path for one slice of at most cdist_tc_max_width(c) query
+// columns (B stays resident in shared memory); cudaErrorNotSupported otherwise.
 cudaError_t launch_cdist_tc(const wmd_corpus* c, const int32_t* q_ids, const float* q_w, int v_r,
                             int VR, float lambda, wmd_precision prec, void* K, int ldk, int kcol0,
                             float* r_out, float* lam_out, int* err, cudaStream_t s) {
-  if (!c->tmap_ok || VR > 64 || c->U == 0) return cudaErrorNotSupported;
+  if (!c->tmap_ok || VR > 128 || c->U == 0) return cudaErrorNotSupported;
   tc::Params p;
-  p.vecs = c->vecs;
+  p.vhi = c->vecs_hi;
+  p.vlo = c->vecs_lo;
+  p.rscale = c->rscale;
   p.ldv = c->ldv;
   p.norms = c->norms;
   p.U = c->U;
@@ -657,20 +699,14 @@ cudaError_t launch_cdist_tc(const wmd_corpus* c, const int32_t* q_ids, const flo
   p.r_out = r_out;
   p.lam_out = lam_out;
   p.num_tiles = (int)((c->U + tc::kM - 1) / tc::kM);
-  p.KB = (c->ldv + tc::kKB - 1) / tc::kKB;
+  p.KB = tc::num_kblocks(c);
+  p.S = 0;
   p.err = err;
   const bool bf = prec == WMD_PREC_BF16_K;
-  const size_t limit = 232448;
-  if (VR <= 16) {
-    if (tc::smem_bytes<16, 8, 3>(p.KB) > limit) return cudaErrorNotSupported;
-    return bf ? tc::launch_t<16, 8, 3, __nv_bfloat16>(c, p, s) : tc::launch_t<16, 8, 3, float>(c, p, s);
-  }
-  if (VR <= 32) {
-    if (tc::smem_bytes<32, 6, 3>(p.KB) > limit) return cudaErrorNotSupported;
-    return bf ? tc::launch_t<32, 6, 3, __nv_bfloat16>(c, p, s) : tc::launch_t<32, 6, 3, float>(c, p, s);
-  }
-  if (tc::smem_bytes<64, 3, 1>(p.KB) > limit) return cudaErrorNotSupported;
-  return bf ? tc::launch_t<64, 3, 1, __nv_bfloat16>(c, p, s) : tc::launch_t<64, 3, 1, float>(c, p, s);
+  if (VR <= 16) return bf ? tc::launch_t<16, __nv_bfloat16>(c, p, s) : tc::launch_t<16, float>(c, p, s);
+  if (VR <= 32) return bf ? tc::launch_t<32, __nv_bfloat16>(c, p, s) : tc::launch_t<32, float>(c, p, s);
+  if (VR <= 64) return bf ? tc::launch_t<64, __nv_bfloat16>(c, p, s) : tc::launch_t<64, float>(c, p, s);
+  return bf ? tc::launch_t<128, __nv_bfloat16>(c, p, s) : tc::launch_t<128, float>(c, p, s);
 }
 
 }  // namespace wmd

@@ -74,6 +74,12 @@ struct wmd_corpus {
   // device, resident
   float* vecs = nullptr;       // V x ldv, rows permuted: active words first
   float* norms = nullptr;      // V, squared row norms (fp64 sum, rounded)
+  // the same rows as an fp16 pair for the tensor cores: row w scaled by 2^e_w
+  // (its largest entry in [2^14, 2^15)), x = hi + lo * 2^-11 up to 2^-22
+  // relative; rscale[w] = 2^-e_w
+  uint16_t* vecs_hi = nullptr; // V x ldv fp16 bits
+  uint16_t* vecs_lo = nullptr; // V x ldv fp16 bits
+  float* rscale = nullptr;     // V
   int32_t* perm = nullptr;     // V: word id -> device row
   int64_t* doc_ptr = nullptr;  // N+1, document-major CSR of c^T
   int32_t* doc_words = nullptr;// nnz, device rows (< U) sorted within a doc
@@ -85,8 +91,9 @@ struct wmd_corpus {
   size_t device_bytes = 0;
   int num_sms = 0;
   int* d_err = nullptr;        // device-side timeout flag (sticky); also read by wmd_query
-  bool tmap_ok = false;        // tensor-core cdist available (TMA descriptor built)
-  alignas(64) unsigned char tmap_vecs[128];  // CUtensorMap of vecs (128-byte tiles of 128 rows)
+  bool tmap_ok = false;        // tensor-core cdist available (TMA descriptors built)
+  alignas(64) unsigned char tmap_hi[128];  // CUtensorMap of vecs_hi (128-byte tiles of 128 rows)
+  alignas(64) unsigned char tmap_lo[128];  // CUtensorMap of vecs_lo
 
   // host path (wmd_query) state, guarded by mu
   std::mutex mu;
@@ -127,6 +134,8 @@ cudaError_t launch_cdist_tc(const wmd_corpus* c, const int32_t* q_ids, const flo
                             int VR, float lambda, wmd_precision prec, void* K, int ldk, int kcol0,
                             float* r_out, float* lam_out, int* err, cudaStream_t s);
 bool make_vecs_tensor_map(wmd_corpus* c);
+// Widest query slice the tensor-core cdist takes for this corpus (0: none).
+int cdist_tc_max_width(const wmd_corpus* c);
 void release_batch_state(const wmd_corpus* c);  // serve.cu: cached batch buffers and graphs
 // One query of a batched loop launch: its padded weights r, output row, first
 // column of its block in the word-major K, and its number of words.
