@@ -333,6 +333,14 @@ __global__ void __launch_bounds__(kThreads, 1)
   const int lane = tid & 31;
   if (tid == 0) TC_TRACE(5, 0);
 
+  // the device rows of the query words (ids -> permutation) are looked up
+  // first, so that these dependent loads overlap the prologue
+  int qrow = -1;
+  if (tid < N && tid < p.v_r) {
+    const int64_t id = p.q_ids[tid];
+    qrow = (id >= 0 && id < p.V) ? p.perm[id] : -2;
+  }
+
   // ---- prologue: barriers and TMEM only, so that the producer starts at once
   if (tid == 0) {
     for (int s = 0; s < S; ++s) {
@@ -364,14 +372,10 @@ __global__ void __launch_bounds__(kThreads, 1)
     // K-major layout (chunk c of row n lands at chunk c ^ (n % 8)): hi rows
     // 0..N-1, lo rows N..2N-1 of every k-block; every thread issues all its
     // loads before its first store
-    const int bt = tid < 256 ? tid : tid - 32;  // 0 .. 287
+    const int bt = tid < 256 ? tid : tid - 32;  // 0 .. 287 (bt = tid below N)
     float qn = 0.f, qrs = 0.f;
     if (bt < N) {
-      int row = -1;
-      if (bt < p.v_r) {
-        const int64_t id = p.q_ids[bt];
-        row = (id >= 0 && id < p.V) ? p.perm[id] : -2;
-      }
+      const int row = qrow;
       qrow_s[bt] = row;
       // these two loads stay in flight behind the B loads below
       if (row >= 0) {
@@ -384,6 +388,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     if (p.r_out && blockIdx.x == 0 && bt < p.VR) p.r_out[bt] = bt < p.v_r ? p.q_w[bt] : 0.f;
     if (p.lam_out && blockIdx.x == 0 && bt == 0) *p.lam_out = p.lambda;
     asm volatile("bar.sync 1, %0;" ::"r"(kBuildThreads) : "memory");
+    if (tid == 0) TC_TRACE(6, 0);
     constexpr int kBatch = 16;
     const int per_row = KB * 8;                 // 16-byte chunks of one row's hi (or lo) part
     const int total = 2 * N * per_row;
@@ -409,6 +414,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         // the producer may stream the vocabulary now: these loads are ahead of it
         asm volatile("" ::: "memory");
         if (lane == 0) atomicAdd(const_cast<int*>(issued_s), 1);
+        if (tid == 0) TC_TRACE(6, 1);
         first = false;
       }
 #pragma unroll
