@@ -55,11 +55,9 @@ void free_corpus_device(wmd_corpus* c) {
   cudaFree(c->doc_ptr);
   cudaFree(c->doc_words);
   cudaFree(c->doc_vals);
-  cudaFree(c->order);
-  cudaFree(c->slots);
   cudaFree(c->d_err);
   for (auto& sc : c->sched)
-    for (auto& s : sc) cudaFree(s.d_items);
+    for (auto& s : sc) cudaFree(s.d_tasks);
   cudaFree(c->ws);
   cudaFree(c->d_qids);
   cudaFree(c->d_out);
@@ -189,8 +187,9 @@ wmd_status wmd_corpus_load(const float* vecs, int64_t V, int32_t d, const int64_
   c->N = N;
   c->nnz = nnz;
   c->d = d;
-  // rows padded to 128 bytes: every 32-float k-block of a row is one whole
-  // cache line for the TMA tiles of the cdist kernel
+  // rows padded to 32 elements: 128-byte float32 rows for the CUDA-core
+  // cdist, and 16-byte aligned fp16 rows (64-byte strides) for the TMA tiles
+  // of the tensor-core cdist
   c->ldv = (int32_t)align_up((size_t)d, 32);
 
   // active vocabulary first: device row of word w
@@ -266,6 +265,12 @@ wmd_status wmd_corpus_load(const float* vecs, int64_t V, int32_t d, const int64_
       dvals[pos] = val[e];
     }
 
+  for (int64_t j = 0; j < N; ++j)
+    if (dptr[j + 1] - dptr[j] >= (int64_t(1) << kTaskWShift)) {
+      delete c;
+      return set_error(WMD_ERR_UNSUPPORTED, "a document has 2^24 or more distinct words");
+    }
+
   // documents by decreasing length (longest first), ties by id
   std::vector<int32_t> order(N);
   std::iota(order.begin(), order.end(), 0);
@@ -285,13 +290,6 @@ wmd_status wmd_corpus_load(const float* vecs, int64_t V, int32_t d, const int64_
   if (e == cudaSuccess) e = upload(&c->doc_ptr, dptr.data(), dptr.size(), &bytes);
   if (e == cudaSuccess) e = upload(&c->doc_words, dwords.data(), dwords.size(), &bytes);
   if (e == cudaSuccess) e = upload(&c->doc_vals, dvals.data(), dvals.size(), &bytes);
-  if (e == cudaSuccess) e = upload(&c->order, order.data(), order.size(), &bytes);
-  if (e == cudaSuccess) {
-    std::vector<SlotInfo> slots(N);
-    for (int64_t i = 0; i < N; ++i)
-      slots[i] = SlotInfo{dptr[order[i]], (int32_t)(dptr[order[i] + 1] - dptr[order[i]]), order[i]};
-    e = upload(&c->slots, slots.data(), slots.size(), &bytes);
-  }
   if (e == cudaSuccess) {
     const int zero = 0;
     e = upload(&c->d_err, &zero, 1, &bytes);
@@ -317,7 +315,8 @@ wmd_status wmd_corpus_load(const float* vecs, int64_t V, int32_t d, const int64_
         while (W < nw && n > W * rpw) W *= 2;
         return W;
       };
-      std::vector<LoopItem> items;
+      std::vector<WarpTask> tasks;
+      int32_t n_items = 0;
       int64_t i = 0;
       while (i < N) {
         const int64_t n = dptr[order[i] + 1] - dptr[order[i]];
@@ -325,12 +324,22 @@ wmd_status wmd_corpus_load(const float* vecs, int64_t V, int32_t d, const int64_
         const int per = nw / W;
         int64_t j = i;
         while (j < N && team(dptr[order[j] + 1] - dptr[order[j]]) == W) ++j;
-        for (int64_t b = i; b < j; b += per)
-          items.push_back(LoopItem{W, (int32_t)b, (int32_t)std::min<int64_t>(b + per, j), 0});
+        for (int64_t b = i; b < j; b += per, ++n_items) {
+          for (int warp = 0; warp < nw; ++warp) {
+            const int64_t slot = b + warp / W;
+            if (slot < std::min<int64_t>(b + per, j)) {
+              const int32_t d = order[slot];
+              const int32_t len = (int32_t)(dptr[d + 1] - dptr[d]);
+              tasks.push_back(WarpTask{dptr[d], len | (W << kTaskWShift), d});
+            } else {
+              tasks.push_back(WarpTask{0, 0, 0});
+            }
+          }
+        }
         i = j;
       }
-      c->sched[cls][var].n_items = (int32_t)items.size();
-      e = upload(&c->sched[cls][var].d_items, items.data(), items.size(), &bytes);
+      c->sched[cls][var].n_items = n_items;
+      e = upload(&c->sched[cls][var].d_tasks, tasks.data(), tasks.size(), &bytes);
     }
   }
   c->device_bytes = bytes;

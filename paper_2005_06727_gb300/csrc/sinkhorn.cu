@@ -21,10 +21,10 @@
 // load per 4 columns reads 16 PI contiguous bytes per row group.
 //
 // K .* M for the final step is recovered from the K block already in
-// registers: M = -ln(K) / lambda, exact for K = 1 (the query's own word) and
-// within a few float32 ulps of m while K is a normal float (the cdist kernel
-// computed K = exp(-lambda m) in float32, so -ln K returns lambda m up to the
-// rounding of that product and of expf).
+// registers: M = -ln(K) / lambda = -log2(K) ln 2 / lambda, exact for K = 1
+// (the query's own word) and within a few float32 ulps of m while K is a
+// normal float (the cdist kernel computed K = exp(-lambda m) in float32, so
+// -ln K returns lambda m up to the rounding of that product and of expf).
 #include "wmd_internal.h"
 
 namespace wmd {
@@ -41,8 +41,7 @@ struct LoopParams {
   const float* lam;  // lambda of the single query (written by the cdist kernel)
   int v_r;
   int T;
-  const LoopItem* items;
-  const SlotInfo* slots;
+  const WarpTask* tasks;  // [item][warp]
   double* out;
   const int* err;  // set by a cdist kernel that gave up waiting: results are NaN
   const QueryDesc* queries;  // blockIdx.y selects the query; NULL: the fields above
@@ -77,11 +76,19 @@ __device__ __forceinline__ void team_barrier(int id, int nthreads) {
   asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
 }
 
-// K[w,i] (-ln K[w,i]) = lambda K[w,i] M[w,i]; 0 where K underflowed to a
-// subnormal or zero.
-__device__ __forceinline__ float k_times_neg_logk(float k) {
-  return k >= 1.17549435e-38f ? -k * __logf(k) : 0.f;
+// K log2 K = -lambda K M / ln 2 for two entries of K.  K below the smallest
+// normal float is clamped there, so that its term stays finite (and below
+// 1.5e-36 in magnitude).
+__device__ __forceinline__ float2 k_log2k(float2 k) {
+  // opaque to the compiler, so that the logarithms stay in the last pass
+  // instead of being hoisted out of the iterations (96 live values per lane
+  // would not fit in registers)
+  asm volatile("" : "+f"(k.x), "+f"(k.y));
+  const float2 l = make_float2(__log2f(fmaxf(k.x, 1.17549435e-38f)), __log2f(fmaxf(k.y, 1.17549435e-38f)));
+  return __fmul2_rn(k, l);
 }
+
+constexpr double kLn2 = 0.69314718055994530942;  // ln 2
 
 // Knuth's TwoSum: s + e == a + b exactly (s = fl(a + b)).
 __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
@@ -214,18 +221,15 @@ __device__ __forceinline__ void solve(const LoopParams& p, const TeamCtx& t) {
           for (int q = 0; q < C2; ++q) xp[q] = __ffma2_rn(kt[rI][q], vv, xp[q]);
         }
       } else {
-        // final reduction: sum_w v_w sum_i u_i K[w, i] (-ln K[w, i]) (= lambda
-        // times the WMD); a lane's few terms are summed in float32, lanes and
-        // warps in float64
+        // final reduction: sum_w v_w sum_i u_i K[w, i] log2 K[w, i] (= -lambda /
+        // ln 2 times the WMD); a lane's few terms are summed in float32, lanes
+        // in double-float and warps in float64
 #pragma unroll
         for (int rI = 0; rI < R; ++rI) {
-          float tt = 0.f;
+          float2 tt = make_float2(0.f, 0.f);
 #pragma unroll
-          for (int q = 0; q < C2; ++q) {
-            tt = fmaf(u[q].x, k_times_neg_logk(kt[rI][q].x), tt);
-            tt = fmaf(u[q].y, k_times_neg_logk(kt[rI][q].y), tt);
-          }
-          wacc = fmaf(v[rI], tt, wacc);
+          for (int q = 0; q < C2; ++q) tt = __ffma2_rn(u[q], k_log2k(kt[rI][q]), tt);
+          wacc = fmaf(v[rI], tt.x + tt.y, wacc);
         }
       }
     }
@@ -289,10 +293,10 @@ __device__ __forceinline__ void solve(const LoopParams& p, const TeamCtx& t) {
     if (t.kw == 0 && t.lane == 0) {
       double acc = 0.0;
       for (int k2 = 0; k2 < t.W; ++k2) acc += t.wred[t.team * t.W + k2];
-      t.q.out[t.doc] = acc / (double)t.q.lambda;
+      t.q.out[t.doc] = acc * (-kLn2 / (double)t.q.lambda);
     }
   } else if (t.lane == 0) {
-    t.q.out[t.doc] = wsum / (double)t.q.lambda;
+    t.q.out[t.doc] = wsum * (-kLn2 / (double)t.q.lambda);
   }
 }
 
@@ -322,17 +326,14 @@ __global__ void __launch_bounds__(NW * 32, MINB) sinkhorn_fused_kernel(LoopParam
   t.lane = threadIdx.x & 31;
   t.pi = t.lane % PI;
   t.pw = t.lane / PI;
-  const LoopItem item = p.items[blockIdx.x];
-  t.W = item.W;
+  const WarpTask task = p.tasks[blockIdx.x * NW + t.warp];
+  t.W = task.n_w >> kTaskWShift;
+  if (t.W == 0) return;  // no team in this item (whole teams leave together)
   t.team = t.warp / t.W;
   t.kw = t.warp - t.team * t.W;
-  const int slot = item.begin + t.team;
-  if (t.team >= NW / t.W || slot >= item.end) return;  // whole team leaves together
-
-  const SlotInfo si = p.slots[slot];
-  t.doc = si.doc;
-  t.beg = si.beg;
-  t.n = si.n;
+  t.doc = task.doc;
+  t.beg = task.beg;
+  t.n = task.n_w & ((1 << kTaskWShift) - 1);
   if (*p.err) {
     if (t.kw == 0 && t.lane == 0) t.q.out[t.doc] = __longlong_as_double(0x7ff8000000000000ll);
     return;
@@ -445,8 +446,7 @@ static LoopParams base_params(const wmd_corpus* c, int cls, int var, const void*
   p.lam = nullptr;
   p.v_r = 0;
   p.T = T;
-  p.items = c->sched[cls][var].d_items;
-  p.slots = c->slots;
+  p.tasks = c->sched[cls][var].d_tasks;
   p.out = nullptr;
   p.err = c->d_err;
   p.queries = nullptr;

@@ -41,26 +41,20 @@ constexpr int kClassVariants[kNumClasses] = {1, 1, 2, 2, 2, 2};
 int rows_per_warp(int cls, int var);
 int warps_per_cta(int cls, int var);  // 4 or 8
 
-// One CTA work item of the fused loop: a team size W (warps per document),
-// and the range [begin, end) of the length-sorted document order that the
-// CTA's NW/W teams take, one document each (NW = warps per CTA).
-struct LoopItem {
-  int32_t W;
-  int32_t begin;
-  int32_t end;
-  int32_t pad;
-};
-
-// Where one slot of the length-sorted document order lives in the
-// document-major CSR (one 16-byte load at team start).
-struct SlotInfo {
+// The task of one warp in one CTA work item of the fused loop: the document
+// its team solves (its range in the document-major CSR, its length and id)
+// and the team size W (warps per document).  A CTA's NW/W teams take
+// consecutive documents of the length-sorted order; W = 0 marks a warp with
+// no team in the item.  One 16-byte load per warp at item start.
+struct WarpTask {
   int64_t beg;
-  int32_t n;
+  int32_t n_w;  // n | W << 24
   int32_t doc;
 };
+constexpr int kTaskWShift = 24;
 
 struct Schedule {
-  LoopItem* d_items = nullptr;
+  WarpTask* d_tasks = nullptr;  // n_items x (warps per CTA)
   int32_t n_items = 0;
 };
 
@@ -84,8 +78,6 @@ struct wmd_corpus {
   int64_t* doc_ptr = nullptr;  // N+1, document-major CSR of c^T
   int32_t* doc_words = nullptr;// nnz, device rows (< U) sorted within a doc
   float* doc_vals = nullptr;   // nnz
-  int32_t* order = nullptr;    // N, documents by decreasing length
-  wmd::SlotInfo* slots = nullptr;  // N, {beg, n, doc} of order[i]
   wmd::Schedule sched[wmd::kNumClasses][wmd::kMaxVariants];
   int loop_variant[wmd::kNumClasses][2] = {};  // chosen variant per class and precision
   size_t device_bytes = 0;
