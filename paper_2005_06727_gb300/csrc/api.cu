@@ -60,7 +60,6 @@ void free_corpus_device(wmd_corpus* c) {
     for (auto& s : sc) cudaFree(s.d_tasks);
   cudaFree(c->ws);
   cudaFree(c->d_qids);
-  cudaFree(c->d_out);
   cudaFreeHost(c->h_stage);
   cudaFreeHost(c->h_out);
   for (auto& g : c->qgraphs)
@@ -399,8 +398,12 @@ wmd_status wmd_build_kernel_matrix(wmd_corpus* c, const int32_t* d_q_ids, const 
   return WMD_OK;
 }
 
-wmd_status wmd_sinkhorn_loop(wmd_corpus* c, int32_t v_r, int32_t max_iter, wmd_precision prec,
-                             void* d_ws, size_t ws_bytes, double* d_out, void* stream) {
+namespace {
+
+// The fused loop of wmd_sinkhorn_loop; err_out (optional, device-visible)
+// receives the cdist timeout word.
+wmd_status sinkhorn_loop(wmd_corpus* c, int32_t v_r, int32_t max_iter, wmd_precision prec,
+                         void* d_ws, size_t ws_bytes, double* d_out, int* err_out, void* stream) {
   wmd_status st = check_query_args(c, v_r, 1.f, max_iter);
   if (st != WMD_OK) return st;
   if (!d_out && c->N > 0) return set_error(WMD_ERR_INVALID_ARG, "d_out is NULL");
@@ -412,8 +415,15 @@ wmd_status wmd_sinkhorn_loop(wmd_corpus* c, int32_t v_r, int32_t max_iter, wmd_p
   char* ws = static_cast<char*>(d_ws);
   const float* r = reinterpret_cast<const float*>(ws + L.r_off);
   WMD_CUDA_TRY(launch_loop(c, cls, ws + L.k_off, VR, 0, r, r + VR, v_r, max_iter, prec, d_out,
-                           static_cast<cudaStream_t>(stream)));
+                           err_out, static_cast<cudaStream_t>(stream)));
   return WMD_OK;
+}
+
+}  // namespace
+
+wmd_status wmd_sinkhorn_loop(wmd_corpus* c, int32_t v_r, int32_t max_iter, wmd_precision prec,
+                             void* d_ws, size_t ws_bytes, double* d_out, void* stream) {
+  return sinkhorn_loop(c, v_r, max_iter, prec, d_ws, ws_bytes, d_out, nullptr, stream);
 }
 
 wmd_status wmd_query_device(wmd_corpus* c, const int32_t* d_q_ids, const float* d_q_w,
@@ -527,7 +537,7 @@ wmd_status wmd_query(wmd_corpus* c, const int32_t* q_ids, const float* q_w, int3
   DeviceGuard g(c->device);
   if (!c->stream) WMD_CUDA_TRY(cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking));
   if (!c->h_stage)
-    WMD_CUDA_TRY(cudaMallocHost(&c->h_stage, (2 * WMD_MAX_VR + 4) * sizeof(int32_t)));
+    WMD_CUDA_TRY(cudaHostAlloc(&c->h_stage, (2 * WMD_MAX_VR + 4) * sizeof(int32_t), cudaHostAllocMapped));
   // compact straight into the pinned staging block: ids, then weights
   int32_t* h_ids = c->h_stage;
   float* h_w = reinterpret_cast<float*>(c->h_stage + WMD_MAX_VR);
@@ -554,34 +564,53 @@ wmd_status wmd_query(wmd_corpus* c, const int32_t* q_ids, const float* q_w, int3
   if (!c->d_qids) {
     WMD_CUDA_TRY(cudaMalloc(&c->d_qids, 2 * WMD_MAX_VR * sizeof(int32_t)));
     c->d_qw = reinterpret_cast<float*>(c->d_qids + WMD_MAX_VR);
-    WMD_CUDA_TRY(cudaMalloc(&c->d_out, (std::max<int64_t>(c->N, 1) + 1) * sizeof(double)));
-    WMD_CUDA_TRY(cudaMallocHost(&c->h_out, std::max<int64_t>(c->N, 1) * sizeof(double)));
+    WMD_CUDA_TRY(cudaHostAlloc(&c->h_out, std::max<int64_t>(c->N, 1) * sizeof(double), cudaHostAllocMapped));
   }
   // one copy for ids and weights (the staging block is contiguous)
   if (v_r < WMD_MAX_VR) std::memmove(h_ids + v_r, h_w, v_r * sizeof(float));
   float* d_w = reinterpret_cast<float*>(c->d_qids + v_r);
 
-  // the whole sequence (H2D, cdist, loop, D2H of results and error word)
-  // runs eagerly on the first use of a query shape and from a captured CUDA
-  // graph from the second use on
+  // the results and the error word reach host memory directly: the loop
+  // kernel writes them into the mapped pinned blocks (no copy back)
+  double* dh_out = nullptr;
+  int32_t* dh_stage = nullptr;
+  WMD_CUDA_TRY(cudaHostGetDevicePointer(reinterpret_cast<void**>(&dh_out), c->h_out, 0));
+  WMD_CUDA_TRY(cudaHostGetDevicePointer(reinterpret_cast<void**>(&dh_stage), c->h_stage, 0));
+  int* dh_err = dh_stage + 2 * WMD_MAX_VR;
+  // a caller buffer that is pinned and mapped into the device's address space
+  // takes the results directly (no copy out of the staging block)
+  bool direct = false;
+  if (c->N > 0) {
+    cudaPointerAttributes pa;
+    if (cudaPointerGetAttributes(&pa, out_wmd) == cudaSuccess) {
+      if (pa.type == cudaMemoryTypeHost && pa.devicePointer) {
+        dh_out = static_cast<double*>(pa.devicePointer);
+        direct = true;
+      }
+    } else {
+      cudaGetLastError();
+    }
+  }
+
+  // the whole sequence (H2D of the query, cdist, loop) runs eagerly on the
+  // first use of a query shape and from a captured CUDA graph from the second
+  // use on
   const int cls = vr_class(v_r);
   const int variant = c->loop_variant[cls][prec == WMD_PREC_BF16_K];
   auto enqueue = [&]() -> wmd_status {
     WMD_CUDA_TRY(cudaMemcpyAsync(c->d_qids, h_ids, 2 * v_r * sizeof(int32_t),
                                  cudaMemcpyHostToDevice, c->stream));
-    wmd_status s2 = wmd_query_device(c, c->d_qids, d_w, v_r, lambda, max_iter, prec, c->ws,
-                                     c->ws_bytes, c->d_out, c->stream);
-    if (s2 != WMD_OK) return s2;
-    if (c->N > 0)
-      WMD_CUDA_TRY(cudaMemcpyAsync(c->h_out, c->d_out, c->N * sizeof(double),
-                                   cudaMemcpyDeviceToHost, c->stream));
-    WMD_CUDA_TRY(cudaMemcpyAsync(h_err, c->d_err, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
-    return WMD_OK;
+    wmd_status s2 = check_query_args(c, v_r, lambda, max_iter);
+    if (s2 == WMD_OK)
+      s2 = wmd_build_kernel_matrix(c, c->d_qids, d_w, v_r, lambda, prec, c->ws, c->ws_bytes, c->stream);
+    if (s2 == WMD_OK)
+      s2 = sinkhorn_loop(c, v_r, max_iter, prec, c->ws, c->ws_bytes, dh_out, dh_err, c->stream);
+    return s2;
   };
   wmd_corpus::QueryGraph* qg = nullptr;
   for (auto& g2 : c->qgraphs)
     if (g2.v_r == v_r && g2.T == max_iter && g2.prec == (int)prec && g2.variant == variant &&
-        g2.lambda == lambda)
+        g2.lambda == lambda && g2.dout == dh_out)
       qg = &g2;
   if (!qg) {
     if (c->qgraphs.size() >= 8) {
@@ -592,7 +621,8 @@ wmd_status wmd_query(wmd_corpus* c, const int32_t* q_ids, const float* q_w, int3
       if (oldest->exec) cudaGraphExecDestroy(oldest->exec);
       c->qgraphs.erase(oldest);
     }
-    c->qgraphs.push_back(wmd_corpus::QueryGraph{v_r, max_iter, (int)prec, variant, lambda, 0, nullptr, 0});
+    c->qgraphs.push_back(
+        wmd_corpus::QueryGraph{v_r, max_iter, (int)prec, variant, lambda, dh_out, 0, nullptr, 0});
     qg = &c->qgraphs.back();
   }
   qg->last = ++c->qtick;
@@ -624,17 +654,18 @@ wmd_status wmd_query(wmd_corpus* c, const int32_t* q_ids, const float* q_w, int3
   }
   qg->uses += 1;
   WMD_CUDA_TRY(cudaStreamSynchronize(c->stream));
-  if (c->N > 0) std::memcpy(out_wmd, c->h_out, c->N * sizeof(double));
-  const int err = *h_err;
+  if (c->N > 0 && !direct) std::memcpy(out_wmd, c->h_out, c->N * sizeof(double));
+  const int err = *reinterpret_cast<volatile int32_t*>(h_err);
   if (err) {
-    static const char* roles[] = {"?", "producer (stage free)", "converter (tile landed)",
-                                  "MMA (accumulator free)", "MMA (tile landed or converted)",
-                                  "epilogue (accumulator full)", "converter (lo slot free)"};
+    static const char* roles[] = {"?", "producer (stage free)", "?",
+                                  "MMA (accumulator free)", "MMA (tile landed)",
+                                  "epilogue (accumulator full)", "?",
+                                  "producer (query gathers in flight)"};
     const int role = (err >> 24) & 0x3f;
     char msg[160];
     std::snprintf(msg, sizeof msg,
                   "a device-side wait in the cdist kernel timed out: %s, iteration %d (code 0x%08x)",
-                  roles[role < 7 ? role : 0], err & 0xffffff, (unsigned)err);
+                  roles[role < 8 ? role : 0], err & 0xffffff, (unsigned)err);
     return set_error(WMD_ERR_TIMEOUT, msg);
   }
   return WMD_OK;

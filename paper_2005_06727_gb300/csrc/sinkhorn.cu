@@ -44,6 +44,7 @@ struct LoopParams {
   const WarpTask* tasks;  // [item][warp]
   double* out;
   const int* err;  // set by a cdist kernel that gave up waiting: results are NaN
+  int* err_out;    // optional copy of *err for the host (block 0 writes it)
   const QueryDesc* queries;  // blockIdx.y selects the query; NULL: the fields above
 };
 
@@ -326,6 +327,7 @@ __global__ void __launch_bounds__(NW * 32, MINB) sinkhorn_fused_kernel(LoopParam
   t.lane = threadIdx.x & 31;
   t.pi = t.lane % PI;
   t.pw = t.lane / PI;
+  if (p.err_out && blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) *p.err_out = *p.err;
   const WarpTask task = p.tasks[blockIdx.x * NW + t.warp];
   t.W = task.n_w >> kTaskWShift;
   if (t.W == 0) return;  // no team in this item (whole teams leave together)
@@ -449,13 +451,14 @@ static LoopParams base_params(const wmd_corpus* c, int cls, int var, const void*
   p.tasks = c->sched[cls][var].d_tasks;
   p.out = nullptr;
   p.err = c->d_err;
+  p.err_out = nullptr;
   p.queries = nullptr;
   return p;
 }
 
 cudaError_t launch_loop(const wmd_corpus* c, int cls, const void* K, int ldk, int kcol0,
                         const float* r, const float* lam, int v_r, int T, wmd_precision prec,
-                        double* out, cudaStream_t s) {
+                        double* out, int* err_out, cudaStream_t s) {
   const int var = c->loop_variant[cls][prec == WMD_PREC_BF16_K];
   LoopParams p = base_params(c, cls, var, K, ldk, T);
   p.kcol0 = kcol0;
@@ -463,6 +466,7 @@ cudaError_t launch_loop(const wmd_corpus* c, int cls, const void* K, int ldk, in
   p.lam = lam;
   p.v_r = v_r;
   p.out = out;
+  p.err_out = err_out;
   const int n_items = c->sched[cls][var].n_items;
   if (prec == WMD_PREC_BF16_K) return dispatch_loop<__nv_bfloat16>(cls, var, p, n_items, 1, s);
   return dispatch_loop<float>(cls, var, p, n_items, 1, s);

@@ -94,13 +94,13 @@ struct wmd_corpus {
   size_t ws_bytes = 0;
   int32_t* d_qids = nullptr;   // WMD_MAX_VR ids followed by WMD_MAX_VR weights
   float* d_qw = nullptr;       // = d_qids + WMD_MAX_VR
-  int32_t* h_stage = nullptr;  // pinned: ids, weights, error word
-  double* d_out = nullptr;     // N doubles followed by one int error word (host path)
-  double* h_out = nullptr;     // pinned N doubles (host path, graph replay)
+  int32_t* h_stage = nullptr;  // pinned: ids, weights, error word (mapped: the loop kernel writes the error word)
+  double* h_out = nullptr;     // pinned, mapped N doubles: the loop kernel writes the results here (host path)
   // captured host-path sequences, keyed by query shape (second use onwards)
   struct QueryGraph {
     int v_r, T, prec, variant;
     float lambda;
+    double* dout;  // where the loop kernel writes the results
     int uses;
     cudaGraphExec_t exec;
     uint64_t last;
@@ -141,8 +141,9 @@ struct QueryDesc {
 cudaError_t launch_loop_batch(const wmd_corpus* c, int cls, const void* K, int ldk,
                               const QueryDesc* d_queries, int nq, int T, wmd_precision prec,
                               cudaStream_t s);
+// err_out (optional, device-visible): receives the cdist timeout word
 cudaError_t launch_loop(const wmd_corpus* c, int cls, const void* K, int ldk, int kcol0,
                         const float* r, const float* lam, int v_r, int T, wmd_precision prec,
-                        double* out, cudaStream_t s);
+                        double* out, int* err_out, cudaStream_t s);
 
 }  // namespace wmd

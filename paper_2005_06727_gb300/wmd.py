@@ -124,7 +124,8 @@ def _check(st: int):
 
 
 def _ptr(a: np.ndarray):
-    return a.ctypes.data_as(C.c_void_p) if a.size else None
+    # the raw address: the arguments are declared c_void_p, which takes an int
+    return a.ctypes.data if a.size else None
 
 
 def loop_variant_count(v_r: int) -> int:

@@ -63,6 +63,24 @@ def test_graph_replay_with_new_words_and_lambdas(wmd, setup):
     assert not np.array_equal(first, got)
 
 
+def test_query_into_pinned_output_buffers(wmd, setup):
+    """wmd_query writes straight into a caller buffer that is pinned and mapped
+    (and through its own staging block otherwise): every route, first use and
+    graph replay alike, gives the same bits."""
+    torch = pytest.importorskip("torch")
+    _, c, corpus, queries = setup
+    q_ids, q_w = queries[6]
+    ref = corpus.query(q_ids, q_w, 10.0, 15)  # pageable output
+    pinned = [torch.empty(c.N, dtype=torch.float64).pin_memory().numpy() for _ in range(2)]
+    for _ in range(3):  # eager, capture, replay
+        for buf in pinned:
+            buf.fill(np.nan)
+            corpus.query(q_ids, q_w, 10.0, 15, out=buf)
+            assert np.array_equal(buf, ref)
+    again = corpus.query(q_ids, q_w, 10.0, 15)
+    assert np.array_equal(again, ref)
+
+
 def test_batch_against_oracle(wmd, setup):
     vecs, c, corpus, queries = setup
     sel = [0, 6, 11, 15, 20]
