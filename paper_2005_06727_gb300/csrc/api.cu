@@ -393,8 +393,9 @@ wmd_status wmd_build_kernel_matrix(wmd_corpus* c, const int32_t* d_q_ids, const 
   char* ws = static_cast<char*>(d_ws);
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   float* r = reinterpret_cast<float*>(ws + L.r_off);
+  const L2Prefetch pf = loop_inputs(c, vr_class(v_r), prec);
   WMD_CUDA_TRY(launch_cdist(c, d_q_ids, d_q_w, v_r, VR, lambda, prec, ws + L.k_off, VR, 0, r,
-                            r + VR, s));
+                            r + VR, &pf, s));
   return WMD_OK;
 }
 

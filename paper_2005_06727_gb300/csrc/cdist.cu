@@ -230,7 +230,7 @@ cudaError_t dispatch_cdist(const wmd_corpus* c, const int32_t* q_ids, const floa
 
 cudaError_t launch_cdist(const wmd_corpus* c, const int32_t* q_ids, const float* q_w, int v_r,
                          int VR, float lambda, wmd_precision prec, void* K, int ldk, int kcol0,
-                         float* r_out, float* lam_out, cudaStream_t s) {
+                         float* r_out, float* lam_out, const L2Prefetch* pf, cudaStream_t s) {
   // tensor cores (cdist_tc.cu): the query's columns in slices as wide as the
   // resident query operand allows (128 at most); every slice streams the
   // active vocabulary once
@@ -238,7 +238,7 @@ cudaError_t launch_cdist(const wmd_corpus* c, const int32_t* q_ids, const float*
   const int width = cdist_tc_max_width(c);
   if (width >= VR || (width > 0 && VR <= 16)) {
     e = launch_cdist_tc(c, q_ids, q_w, v_r, VR, lambda, prec, K, ldk, kcol0, r_out, lam_out,
-                        c->d_err, s);
+                        c->d_err, pf, s);
   } else if (width > 0) {
     const size_t esz = prec == WMD_PREC_BF16_K ? 2 : 4;
     for (int j0 = 0; j0 < VR; j0 += width) {
@@ -246,7 +246,8 @@ cudaError_t launch_cdist(const wmd_corpus* c, const int32_t* q_ids, const float*
       // a slice past the last query word still writes its zero padding
       e = launch_cdist_tc(c, q_ids + std::min(j0, v_r), q_w + std::min(j0, v_r), vr_slice, width,
                           lambda, prec, static_cast<char*>(K) + (size_t)j0 * esz, ldk, kcol0,
-                          r_out ? r_out + j0 : nullptr, j0 == 0 ? lam_out : nullptr, c->d_err, s);
+                          r_out ? r_out + j0 : nullptr, j0 == 0 ? lam_out : nullptr, c->d_err,
+                          j0 == 0 ? pf : nullptr, s);
       if (e != cudaSuccess) break;
     }
   }

@@ -76,6 +76,10 @@ struct Params {
   int KB;
   int S;  // stages of the A ring
   int* err;
+  // read-only data the next kernel (the fused loop) starts from: prefetched
+  // into L2 with the evict-last priority while the vocabulary streams
+  const void* pf_ptr[3];
+  size_t pf_bytes[3];
 };
 
 #ifdef WMD_TC_TRACE
@@ -527,6 +531,17 @@ __global__ void __launch_bounds__(kThreads, 1)
       while (!mbar_try_wait(drain, 0) && clock64() - t0 < kWaitCycles) {
       }
     }
+    __syncwarp();
+    // the vocabulary stream is over; while the last epilogue runs, the warp
+    // prefetches this CTA's share of the next kernel's read-only inputs into
+    // L2 (evict-last), one 128-byte line per prefetch
+    for (int r = 0; r < 3; ++r) {
+      const char* base = static_cast<const char*>(p.pf_ptr[r]);
+      if (!base) continue;
+      const size_t lines = (p.pf_bytes[r] + 127) / 128;
+      for (size_t l = (size_t)blockIdx.x * 32 + lane; l < lines; l += (size_t)gridDim.x * 32)
+        asm volatile("prefetch.global.L2::evict_last [%0];" ::"l"(base + l * 128));
+    }
   } else {
     // ---------------------------------------------------------------- epilogue
     // warp w reads TMEM lanes 32 (w % 4) .. + 31 (its rows) and the columns
@@ -683,7 +698,8 @@ int cdist_tc_max_width(const wmd_corpus* c) {
 // columns (B stays resident in shared memory); cudaErrorNotSupported otherwise.
 cudaError_t launch_cdist_tc(const wmd_corpus* c, const int32_t* q_ids, const float* q_w, int v_r,
                             int VR, float lambda, wmd_precision prec, void* K, int ldk, int kcol0,
-                            float* r_out, float* lam_out, int* err, cudaStream_t s) {
+                            float* r_out, float* lam_out, int* err, const L2Prefetch* pf,
+                            cudaStream_t s) {
   if (!c->tmap_ok || VR > 128 || c->U == 0) return cudaErrorNotSupported;
   tc::Params p;
   p.vhi = c->vecs_hi;
@@ -708,6 +724,10 @@ cudaError_t launch_cdist_tc(const wmd_corpus* c, const int32_t* q_ids, const flo
   p.KB = tc::num_kblocks(c);
   p.S = 0;
   p.err = err;
+  for (int r = 0; r < 3; ++r) {
+    p.pf_ptr[r] = pf ? pf->ptr[r] : nullptr;
+    p.pf_bytes[r] = pf ? pf->bytes[r] : 0;
+  }
   const bool bf = prec == WMD_PREC_BF16_K;
   if (VR <= 16) return bf ? tc::launch_t<16, __nv_bfloat16>(c, p, s) : tc::launch_t<16, float>(c, p, s);
   if (VR <= 32) return bf ? tc::launch_t<32, __nv_bfloat16>(c, p, s) : tc::launch_t<32, float>(c, p, s);

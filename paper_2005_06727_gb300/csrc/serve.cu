@@ -200,10 +200,12 @@ wmd_status enqueue_batch(wmd_corpus* c, Slot& s, const std::vector<const Req*>& 
   WMD_CUDA_TRY(cudaMemcpyAsync(s.d_ids, s.h_ids, L.words * sizeof(int32_t), cudaMemcpyHostToDevice, st));
   WMD_CUDA_TRY(cudaMemcpyAsync(s.d_w, s.h_w, L.words * sizeof(float), cudaMemcpyHostToDevice, st));
   WMD_CUDA_TRY(cudaMemcpyAsync(s.d_desc, s.h_desc, nq * sizeof(QueryDesc), cudaMemcpyHostToDevice, st));
+  // the first cdist launch prefetches the loop's document CSR into L2
+  const L2Prefetch pf = loop_inputs(c, vr_class(qs[0]->v_r), prec);
   for (size_t q = 0; q < nq; ++q)
     WMD_CUDA_TRY(launch_cdist(c, s.d_ids + word_off[q], s.d_w + word_off[q], qs[q]->v_r, qs[q]->VR,
                               qs[q]->lambda, prec, ws + L.k_off, L.ldk, L.col0[q],
-                              r_all + L.col0[q], nullptr, st));
+                              r_all + L.col0[q], nullptr, q == 0 ? &pf : nullptr, st));
   for (int cls = 0; cls < kNumClasses; ++cls) {
     const int n = L.cls_begin[cls + 1] - L.cls_begin[cls];
     if (n)

@@ -435,6 +435,19 @@ int warps_per_cta(int cls, int var) {
   }
 }
 
+L2Prefetch loop_inputs(const wmd_corpus* c, int cls, wmd_precision prec) {
+  L2Prefetch pf{};
+  if (cls < 0 || cls >= kNumClasses) return pf;
+  const int var = c->loop_variant[cls][prec == WMD_PREC_BF16_K];
+  pf.ptr[0] = c->sched[cls][var].d_tasks;
+  pf.bytes[0] = (size_t)c->sched[cls][var].n_items * warps_per_cta(cls, var) * sizeof(WarpTask);
+  pf.ptr[1] = c->doc_words;
+  pf.bytes[1] = (size_t)c->nnz * sizeof(int32_t);
+  pf.ptr[2] = c->doc_vals;
+  pf.bytes[2] = (size_t)c->nnz * sizeof(float);
+  return pf;
+}
+
 static LoopParams base_params(const wmd_corpus* c, int cls, int var, const void* K, int ldk,
                               int T) {
   LoopParams p;

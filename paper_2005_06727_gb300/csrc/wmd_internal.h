@@ -118,13 +118,24 @@ struct WsLayout {
 };
 WsLayout ws_layout(const wmd_corpus* c, int VR, wmd_precision prec);
 
+// Read-only regions (up to three) that the kernel after cdist starts from;
+// the tensor-core cdist prefetches them into L2 while it streams.
+struct L2Prefetch {
+  const void* ptr[3];
+  size_t bytes[3];
+};
+// The fused loop's inputs for query class cls: its work items and the
+// document-major CSR.
+L2Prefetch loop_inputs(const wmd_corpus* c, int cls, wmd_precision prec);
+
 // Kernel launchers (cdist.cu / sinkhorn.cu).
 cudaError_t launch_cdist(const wmd_corpus* c, const int32_t* q_ids, const float* q_w, int v_r,
                          int VR, float lambda, wmd_precision prec, void* K, int ldk, int kcol0,
-                         float* r_out, float* lam_out, cudaStream_t s);
+                         float* r_out, float* lam_out, const L2Prefetch* pf, cudaStream_t s);
 cudaError_t launch_cdist_tc(const wmd_corpus* c, const int32_t* q_ids, const float* q_w, int v_r,
                             int VR, float lambda, wmd_precision prec, void* K, int ldk, int kcol0,
-                            float* r_out, float* lam_out, int* err, cudaStream_t s);
+                            float* r_out, float* lam_out, int* err, const L2Prefetch* pf,
+                            cudaStream_t s);
 bool make_vecs_tensor_map(wmd_corpus* c);
 // Widest query slice the tensor-core cdist takes for this corpus (0: none).
 int cdist_tc_max_width(const wmd_corpus* c);
