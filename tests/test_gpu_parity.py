@@ -272,7 +272,7 @@ def _workspace_k(wmd, corpus, dq, VR, prec):
 @pytest.mark.parametrize("v_r", [5, 16, 30, 64, 100])
 def test_cdist_kernel_matrix_elementwise(wmd, monkeypatch, kernel, v_r):
     """K = exp(-lambda M) against the oracle's FP64 distances, for the
-    tensor-core (3xTF32) and the CUDA-core kernel; the query's own words give
+    tensor-core (fp16 pairs) and the CUDA-core kernel; the query's own words give
     K = 1 exactly; padding columns are 0; r and lambda land next to K."""
     import torch
     if kernel == "simt":
