@@ -310,6 +310,43 @@ def test_cdist_kernel_matrix_elementwise(wmd, monkeypatch, kernel, v_r):
         assert own.sum() == len(rows)
 
 
+def test_cdist_tc_rows_of_mixed_magnitude(wmd, monkeypatch):
+    """The tensor-core cdist scales every vocabulary row by its own power of
+    two before splitting it into fp16 hi and lo parts: rows whose magnitudes
+    span 12 decades keep float32-grade distances.  Bound per element from the
+    arithmetic: the pair product loses at most ~2^-21 |a| |b| and m^2 a few
+    float32 ulps of |a|^2 + |b|^2, so |dm| <= 1e-5 (|a|^2 + |b|^2) / (2 m)
+    (or the square root of that numerator when m is smaller) and
+    |dK| <= K (lambda |dm| + 2.4e-7), the last term for expf and the float32
+    rounding of K itself (4 ulps: K = 1 - 1e-8 is stored as 1)."""
+    import torch
+    monkeypatch.delenv("WMD_CDIST_KERNEL", raising=False)
+    V, d, v_r = 3000, 64, 16
+    rng = np.random.default_rng(23)
+    vecs = synth.make_vecs(V, d, 21) * (10.0 ** rng.uniform(-6, 6, size=(V, 1))).astype(np.float32)
+    vecs = vecs.astype(np.float32)
+    c = synth.make_corpus(V, 200, 5, 40, 22)
+    q_ids, q_w = synth.make_query(V, v_r, 24)
+    corpus = wmd.Corpus.from_synth(vecs, c)
+    words = _active_words(c)
+    M = orc.cdist(vecs, q_ids, words).T                    # U x v_r, float64
+    lam = float(3.0 / np.median(M))
+    dq = wmd.DeviceQuery(corpus, q_ids, q_w, wmd.PREC_FP32)
+    corpus.build_kernel_matrix(dq.ids, dq.w, dq.v_r, lam, wmd.PREC_FP32, dq.ws, dq.ws_bytes)
+    torch.cuda.synchronize()
+    _, _, K = _workspace_k(wmd, corpus, dq, 16, wmd.PREC_FP32)
+    a2 = np.sum(vecs[words].astype(np.float64) ** 2, axis=1)[:, None]
+    b2 = np.sum(vecs[q_ids].astype(np.float64) ** 2, axis=1)[None, :]
+    dm2 = 1e-5 * (a2 + b2)
+    dm = np.where(M * M > dm2, dm2 / (2 * np.maximum(M, 1e-300)), np.sqrt(dm2))
+    Kw = np.exp(-lam * M)
+    err = np.abs(K[:, :v_r].astype(np.float64) - Kw)
+    bound = Kw * (np.expm1(lam * dm) + 2.4e-7) + 1e-37
+    assert np.all(err <= bound), f"worst excess {np.max(err / bound):.3g}"
+    # and a non-trivial share of K is well above underflow
+    assert np.mean(Kw > 1e-6) > 0.05
+
+
 @pytest.mark.parametrize("kernel", ["tc", "simt"])
 def test_paper_shaped_with_both_cdist_kernels(wmd, monkeypatch, kernel):
     if kernel == "simt":
