@@ -120,7 +120,7 @@ struct TeamCtx {
   QueryDesc q;  // the query this CTA works for (q.lambda resolved)
   int rpw_res;  // rows per warp when the document is register resident
   int nch;      // chunks this warp handles
-  float* red;   // [2][NW][VR] partial x of every warp of the CTA
+  float* red;   // [NW][VR] partial x of every warp, then [NW / 2][VR] u of every team
   double* wred; // [NW] partial WMD of every warp of the CTA
   int nw;       // warps in the CTA
 };
@@ -183,7 +183,18 @@ __device__ __forceinline__ void solve(const LoopParams& p, const TeamCtx& t) {
   };
   if (!RELOAD && t.nch) load_chunk(0);
 
-  int buf = 0;
+  // teams of several warps finish u column by column: lane tl of the team
+  // owns columns tl, tl + 32 W, ... (at most kTeamCols of them)
+  constexpr int kTeamCols = VR / 64 > 1 ? VR / 64 : 1;
+  const int tl = t.kw * 32 + t.lane;
+  float* red = t.red;                        // [NW][VR] partial x of every warp
+  float* ured = t.red + t.nw * VR + t.team * VR;  // u of this team
+  float rcol[kTeamCols];
+#pragma unroll
+  for (int j = 0; j < kTeamCols; ++j) {
+    const int col = tl + j * 32 * t.W;
+    rcol[j] = t.W > 1 && col < t.q.v_r ? t.q.r[col] : 0.f;
+  }
   float wacc = 0.f;
   for (int it = 0; it <= p.T; ++it) {
     const bool last = it == p.T;
@@ -246,9 +257,11 @@ __device__ __forceinline__ void solve(const LoopParams& p, const TeamCtx& t) {
           xp[q] = __fadd2_rn(xp[q], o);
         }
       }
-      // ... and over the warps of the team (fixed order, so deterministic)
+      // u = 1 / x with x = diag(1/r) (K v):  u_i = r_i / (K v)_i
       if (t.W > 1) {
-        float* red = t.red + buf * t.nw * VR;
+        // ... and over the warps of the team: each lane of the team finishes
+        // whole columns (the team's partial sums in fixed warp order, so
+        // deterministic, then u), and every lane reads back its columns' u
         if (t.pw == 0) {
 #pragma unroll
           for (int q = 0; q < C2; ++q) {
@@ -258,19 +271,25 @@ __device__ __forceinline__ void solve(const LoopParams& p, const TeamCtx& t) {
         }
         team_barrier(1 + t.team, 32 * t.W);
 #pragma unroll
+        for (int j = 0; j < kTeamCols; ++j) {
+          const int col = tl + j * 32 * t.W;
+          if (col < VR) {
+            float x = 0.f;
+            for (int k2 = 0; k2 < t.W; ++k2) x += red[(t.team * t.W + k2) * VR + col];
+            ured[col] = rcol[j] * fast_rcp(x);
+          }
+        }
+        team_barrier(1 + t.team, 32 * t.W);
+#pragma unroll
         for (int q = 0; q < C2; ++q) {
           const int col = (q >> 1) * 4 * PI + 4 * t.pi + 2 * (q & 1);
-          float2 x = make_float2(0.f, 0.f);
-          for (int k2 = 0; k2 < t.W; ++k2)
-            x = __fadd2_rn(x, *reinterpret_cast<const float2*>(&red[(t.team * t.W + k2) * VR + col]));
-          xp[q] = x;
+          u[q] = *reinterpret_cast<const float2*>(&ured[col]);
         }
-        buf ^= 1;
-      }
-      // u = 1 / x with x = diag(1/r) (K v):  u_i = r_i / (K v)_i
+      } else {
 #pragma unroll
-      for (int q = 0; q < C2; ++q)
-        u[q] = __fmul2_rn(rr[q], make_float2(fast_rcp(xp[q].x), fast_rcp(xp[q].y)));
+        for (int q = 0; q < C2; ++q)
+          u[q] = __fmul2_rn(rr[q], make_float2(fast_rcp(xp[q].x), fast_rcp(xp[q].y)));
+      }
     }
   }
 
