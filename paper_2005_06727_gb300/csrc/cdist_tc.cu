@@ -336,6 +336,9 @@ __global__ void __launch_bounds__(kThreads, 1)
   const int warp = tid >> 5;
   const int lane = tid & 31;
   if (tid == 0) TC_TRACE(5, 0);
+  // the next kernel in the stream (the fused loop) may start its CTAs now;
+  // they wait for this grid's results before reading them
+  if (tid == 0) asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
 
   // the device rows of the query words (ids -> permutation) are looked up
   // first, so that these dependent loads overlap the prologue

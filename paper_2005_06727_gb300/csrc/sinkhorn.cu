@@ -25,6 +25,8 @@
 // (the query's own word) and within a few float32 ulps of m while K is a
 // normal float (the cdist kernel computed K = exp(-lambda m) in float32, so
 // -ln K returns lambda m up to the rounding of that product and of expf).
+#include <mutex>
+
 #include "wmd_internal.h"
 
 namespace wmd {
@@ -73,6 +75,14 @@ __device__ __forceinline__ void load_krow(const KT* __restrict__ Kb, int64_t row
   }
 }
 
+// Programmatic dependent launch: the kernel may start while the cdist
+// kernel before it in the stream still runs; from this wait on, everything
+// that kernel wrote (K, r, lambda, the timeout word) is visible.  A no-op when
+// the launch has no programmatic predecessor.
+__device__ __forceinline__ void wait_for_producer() {
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+}
+
 __device__ __forceinline__ void team_barrier(int id, int nthreads) {
   asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
 }
@@ -117,7 +127,7 @@ struct TeamCtx {
   int lane;
   int pi;
   int pw;
-  QueryDesc q;  // the query this CTA works for (q.lambda resolved)
+  QueryDesc q;  // the query this CTA works for (q.lambda: batched launches only)
   int rpw_res;  // rows per warp when the document is register resident
   int nch;      // chunks this warp handles
   float* red;   // [NW][VR] partial x of every warp, then [NW / 2][VR] u of every team
@@ -136,6 +146,33 @@ __device__ __forceinline__ void solve(const LoopParams& p, const TeamCtx& t) {
   constexpr int PW = 32 / PI;
   const KT* Kb = static_cast<const KT*>(p.K);
 
+  // corpus data first (the previous kernel does not write it): the word ids
+  // and weights of my rows, then wait for that kernel's K and r
+  float cw[R];
+  int wrow[R];
+  if (!RELOAD && t.nch) {
+    const int start = t.kw * t.rpw_res;
+    const int len = min(t.rpw_res, t.n - start);
+#pragma unroll
+    for (int rI = 0; rI < R; ++rI) {
+      const int row = rI * PW + t.pw;
+      if (row < len) {
+        const int64_t e = t.beg + start + row;
+        cw[rI] = p.doc_vals[e];
+        wrow[rI] = p.doc_words[e];
+      } else {
+        cw[rI] = 0.f;
+        wrow[rI] = -1;
+      }
+    }
+  }
+  wait_for_producer();
+  if (*p.err) {  // the cdist kernel gave up waiting: no result (whole teams leave together)
+    if (t.kw == 0 && t.lane == 0) t.q.out[t.doc] = __longlong_as_double(0x7ff8000000000000ll);
+    return;
+  }
+  const float lam = p.queries ? t.q.lambda : *p.lam;
+
   // query weights and the initial u = 1 / x = v_r for my columns; one lane
   // per column seeds the SpMM sums of padding columns with 1 so that 1/x stays
   // finite there (their r is 0, so u = r / x = 0, and K = 0 keeps them out of
@@ -152,7 +189,6 @@ __device__ __forceinline__ void solve(const LoopParams& p, const TeamCtx& t) {
   }
 
   float2 kt[R][C2];
-  float cw[R];
   auto chunk = [&](int m, int& start, int& len) {
     if (RELOAD) {
       start = (m * t.W + t.kw) * (PW * R);
@@ -181,7 +217,19 @@ __device__ __forceinline__ void solve(const LoopParams& p, const TeamCtx& t) {
       }
     }
   };
-  if (!RELOAD && t.nch) load_chunk(0);
+  if (!RELOAD && t.nch) {
+    // K rows of the resident block; padding rows: c = 0 gives v = 0, and
+    // K = 1 keeps s > 0 so that c / s needs no guard
+#pragma unroll
+    for (int rI = 0; rI < R; ++rI) {
+      if (wrow[rI] >= 0) {
+        load_krow<KT, C, PI>(Kb, wrow[rI], p.ldk, t.q.kcol0, t.pi, kt[rI]);
+      } else {
+#pragma unroll
+        for (int q = 0; q < C2; ++q) kt[rI][q] = make_float2(1.f, 1.f);
+      }
+    }
+  }
 
   // teams of several warps finish u column by column: lane tl of the team
   // owns columns tl, tl + 32 W, ... (at most kTeamCols of them)
@@ -313,10 +361,10 @@ __device__ __forceinline__ void solve(const LoopParams& p, const TeamCtx& t) {
     if (t.kw == 0 && t.lane == 0) {
       double acc = 0.0;
       for (int k2 = 0; k2 < t.W; ++k2) acc += t.wred[t.team * t.W + k2];
-      t.q.out[t.doc] = acc * (-kLn2 / (double)t.q.lambda);
+      t.q.out[t.doc] = acc * (-kLn2 / (double)lam);
     }
   } else if (t.lane == 0) {
-    t.q.out[t.doc] = wsum * (-kLn2 / (double)t.q.lambda);
+    t.q.out[t.doc] = wsum * (-kLn2 / (double)lam);
   }
 }
 
@@ -333,20 +381,14 @@ __global__ void __launch_bounds__(NW * 32, MINB) sinkhorn_fused_kernel(LoopParam
   __shared__ double wred[NW];
 
   TeamCtx t;
-  if (p.queries) {
-    t.q = p.queries[blockIdx.y];
-  } else {
-    t.q.r = p.r;
-    t.q.out = p.out;
-    t.q.kcol0 = p.kcol0;
-    t.q.v_r = p.v_r;
-    t.q.lambda = *p.lam;
-  }
   t.warp = threadIdx.x >> 5;
   t.lane = threadIdx.x & 31;
   t.pi = t.lane % PI;
   t.pw = t.lane / PI;
-  if (p.err_out && blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) *p.err_out = *p.err;
+  if (p.err_out && blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) {
+    wait_for_producer();
+    *p.err_out = *p.err;
+  }
   const WarpTask task = p.tasks[blockIdx.x * NW + t.warp];
   t.W = task.n_w >> kTaskWShift;
   if (t.W == 0) return;  // no team in this item (whole teams leave together)
@@ -355,13 +397,18 @@ __global__ void __launch_bounds__(NW * 32, MINB) sinkhorn_fused_kernel(LoopParam
   t.doc = task.doc;
   t.beg = task.beg;
   t.n = task.n_w & ((1 << kTaskWShift) - 1);
-  if (*p.err) {
-    if (t.kw == 0 && t.lane == 0) t.q.out[t.doc] = __longlong_as_double(0x7ff8000000000000ll);
-    return;
+  if (p.queries) {
+    t.q = p.queries[blockIdx.y];  // written by the host before the cdist kernel
+  } else {
+    t.q.r = p.r;
+    t.q.out = p.out;
+    t.q.kcol0 = p.kcol0;
+    t.q.v_r = p.v_r;
   }
   if (t.n == 0) {
+    wait_for_producer();  // the timeout word comes from the cdist kernel
     if (t.kw == 0 && t.lane == 0)
-      t.q.out[t.doc] = p.T >= 1 ? __longlong_as_double(0x7ff8000000000000ll) : 0.0;
+      t.q.out[t.doc] = *p.err || p.T >= 1 ? __longlong_as_double(0x7ff8000000000000ll) : 0.0;
     return;
   }
   t.red = red;
@@ -411,10 +458,31 @@ template <> struct Var<5, 1> { static constexpr int VR = 256, PI = 16, RMAX = 8,
 template <int CLS, int V, typename KT>
 cudaError_t launch_var(const LoopParams& p, int n_items, int nq, cudaStream_t s) {
   using Cf = Var<CLS, V>;
+  auto kern = sinkhorn_fused_kernel<Cf::VR, Cf::PI, Cf::RMAX, Cf::MINB, Cf::NW, KT>;
   if (n_items == 0 || nq == 0) return cudaSuccess;
-  dim3 grid((unsigned)n_items, (unsigned)nq);
-  sinkhorn_fused_kernel<Cf::VR, Cf::PI, Cf::RMAX, Cf::MINB, Cf::NW, KT><<<grid, Cf::NW * 32, 0, s>>>(p);
-  return cudaGetLastError();
+  // the same shared-memory carveout as the cdist kernel, so that the first
+  // CTAs can share SMs with it (once per process, never inside a capture:
+  // the first launch of a shape always runs eagerly)
+  static std::once_flag once;
+  static cudaError_t attr_err = cudaSuccess;
+  std::call_once(once, [&] {
+    attr_err = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                    (int)cudaSharedmemCarveoutMaxShared);
+  });
+  if (attr_err != cudaSuccess) return attr_err;
+  // programmatic dependent launch: CTAs may start while the kernel before
+  // them (the cdist kernel) finishes; they wait for its results in solve()
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)n_items, (unsigned)nq);
+  cfg.blockDim = dim3(Cf::NW * 32);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kern, p);
 }
 
 template <typename KT>
