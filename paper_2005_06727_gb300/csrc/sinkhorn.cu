@@ -132,6 +132,7 @@ struct TeamCtx {
   int nch;      // chunks this warp handles
   float* red;   // [NW][VR] partial x of every warp, then [NW / 2][VR] u of every team
   double* wred; // [NW] partial WMD of every warp of the CTA
+  float* wpart; // [NW][PW + 1][VR] per warp: row-group partial x, then u
   int nw;       // warps in the CTA
 };
 
@@ -177,13 +178,16 @@ __device__ __forceinline__ void solve(const LoopParams& p, const TeamCtx& t) {
   // per column seeds the SpMM sums of padding columns with 1 so that 1/x stays
   // finite there (their r is 0, so u = r / x = 0, and K = 0 keeps them out of
   // every sum); bit 2q+h of `seed` marks those columns
+  // one-warp teams of narrow queries finish x through shared memory (below);
+  // wider ones keep the query weights of their columns in registers
+  constexpr bool kSmemFinish = VR <= 32;
   float2 rr[C2], u[C2];
   uint32_t seed = 0;
 #pragma unroll
   for (int q = 0; q < C2; ++q) {
     const int col = (q >> 1) * 4 * PI + 4 * t.pi + 2 * (q & 1);
     const bool l0 = col < t.q.v_r, l1 = col + 1 < t.q.v_r;
-    rr[q] = make_float2(l0 ? t.q.r[col] : 0.f, l1 ? t.q.r[col + 1] : 0.f);
+    if (!kSmemFinish) rr[q] = make_float2(l0 ? t.q.r[col] : 0.f, l1 ? t.q.r[col + 1] : 0.f);
     u[q] = make_float2(l0 ? (float)t.q.v_r : 0.f, l1 ? (float)t.q.v_r : 0.f);
     if (t.pw == 0 && t.kw == 0) seed |= (l0 ? 0u : 1u) << (2 * q) | (l1 ? 0u : 1u) << (2 * q + 1);
   }
@@ -231,17 +235,20 @@ __device__ __forceinline__ void solve(const LoopParams& p, const TeamCtx& t) {
     }
   }
 
-  // teams of several warps finish u column by column: lane tl of the team
-  // owns columns tl, tl + 32 W, ... (at most kTeamCols of them)
-  constexpr int kTeamCols = VR / 64 > 1 ? VR / 64 : 1;
+  // u is finished column by column: lane tl of the team (of the warp for
+  // one-warp teams of narrow queries) owns columns tl, tl + 32 W, ... (at
+  // most kLaneCols of them)
+  constexpr int kLaneCols = VR / 64 > 1 ? VR / 64 : 1;
   const int tl = t.kw * 32 + t.lane;
   float* red = t.red;                        // [NW][VR] partial x of every warp
   float* ured = t.red + t.nw * VR + t.team * VR;  // u of this team
-  float rcol[kTeamCols];
+  float* wpart = t.wpart + t.warp * (PW + 1) * VR;  // [PW][VR] partial x of the warp's row groups
+  float* wu = wpart + PW * VR;                       // [VR] u of a one-warp team
+  float rcol[kLaneCols];
 #pragma unroll
-  for (int j = 0; j < kTeamCols; ++j) {
+  for (int j = 0; j < kLaneCols; ++j) {
     const int col = tl + j * 32 * t.W;
-    rcol[j] = t.W > 1 && col < t.q.v_r ? t.q.r[col] : 0.f;
+    rcol[j] = col < t.q.v_r ? t.q.r[col] : 0.f;
   }
   float wacc = 0.f;
   for (int it = 0; it <= p.T; ++it) {
@@ -294,7 +301,35 @@ __device__ __forceinline__ void solve(const LoopParams& p, const TeamCtx& t) {
       }
     }
 
-    if (!last) {
+    if (kSmemFinish && !last && t.W == 1) {
+      // x = sum over the PW row groups of the warp, finished through shared
+      // memory: every lane stores its partial sums, lane L sums column L (and
+      // L + 32, ...) in fixed row-group order and writes u = r / x, every lane
+      // reads back its columns' u
+      // (u = 1 / x with x = diag(1/r) (K v):  u_i = r_i / (K v)_i)
+#pragma unroll
+      for (int q = 0; q < C2; ++q) {
+        const int col = (q >> 1) * 4 * PI + 4 * t.pi + 2 * (q & 1);
+        *reinterpret_cast<float2*>(&wpart[t.pw * VR + col]) = xp[q];
+      }
+      __syncwarp();
+#pragma unroll
+      for (int j = 0; j < kLaneCols; ++j) {
+        const int col = t.lane + 32 * j;
+        if (col < VR) {
+          float x = 0.f;
+#pragma unroll
+          for (int k2 = 0; k2 < PW; ++k2) x += wpart[k2 * VR + col];
+          wu[col] = rcol[j] * fast_rcp(x);
+        }
+      }
+      __syncwarp();
+#pragma unroll
+      for (int q = 0; q < C2; ++q) {
+        const int col = (q >> 1) * 4 * PI + 4 * t.pi + 2 * (q & 1);
+        u[q] = *reinterpret_cast<const float2*>(&wu[col]);
+      }
+    } else if (!last) {
       // x: sum over the PW row groups of the warp ...
 #pragma unroll
       for (int off = PI; off < 32; off <<= 1) {
@@ -306,7 +341,11 @@ __device__ __forceinline__ void solve(const LoopParams& p, const TeamCtx& t) {
         }
       }
       // u = 1 / x with x = diag(1/r) (K v):  u_i = r_i / (K v)_i
-      if (t.W > 1) {
+      if (t.W == 1) {
+#pragma unroll
+        for (int q = 0; q < C2; ++q)
+          u[q] = __fmul2_rn(rr[q], make_float2(fast_rcp(xp[q].x), fast_rcp(xp[q].y)));
+      } else {
         // ... and over the warps of the team: each lane of the team finishes
         // whole columns (the team's partial sums in fixed warp order, so
         // deterministic, then u), and every lane reads back its columns' u
@@ -319,7 +358,7 @@ __device__ __forceinline__ void solve(const LoopParams& p, const TeamCtx& t) {
         }
         team_barrier(1 + t.team, 32 * t.W);
 #pragma unroll
-        for (int j = 0; j < kTeamCols; ++j) {
+        for (int j = 0; j < kLaneCols; ++j) {
           const int col = tl + j * 32 * t.W;
           if (col < VR) {
             float x = 0.f;
@@ -333,10 +372,6 @@ __device__ __forceinline__ void solve(const LoopParams& p, const TeamCtx& t) {
           const int col = (q >> 1) * 4 * PI + 4 * t.pi + 2 * (q & 1);
           u[q] = *reinterpret_cast<const float2*>(&ured[col]);
         }
-      } else {
-#pragma unroll
-        for (int q = 0; q < C2; ++q)
-          u[q] = __fmul2_rn(rr[q], make_float2(fast_rcp(xp[q].x), fast_rcp(xp[q].y)));
       }
     }
   }
@@ -378,6 +413,7 @@ __global__ void __launch_bounds__(NW * 32, MINB) sinkhorn_fused_kernel(LoopParam
   static_assert(RMAX % 4 == 0, "RMAX must split into 4 steps");
 
   __shared__ __align__(16) float red[2 * NW * VR];
+  __shared__ __align__(16) float wpart[VR <= 32 ? NW * (PW + 1) * VR : 4];
   __shared__ double wred[NW];
 
   TeamCtx t;
@@ -413,6 +449,7 @@ __global__ void __launch_bounds__(NW * 32, MINB) sinkhorn_fused_kernel(LoopParam
   }
   t.red = red;
   t.wred = wred;
+  t.wpart = wpart;
   t.nw = NW;
 
   if (t.n <= t.W * RPW) {
