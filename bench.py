@@ -437,7 +437,8 @@ def run_ours(args, w):
     while VR < v_r:
         VR *= 2
     kelem = 2 if prec == wmd.PREC_BF16_K else 4
-    cdist_bytes = U * ldv * 4 + U * VR * kelem + U * 4 + v_r * ldv * 4
+    # fp16 hi + lo rows of the active vocabulary, K, norms and row scales, the query rows
+    cdist_bytes = U * ldv * 4 + U * VR * kelem + U * 8 + v_r * ldv * 4
     loop_flops = 4.0 * v_r * c.nnz * (w.max_iter + 1)
     alu_peak = NUM_SMS * FP32_LANES_PER_SM * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6
     kernels = {
