@@ -481,7 +481,8 @@ __global__ void __launch_bounds__(NW * 32, MINB) sinkhorn_fused_kernel(LoopParam
 // keeps a long document's K block resident.  The autotuner (wmd_autotune)
 // picks one per class and precision by timing.
 template <int CLS, int V> struct Var;
-template <> struct Var<0, 0> { static constexpr int VR = 8, PI = 2, RMAX = 24, MINB = 2, NW = 4; };
+template <> struct Var<0, 0> { static constexpr int VR = 8, PI = 2, RMAX = 12, MINB = 4, NW = 4; };
+template <> struct Var<0, 1> { static constexpr int VR = 8, PI = 2, RMAX = 24, MINB = 2, NW = 4; };
 template <> struct Var<1, 0> { static constexpr int VR = 16, PI = 4, RMAX = 24, MINB = 3, NW = 4; };
 template <> struct Var<2, 0> { static constexpr int VR = 32, PI = 4, RMAX = 12, MINB = 3, NW = 4; };
 template <> struct Var<2, 1> { static constexpr int VR = 32, PI = 4, RMAX = 8, MINB = 4, NW = 4; };
@@ -526,7 +527,7 @@ template <typename KT>
 cudaError_t dispatch_loop(int cls, int var, const LoopParams& p, int n_items, int nq,
                           cudaStream_t s) {
   switch (cls) {
-    case 0: return launch_var<0, 0, KT>(p, n_items, nq, s);
+    case 0: return var ? launch_var<0, 1, KT>(p, n_items, nq, s) : launch_var<0, 0, KT>(p, n_items, nq, s);
     case 1: return launch_var<1, 0, KT>(p, n_items, nq, s);
     case 2: return var ? launch_var<2, 1, KT>(p, n_items, nq, s) : launch_var<2, 0, KT>(p, n_items, nq, s);
     case 3: return var ? launch_var<3, 1, KT>(p, n_items, nq, s) : launch_var<3, 0, KT>(p, n_items, nq, s);
@@ -542,7 +543,7 @@ constexpr int rpw() { return (32 / Var<CLS, V>::PI) * Var<CLS, V>::RMAX; }
 
 int rows_per_warp(int cls, int var) {
   switch (cls) {
-    case 0: return rpw<0, 0>();
+    case 0: return var ? rpw<0, 1>() : rpw<0, 0>();
     case 1: return rpw<1, 0>();
     case 2: return var ? rpw<2, 1>() : rpw<2, 0>();
     case 3: return var ? rpw<3, 1>() : rpw<3, 0>();

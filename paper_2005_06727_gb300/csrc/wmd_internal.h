@@ -37,7 +37,7 @@ inline int vr_class(int v_r) {
 // Fused-loop tile variants per class (sinkhorn.cu) and the rows one warp of
 // variant `var` keeps in registers (row groups x rows per lane).
 constexpr int kMaxVariants = 2;
-constexpr int kClassVariants[kNumClasses] = {1, 1, 2, 2, 2, 2};
+constexpr int kClassVariants[kNumClasses] = {2, 1, 2, 2, 2, 2};
 int rows_per_warp(int cls, int var);
 int warps_per_cta(int cls, int var);  // 4 or 8
 
