@@ -51,6 +51,9 @@ def parse():
     ap.add_argument("--no-systems", action="store_true",
                     help="skip the batched and served measurements")
     ap.add_argument("--serve-requests", type=int, default=300)
+    ap.add_argument("--serving-workload", choices=["paper", "serving"], default="paper",
+                    help="corpus of the serving leg: the paper-shaped one (default, minutes) or "
+                         "the full serving configuration (V = N = 200,000)")
     ap.add_argument("--loop-variant", type=int, default=-1,
                     help="fused-loop tile variant (default: chosen by the autotuner)")
     return ap.parse_args()
@@ -176,15 +179,47 @@ def time_oracle(w, vecs, c, q_ids, q_w, docs=None):
 
 
 def cpu_baseline(w, vecs, c, q_ids, q_w, budget_s=10.0):
-    """The oracle as it stands, whole queries, repeated until ~budget_s."""
+    """The oracle as it stands, whole queries, repeated until ~budget_s.
+    Returns the baseline record and the oracle's WMD[N] for the query."""
     times = []
+    ref = None
     while sum(times) < budget_s and len(times) < 5:
-        t, _ = time_oracle(w, vecs, c, q_ids, q_w)
+        t, ref = time_oracle(w, vecs, c, q_ids, q_w)
         times.append(t)
     t = statistics.mean(times)
     return {"value": w.N / t, "unit": UNIT, "cores": 1, "kind": "oracle",
             "sample": f"{len(times)} full queries (all {w.N} documents, v_r={len(q_ids)}), "
-                      f"FP64 numpy/scipy oracle, single thread, mean {t:.2f} s per query"}
+                      f"FP64 numpy/scipy oracle, single thread, mean {t:.2f} s per query"}, ref
+
+
+def error_vs_oracle(got, ref, prec):
+    """Largest per-document relative error of the GPU result against the FP64
+    oracle (absolute floor 1e-7), beside the tolerance the tests enforce."""
+    got = np.asarray(got, np.float64)
+    ref = np.asarray(ref, np.float64)
+    rel = np.abs(got - ref) / np.maximum(np.abs(ref), 1e-7)
+    return {"max_rel": float(np.max(rel)), "mean_rel": float(np.mean(rel)), "docs": int(ref.size),
+            "tolerance": 1e-5 if prec == wmd_prec_fp32() else 5e-3}
+
+
+def wmd_prec_fp32():
+    from paper_2005_06727_gb300 import wmd
+    return wmd.PREC_FP32
+
+
+def effective_hbm(w, c, v_r, loop_ms, step_ms, peak_gbs):
+    """The paper's per-iteration formulation streams c and the dense u/x
+    state in every SDDMM_SpMM pass and reads K and M once:
+    B_iter = (T+1) [8 nnz + 4 (N+1) + 8 v_r N] + 4 v_r V 2 + 8 N bytes.
+    Its bytes over the measured time, as a fraction of the HBM peak."""
+    T = w.max_iter
+    b_iter = (T + 1) * (8 * c.nnz + 4 * (c.N + 1) + 8 * v_r * c.N) + 4 * v_r * w.V * 2 + 8 * c.N
+    loop_gbs = b_iter / (loop_ms * 1e-3) / 1e9
+    step_gbs = b_iter / (step_ms * 1e-3) / 1e9
+    return {"b_iter_bytes": int(b_iter), "loop_gbs": loop_gbs, "loop_frac": loop_gbs / peak_gbs,
+            "step_gbs": step_gbs, "step_frac": step_gbs / peak_gbs, "peak_gbs": peak_gbs,
+            "note": "B_iter of the paper's per-iteration formulation over the fused loop's (and "
+                    "the whole step's) time; the loop itself is bound by FP32 ALUs (see roofline)"}
 
 
 def run_reference(args, w):
@@ -252,12 +287,13 @@ def bench_batched(wmd, device, reps=2):
             "speedup": t_single / t_batch}
 
 
-def bench_serving(wmd, device, n_requests=300, seed=11):
-    """Poisson arrivals (v_r ~ U[5,200]) against the paper-shaped corpus:
-    latency p50/p99 and throughput of the continuous-batching server at rates
-    below its measured capacity, and the one-query-at-a-time capacity."""
+def bench_serving(wmd, device, n_requests=300, seed=11, workload="paper"):
+    """Poisson arrivals (v_r ~ U[5,200]) against the paper-shaped corpus (or
+    the full serving corpus): latency p50/p99 and throughput of the
+    continuous-batching server at 0.1x to 1.2x of its measured capacity, and
+    the one-query-at-a-time capacity."""
     import threading as th
-    w = synth.PAPER
+    w = synth.SERVING if workload == "serving" else synth.PAPER
     vecs, c, _ = synth.make_workload(w)
     corpus = wmd.Corpus.from_synth(vecs, c, device=device)
     rng = np.random.default_rng(seed)
@@ -283,7 +319,7 @@ def bench_serving(wmd, device, n_requests=300, seed=11):
             srv.poll(t, timeout_us=60_000_000, out=out)
         capacity = len(ts) / (time.perf_counter() - t0)
         rates = []
-        for frac in (0.5, 0.9):
+        for frac in (0.1, 0.5, 0.9, 1.2):
             rate = frac * capacity
             arrivals = np.cumsum(rng.exponential(1.0 / rate, n_requests))
             sub_t, done_t, tickets = {}, {}, []
@@ -478,11 +514,14 @@ def run_ours(args, w):
         "gpu_launches": 2 * args.steps,
         "clocks": clk,
     }
+    out["effective_hbm"] = effective_hbm(w, c, v_r, loop_ms, step_ms, peaks["hbm_gbs"])
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        out["cpu_baseline"] = cpu_baseline(w, vecs, c, q_ids, q_w)
+        out["cpu_baseline"], ref = cpu_baseline(w, vecs, c, q_ids, q_w)
+        out["error_vs_oracle"] = error_vs_oracle(out_np, ref, prec)
     if rank == 0 and not args.no_systems:
         out["batched"] = bench_batched(wmd, local_rank)
-        out["serving"] = bench_serving(wmd, local_rank, args.serve_requests)
+        out["serving"] = bench_serving(wmd, local_rank, args.serve_requests,
+                                       workload=args.serving_workload)
     if rank == 0:
         print(json.dumps(out))
     corpus.close()
