@@ -105,10 +105,14 @@ wmd_status wmd_compact_query(const int32_t* q_ids, const float* q_w, int32_t n_q
  *          (int32 document ids in [0, N), strictly increasing within a row),
  *          val[nnz] (float32, finite and > 0).  All host.
  * device:  CUDA device ordinal that will hold the corpus.
- * On success *out receives a corpus that keeps vecs, the row norms, and a
- * document-major copy of c resident on the device until wmd_corpus_free.
+ * On success *out receives a corpus that keeps resident on the device, until
+ * wmd_corpus_free: vecs (rows permuted so that words occurring in some
+ * document come first), the row norms, the same rows as fp16 hi/lo pairs with
+ * a power-of-two scale per row (the tensor-core cdist operands), a
+ * document-major copy of c, and the fused loop's work items.
  * Errors: WMD_ERR_INVALID_ARG for any malformed input (checked on the host
- * before anything is copied), WMD_ERR_OUT_OF_MEMORY, WMD_ERR_CUDA.
+ * before anything is copied), WMD_ERR_UNSUPPORTED for a document of 2^24 or
+ * more distinct words, WMD_ERR_OUT_OF_MEMORY, WMD_ERR_CUDA.
  * ------------------------------------------------------------------------- */
 wmd_status wmd_corpus_load(const float* vecs, int64_t V, int32_t d,
                            const int64_t* row_ptr, const int32_t* doc_idx,
@@ -126,8 +130,12 @@ wmd_status wmd_corpus_get_info(const wmd_corpus* corpus, wmd_corpus_info* out);
  * lamda, max_iter)`).  q_ids/q_w: sparse query as in wmd_compact_query (host).
  * out_wmd: host array of N doubles, WMD_j for every document j.
  * The call compacts and validates the query on the host, copies it to the
- * device, runs the cdist/K build and the fused loop, and copies the result
- * back.  Calls on one corpus are serialised by an internal lock.
+ * device, and runs the cdist/K build and the fused loop (from a captured CUDA
+ * graph from the second call of a query shape on).  The loop kernel writes
+ * the result straight into out_wmd when out_wmd is pinned host memory mapped
+ * into the device's address space (cudaHostAlloc, or cudaHostRegister with
+ * mapping), else into a pinned staging block that is then copied to out_wmd.
+ * Calls on one corpus are serialised by an internal lock.
  * Errors: those of wmd_compact_query, WMD_ERR_INVALID_ARG for lambda <= 0 or
  * non-finite, max_iter < 0 or an empty query (v_r = 0), WMD_ERR_CUDA.
  * ------------------------------------------------------------------------- */
@@ -147,7 +155,12 @@ wmd_status wmd_query(wmd_corpus* corpus, const int32_t* q_ids, const float* q_w,
  * becomes NaN and so does every result, but uniqueness is not re-checked.
  * d_ws: device workspace of at least wmd_workspace_bytes(...) bytes, 256-byte
  * aligned; it holds r, lambda and K between the two stages.
- * d_out: device array of N doubles.
+ * d_out: device-visible array of N doubles (device memory, or pinned host
+ * memory mapped into the device's address space).
+ * The loop kernel is launched as a programmatic dependent of the kernel
+ * before it on the stream: it may start early, but reads nothing that
+ * kernel (or anything before it) wrote, and writes d_out, only after it has
+ * completed.
  *
  * wmd_build_kernel_matrix (Sec. 2 distance, Sec. 5 GEMM-type cdist,
  * Algorithm 1's K = exp(-lambda M)): K[w, i] for every active word w (a word
