@@ -15,10 +15,18 @@
 // Register tile of one lane: RMAX rows (document words) x C columns (query
 // words).  Lane = pw * PI + pi: the PI lanes of a row group split the row's
 // columns (SDDMM partial dots are combined with PI-lane butterflies), the
-// PW = 32 / PI row groups split the rows (SpMM partial sums are combined with
-// PW-lane butterflies and, for teams of several warps, through shared memory).
-// Column j of lane pi is c(j) = (j / 4) * 4 PI + 4 pi + j % 4, so one float4
-// load per 4 columns reads 16 PI contiguous bytes per row group.
+// PW = 32 / PI row groups split the rows (SpMM partial sums are finished
+// column by column through shared memory for one-warp teams of queries up to
+// 32 wide, else with PW-lane butterflies and, for teams of several warps,
+// across the warps through shared memory; the lane that finishes a column
+// also forms its u = r / x once).  Column j of lane pi is
+// c(j) = (j / 4) * 4 PI + 4 pi + j % 4, so one float4 load per 4 columns
+// reads 16 PI contiguous bytes per row group.
+//
+// The kernel is launched as a programmatic dependent of the cdist kernel: a
+// warp reads its task record and its rows' word ids and weights (corpus data,
+// which cdist prefetched into L2) and only then waits for cdist's K, r,
+// lambda and timeout word.
 //
 // K .* M for the final step is recovered from the K block already in
 // registers: M = -ln(K) / lambda = -log2(K) ln 2 / lambda, exact for K = 1
