@@ -377,8 +377,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     // query columns (device row, norm, inverse scale), the padded weights,
     // then the resident B = the query rows' fp16 pairs in the 128B-swizzled
     // K-major layout (chunk c of row n lands at chunk c ^ (n % 8)): hi rows
-    // 0..N-1, lo rows N..2N-1 of every k-block; every thread issues all its
-    // loads before its first store
+    // 0..N-1, lo rows N..2N-1 of every k-block
     const int bt = tid < 256 ? tid : tid - 32;  // 0 .. 287 (bt = tid below N)
     float qn = 0.f, qrs = 0.f;
     if (bt < N) {
@@ -396,47 +395,32 @@ __global__ void __launch_bounds__(kThreads, 1)
     if (p.lam_out && blockIdx.x == 0 && bt == 0) *p.lam_out = p.lambda;
     asm volatile("bar.sync 1, %0;" ::"r"(kBuildThreads) : "memory");
     if (tid == 0) TC_TRACE(6, 0);
-    constexpr int kBatch = 16;
+    // every 16-byte chunk of B goes straight from global to shared memory
+    // (cp.async, all of a thread's chunks in flight at once); the chunks of
+    // padding rows and of ids outside [0, V) are zero-filled (source size 0)
     const int per_row = KB * 8;                 // 16-byte chunks of one row's hi (or lo) part
     const int total = 2 * N * per_row;
-    bool first = true;
-    for (int base = bt; base < total; base += kBuildThreads * kBatch) {
-      uint4 v[kBatch];
-#pragma unroll
-      for (int j = 0; j < kBatch; ++j) {
-        const int idx = base + j * kBuildThreads;
-        v[j] = make_uint4(0u, 0u, 0u, 0u);
-        if (idx < total) {
-          const int nn = idx / per_row;           // 0..2N-1: hi rows, then lo rows
-          const int n = nn < N ? nn : nn - N;
-          const int rem = idx - nn * per_row;
-          const int k = (rem >> 3) * kKB + (rem & 7) * 8;
-          const int row = qrow_s[n];
-          const uint16_t* src = nn < N ? p.vhi : p.vlo;
-          if (row >= 0 && k < p.ldv)
-            v[j] = __ldg(reinterpret_cast<const uint4*>(src + (size_t)row * p.ldv + k));
-        }
-      }
-      if (first) {
-        // the producer may stream the vocabulary now: these loads are ahead of it
-        asm volatile("" ::: "memory");
-        if (lane == 0) atomicAdd(const_cast<int*>(issued_s), 1);
-        if (tid == 0) TC_TRACE(6, 1);
-        first = false;
-      }
-#pragma unroll
-      for (int j = 0; j < kBatch; ++j) {
-        const int idx = base + j * kBuildThreads;
-        if (idx < total) {
-          const int nn = idx / per_row;
-          const int rem = idx - nn * per_row;
-          const int kb = rem >> 3;
-          const int ch = rem & 7;
-          *reinterpret_cast<uint4*>(Bcat + kb * bblock + nn * 128 + ((ch ^ (nn & 7)) << 4)) = v[j];
-        }
-      }
+    for (int idx = bt; idx < total; idx += kBuildThreads) {
+      const int nn = idx / per_row;             // 0..2N-1: hi rows, then lo rows
+      const int n = nn < N ? nn : nn - N;
+      const int rem = idx - nn * per_row;
+      const int kb = rem >> 3;
+      const int ch = rem & 7;
+      const int k = kb * kKB + ch * 8;
+      const int row = qrow_s[n];
+      const bool ok = row >= 0 && k < p.ldv;
+      const uint16_t* src = (nn < N ? p.vhi : p.vlo) + (ok ? (size_t)row * p.ldv + k : 0);
+      const uint32_t dst = smem_u32(Bcat + kb * bblock + nn * 128 + ((ch ^ (nn & 7)) << 4));
+      asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src),
+                   "r"(ok ? 16 : 0)
+                   : "memory");
     }
-    if (first && lane == 0) atomicAdd(const_cast<int*>(issued_s), 1);
+    asm volatile("cp.async.commit_group;" ::: "memory");
+    // the producer may stream the vocabulary now: the query copies are ahead of it
+    __syncwarp();
+    if (lane == 0) atomicAdd(const_cast<int*>(issued_s), 1);
+    if (tid == 0) TC_TRACE(6, 1);
+    asm volatile("cp.async.wait_all;" ::: "memory");
     if (bt < N) {
       qn_s[bt] = qn;
       qrs_s[bt] = qrs;
