@@ -201,18 +201,10 @@ __device__ __forceinline__ void solve(const LoopParams& p, const TeamCtx& t) {
   }
 
   float2 kt[R][C2];
-  auto chunk = [&](int m, int& start, int& len) {
-    if (RELOAD) {
-      start = (m * t.W + t.kw) * (PW * R);
-      len = min(PW * R, t.n - start);
-    } else {
-      start = t.kw * t.rpw_res;
-      len = min(t.rpw_res, t.n - start);
-    }
-  };
+  // long documents (RELOAD): chunk m of this warp, re-read from L2 each pass
   auto load_chunk = [&](int m) {
-    int start, len;
-    chunk(m, start, len);
+    const int start = (m * t.W + t.kw) * (PW * R);
+    const int len = min(PW * R, t.n - start);
 #pragma unroll
     for (int rI = 0; rI < R; ++rI) {
       const int row = rI * PW + t.pw;
