@@ -508,7 +508,7 @@ def run_ours(args, w):
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(v_r * 8),
                 "d2h_bytes_per_step": int(c.N * 8), "ms_per_step": e2e_ms,
-                "path": "wmd_query: query H2D from pinned memory; the loop kernel writes WMD[N] into the pinned output"},
+                "path": "wmd_query: the kernels read the query from mapped pinned memory and write WMD[N] into the pinned output"},
         "roofline": roof,
         "kernels": kernels,
         "gpu_launches": 2 * args.steps,

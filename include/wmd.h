@@ -129,9 +129,10 @@ wmd_status wmd_corpus_get_info(const wmd_corpus* corpus, wmd_corpus_info* out);
  * One query, host buffers, synchronous (Sec. 3 `sinkhorn_wmd(r, c, vecs,
  * lamda, max_iter)`).  q_ids/q_w: sparse query as in wmd_compact_query (host).
  * out_wmd: host array of N doubles, WMD_j for every document j.
- * The call compacts and validates the query on the host, copies it to the
- * device, and runs the cdist/K build and the fused loop (from a captured CUDA
- * graph from the second call of a query shape on).  The loop kernel writes
+ * The call compacts and validates the query on the host into a pinned,
+ * device-mapped staging block that the kernels read directly, and runs the
+ * cdist/K build and the fused loop (from a captured CUDA graph from the
+ * second call of a query shape on).  The loop kernel writes
  * the result straight into out_wmd when out_wmd is pinned host memory mapped
  * into the device's address space (cudaHostAlloc, or cudaHostRegister with
  * mapping), else into a pinned staging block that is then copied to out_wmd.

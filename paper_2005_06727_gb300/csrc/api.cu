@@ -59,7 +59,6 @@ void free_corpus_device(wmd_corpus* c) {
   for (auto& sc : c->sched)
     for (auto& s : sc) cudaFree(s.d_tasks);
   cudaFree(c->ws);
-  cudaFree(c->d_qids);
   cudaFreeHost(c->h_stage);
   cudaFreeHost(c->h_out);
   for (auto& g : c->qgraphs)
@@ -562,17 +561,12 @@ wmd_status wmd_query(wmd_corpus* c, const int32_t* q_ids, const float* q_w, int3
     WMD_CUDA_TRY(cudaMalloc(&c->ws, need));
     c->ws_bytes = need;
   }
-  if (!c->d_qids) {
-    WMD_CUDA_TRY(cudaMalloc(&c->d_qids, 2 * WMD_MAX_VR * sizeof(int32_t)));
-    c->d_qw = reinterpret_cast<float*>(c->d_qids + WMD_MAX_VR);
+  if (!c->h_out)
     WMD_CUDA_TRY(cudaHostAlloc(&c->h_out, std::max<int64_t>(c->N, 1) * sizeof(double), cudaHostAllocMapped));
-  }
-  // one copy for ids and weights (the staging block is contiguous)
-  if (v_r < WMD_MAX_VR) std::memmove(h_ids + v_r, h_w, v_r * sizeof(float));
-  float* d_w = reinterpret_cast<float*>(c->d_qids + v_r);
 
-  // the results and the error word reach host memory directly: the loop
-  // kernel writes them into the mapped pinned blocks (no copy back)
+  // the query comes from, and the results and the error word go to, host
+  // memory directly: the kernels read the mapped staging block (no copy in)
+  // and the loop kernel writes the mapped output blocks (no copy back)
   double* dh_out = nullptr;
   int32_t* dh_stage = nullptr;
   WMD_CUDA_TRY(cudaHostGetDevicePointer(reinterpret_cast<void**>(&dh_out), c->h_out, 0));
@@ -593,17 +587,16 @@ wmd_status wmd_query(wmd_corpus* c, const int32_t* q_ids, const float* q_w, int3
     }
   }
 
-  // the whole sequence (H2D of the query, cdist, loop) runs eagerly on the
-  // first use of a query shape and from a captured CUDA graph from the second
-  // use on
+  // the whole sequence (cdist, loop) runs eagerly on the first use of a
+  // query shape and from a captured CUDA graph from the second use on
   const int cls = vr_class(v_r);
   const int variant = c->loop_variant[cls][prec == WMD_PREC_BF16_K];
+  const int32_t* dh_ids = dh_stage;
+  const float* dh_w = reinterpret_cast<const float*>(dh_stage + WMD_MAX_VR);
   auto enqueue = [&]() -> wmd_status {
-    WMD_CUDA_TRY(cudaMemcpyAsync(c->d_qids, h_ids, 2 * v_r * sizeof(int32_t),
-                                 cudaMemcpyHostToDevice, c->stream));
     wmd_status s2 = check_query_args(c, v_r, lambda, max_iter);
     if (s2 == WMD_OK)
-      s2 = wmd_build_kernel_matrix(c, c->d_qids, d_w, v_r, lambda, prec, c->ws, c->ws_bytes, c->stream);
+      s2 = wmd_build_kernel_matrix(c, dh_ids, dh_w, v_r, lambda, prec, c->ws, c->ws_bytes, c->stream);
     if (s2 == WMD_OK)
       s2 = sinkhorn_loop(c, v_r, max_iter, prec, c->ws, c->ws_bytes, dh_out, dh_err, c->stream);
     return s2;

@@ -92,9 +92,7 @@ struct wmd_corpus {
   cudaStream_t stream = nullptr;
   void* ws = nullptr;
   size_t ws_bytes = 0;
-  int32_t* d_qids = nullptr;   // WMD_MAX_VR ids followed by WMD_MAX_VR weights
-  float* d_qw = nullptr;       // = d_qids + WMD_MAX_VR
-  int32_t* h_stage = nullptr;  // pinned: ids, weights, error word (mapped: the loop kernel writes the error word)
+  int32_t* h_stage = nullptr;  // pinned, mapped: WMD_MAX_VR ids and WMD_MAX_VR weights (read by the cdist kernel), error word (written by the loop kernel)
   double* h_out = nullptr;     // pinned, mapped N doubles: the loop kernel writes the results here (host path)
   // captured host-path sequences, keyed by query shape (second use onwards)
   struct QueryGraph {
