@@ -12,16 +12,32 @@
 // global memory; nothing is shared between documents, so no atomics are
 // needed (the paper's nnz-balanced partition avoids them the same way).
 //
-// Register tile of one lane: RMAX rows (document words) x C columns (query
+// Register tile of one lane: R rows (document words) x C columns (query
 // words).  Lane = pw * PI + pi: the PI lanes of a row group split the row's
-// columns (SDDMM partial dots are combined with PI-lane butterflies), the
-// PW = 32 / PI row groups split the rows (SpMM partial sums are finished
-// column by column through shared memory for one-warp teams of queries up to
-// 32 wide, else with PW-lane butterflies and, for teams of several warps,
-// across the warps through shared memory; the lane that finishes a column
-// also forms its u = r / x once).  Column j of lane pi is
-// c(j) = (j / 4) * 4 PI + 4 pi + j % 4, so one float4 load per 4 columns
-// reads 16 PI contiguous bytes per row group.
+// columns, the PW = 32 / PI row groups split the rows (SpMM
+// partial sums are finished column by column through shared memory for
+// one-warp teams of queries up to 32 wide, else with PW-lane butterflies and,
+// for teams of several warps, across the warps through shared memory; the
+// lane that finishes a column also forms its u = r / x once).  Column j of
+// lane pi is c(j) = (j / 4) * 4 PI + 4 pi + j % 4, so one float4 load per 4
+// columns reads 16 PI contiguous bytes of a row.
+//
+// The SDDMM row sums end in a reduce-scatter instead of a full butterfly, so
+// that fewer reciprocals are computed twice.  A butterfly over the high bits
+// of pi (xor PX, 2 PX, ... below PI) comes first; then the PX lanes p that
+// differ in the low bits of pi hold the group's R rows in slots
+// (d, k), d < PX, k < R / PX, slot (d, k) of lane p holding row
+// ((p ^ d) R / PX + k).  A shuffle with lane p ^ d then brings lane p the
+// partial sums of its own rows (d = 0), so PX - 1 shuffles per own row
+// finish the sums, each lane forms v = c / s for its R / PX own rows only,
+// and the same xor pattern hands every lane the v of its other slots (an
+// all-gather).  K rows are gathered in plain row order (the PI lanes of a row
+// group read one row together) and then moved to their slots inside each
+// lane with log2(PX) levels of conditional swaps.  PX is 4 for 64-wide
+// queries and 2 otherwise, as timed: four lanes save more shuffles and
+// reciprocals but need R in steps of 4, which costs more padding rows than it
+// saves for the 32-, 128- and 256-wide tiles (and ties at 16); one lane (the
+// full butterfly) was slower for every width.
 //
 // The kernel is launched as a programmatic dependent of the cdist kernel: a
 // warp reads its task record and its rows' word ids and weights (corpus data,
@@ -95,15 +111,22 @@ __device__ __forceinline__ void team_barrier(int id, int nthreads) {
   asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
 }
 
+// Hardware base-2 logarithm (PTX lg2.approx.ftz) of a normal float.
+__device__ __forceinline__ float fast_log2(float x) {
+  float y;
+  asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
 // K log2 K = -lambda K M / ln 2 for two entries of K.  K below the smallest
-// normal float is clamped there, so that its term stays finite (and below
-// 1.5e-36 in magnitude).
+// normal float is clamped there, so that the logarithm needs no subnormal
+// handling and the term stays finite (and below 1.5e-36 in magnitude).
 __device__ __forceinline__ float2 k_log2k(float2 k) {
   // opaque to the compiler, so that the logarithms stay in the last pass
   // instead of being hoisted out of the iterations (96 live values per lane
   // would not fit in registers)
   asm volatile("" : "+f"(k.x), "+f"(k.y));
-  const float2 l = make_float2(__log2f(fmaxf(k.x, 1.17549435e-38f)), __log2f(fmaxf(k.y, 1.17549435e-38f)));
+  const float2 l = make_float2(fast_log2(fmaxf(k.x, 1.17549435e-38f)), fast_log2(fmaxf(k.y, 1.17549435e-38f)));
   return __fmul2_rn(k, l);
 }
 
@@ -124,6 +147,43 @@ __device__ __forceinline__ float fast_rcp(float x) {
   return y;
 }
 
+__host__ __device__ constexpr int round_up(int a, int b) { return (a + b - 1) / b * b; }
+
+// Row stride (floats) of the per-warp partial sums of x in shared memory.  A
+// quarter warp (two row groups of four lanes for PI = 4) stores 16 bytes per
+// lane at column 16 h + 4 pi: for 32-wide queries a stride of VR + 16 puts the
+// two row groups on different banks; narrower queries need no padding.
+__host__ __device__ constexpr int wpart_stride(int VR, int PI) { return VR / PI >= 8 ? VR + 16 : VR; }
+
+// Lanes of the SDDMM reduce-scatter for a query tile VR wide (1 would be the
+// plain butterfly over all PI lanes).
+__host__ __device__ constexpr int scatter_lanes(int VR) { return VR == 64 ? 4 : 2; }
+
+// Moves the K rows of a lane from plain order (slot d holds row group rows
+// d RK .. d RK + RK - 1) to the reduce-scatter order (slot d holds those of
+// d ^ px): one level of conditional swaps per bit of px.
+template <int R, int PX, int C2>
+__device__ __forceinline__ void permute_slots(float2 (&kt)[R][C2], int px) {
+  constexpr int RK = R / PX;
+#pragma unroll
+  for (int b = 1; b < PX; b <<= 1) {
+    const bool f = (px & b) != 0;
+#pragma unroll
+    for (int d = 0; d < PX; ++d) {
+      if (d & b) continue;
+#pragma unroll
+      for (int k = 0; k < RK; ++k) {
+#pragma unroll
+        for (int q = 0; q < C2; ++q) {
+          const float2 a = kt[d * RK + k][q], c = kt[(d | b) * RK + k][q];
+          kt[d * RK + k][q] = f ? c : a;
+          kt[(d | b) * RK + k][q] = f ? a : c;
+        }
+      }
+    }
+  }
+}
+
 struct TeamCtx {
   int doc;
   int64_t beg;
@@ -140,7 +200,7 @@ struct TeamCtx {
   int nch;      // chunks this warp handles
   float* red;   // [NW][VR] partial x of every warp, then [NW / 2][VR] u of every team
   double* wred; // [NW] partial WMD of every warp of the CTA
-  float* wpart; // [NW][PW + 1][VR] per warp: row-group partial x, then u
+  float* wpart; // [NW][PW + 1][wpart_stride] per warp: row-group partial x, then u
   int nw;       // warps in the CTA
 };
 
@@ -153,7 +213,18 @@ __device__ __forceinline__ void solve(const LoopParams& p, const TeamCtx& t) {
   constexpr int C = VR / PI;
   constexpr int C2 = C / 2;
   constexpr int PW = 32 / PI;
+  constexpr int PX = scatter_lanes(VR);  // lanes of the row-sum reduce-scatter
+  constexpr int RK = R / PX;             // rows whose sums a lane finishes
+  static_assert(R % PX == 0, "rows per lane must split over the reduce-scatter lanes");
   const KT* Kb = static_cast<const KT*>(p.K);
+  const int px = t.pi & (PX - 1);
+  // row of slot rI within the warp's chunk: slot (d, k) = (rI / RK, rI % RK)
+  // holds the group's row (px ^ d) RK + k; K is gathered in plain order (row
+  // rI PW + pw into slot rI) and permuted afterwards
+  auto slot_row = [&](int rI) { return ((px ^ (rI / RK)) * RK + rI % RK) * PW + t.pw; };
+  auto plain_row = [&](int rI) { return rI * PW + t.pw; };
+  // first column of float2 pair q of this lane
+  auto lane_col = [&](int q) { return (q >> 1) * 4 * PI + 4 * t.pi + 2 * (q & 1); };
 
   // corpus data first (the previous kernel does not write it): the word ids
   // and weights of my rows, then wait for that kernel's K and r
@@ -164,15 +235,9 @@ __device__ __forceinline__ void solve(const LoopParams& p, const TeamCtx& t) {
     const int len = min(t.rpw_res, t.n - start);
 #pragma unroll
     for (int rI = 0; rI < R; ++rI) {
-      const int row = rI * PW + t.pw;
-      if (row < len) {
-        const int64_t e = t.beg + start + row;
-        cw[rI] = p.doc_vals[e];
-        wrow[rI] = p.doc_words[e];
-      } else {
-        cw[rI] = 0.f;
-        wrow[rI] = -1;
-      }
+      const int srow = slot_row(rI), prow = plain_row(rI);
+      cw[rI] = srow < len ? p.doc_vals[t.beg + start + srow] : 0.f;
+      wrow[rI] = prow < len ? p.doc_words[t.beg + start + prow] : -1;
     }
   }
   wait_for_producer();
@@ -193,7 +258,7 @@ __device__ __forceinline__ void solve(const LoopParams& p, const TeamCtx& t) {
   uint32_t seed = 0;
 #pragma unroll
   for (int q = 0; q < C2; ++q) {
-    const int col = (q >> 1) * 4 * PI + 4 * t.pi + 2 * (q & 1);
+    const int col = lane_col(q);
     const bool l0 = col < t.q.v_r, l1 = col + 1 < t.q.v_r;
     if (!kSmemFinish) rr[q] = make_float2(l0 ? t.q.r[col] : 0.f, l1 ? t.q.r[col + 1] : 0.f);
     u[q] = make_float2(l0 ? (float)t.q.v_r : 0.f, l1 ? (float)t.q.v_r : 0.f);
@@ -207,19 +272,18 @@ __device__ __forceinline__ void solve(const LoopParams& p, const TeamCtx& t) {
     const int len = min(PW * R, t.n - start);
 #pragma unroll
     for (int rI = 0; rI < R; ++rI) {
-      const int row = rI * PW + t.pw;
-      if (row < len) {
-        const int64_t e = t.beg + start + row;
-        cw[rI] = p.doc_vals[e];
-        load_krow<KT, C, PI>(Kb, p.doc_words[e], p.ldk, t.q.kcol0, t.pi, kt[rI]);
+      const int srow = slot_row(rI), prow = plain_row(rI);
+      cw[rI] = srow < len ? p.doc_vals[t.beg + start + srow] : 0.f;
+      if (prow < len) {
+        load_krow<KT, C, PI>(Kb, p.doc_words[t.beg + start + prow], p.ldk, t.q.kcol0, t.pi, kt[rI]);
       } else {
         // padding row: c = 0 gives v = 0, and K = 1 keeps s > 0 so that
         // c / s needs no guard
-        cw[rI] = 0.f;
 #pragma unroll
         for (int q = 0; q < C2; ++q) kt[rI][q] = make_float2(1.f, 1.f);
       }
     }
+    permute_slots<R, PX, C2>(kt, px);
   };
   if (!RELOAD && t.nch) {
     // K rows of the resident block; padding rows: c = 0 gives v = 0, and
@@ -233,6 +297,7 @@ __device__ __forceinline__ void solve(const LoopParams& p, const TeamCtx& t) {
         for (int q = 0; q < C2; ++q) kt[rI][q] = make_float2(1.f, 1.f);
       }
     }
+    permute_slots<R, PX, C2>(kt, px);
   }
 
   // u is finished column by column: lane tl of the team (of the warp for
@@ -242,8 +307,11 @@ __device__ __forceinline__ void solve(const LoopParams& p, const TeamCtx& t) {
   const int tl = t.kw * 32 + t.lane;
   float* red = t.red;                        // [NW][VR] partial x of every warp
   float* ured = t.red + t.nw * VR + t.team * VR;  // u of this team
-  float* wpart = t.wpart + t.warp * (PW + 1) * VR;  // [PW][VR] partial x of the warp's row groups
-  float* wu = wpart + PW * VR;                       // [VR] u of a one-warp team
+  // [PW][kWS] partial x of the warp's row groups, then [VR] u of a one-warp
+  // team; rows padded so that a quarter warp's 16-byte stores hit distinct banks
+  constexpr int kWS = wpart_stride(VR, PI);
+  float* wpart = t.wpart + t.warp * (PW + 1) * kWS;
+  float* wu = wpart + PW * kWS;
   float rcol[kLaneCols];
 #pragma unroll
   for (int j = 0; j < kLaneCols; ++j) {
@@ -270,14 +338,26 @@ __device__ __forceinline__ void solve(const LoopParams& p, const TeamCtx& t) {
         s[rI] = a.x + a.y;
       }
 #pragma unroll
-      for (int off = 1; off < PI; off <<= 1) {
+      for (int off = PX; off < PI; off <<= 1) {
 #pragma unroll
         for (int rI = 0; rI < R; ++rI) s[rI] += __shfl_xor_sync(0xffffffffu, s[rI], off);
       }
-      // v_w = c_w / s_w (padding rows carry c = 0 and give v = 0)
+      // reduce-scatter over the PX lanes: lane px ^ d holds my row k in its
+      // slot (d, k); v_w = c_w / s_w for my RK rows (padding rows carry c = 0
+      // and give v = 0), then the all-gather of the other slots' v
       float v[R];
 #pragma unroll
-      for (int rI = 0; rI < R; ++rI) v[rI] = cw[rI] * fast_rcp(s[rI]);
+      for (int k = 0; k < RK; ++k) {
+        float sk = s[k];
+#pragma unroll
+        for (int d = 1; d < PX; ++d) sk += __shfl_xor_sync(0xffffffffu, s[d * RK + k], d);
+        v[k] = cw[k] * fast_rcp(sk);
+      }
+#pragma unroll
+      for (int d = 1; d < PX; ++d) {
+#pragma unroll
+        for (int k = 0; k < RK; ++k) v[d * RK + k] = __shfl_xor_sync(0xffffffffu, v[k], d);
+      }
 
       if (!last) {
         // SpMM: x_i += K[w, i] v_w over my rows
@@ -308,10 +388,9 @@ __device__ __forceinline__ void solve(const LoopParams& p, const TeamCtx& t) {
       // reads back its columns' u
       // (u = 1 / x with x = diag(1/r) (K v):  u_i = r_i / (K v)_i)
 #pragma unroll
-      for (int q = 0; q < C2; ++q) {
-        const int col = (q >> 1) * 4 * PI + 4 * t.pi + 2 * (q & 1);
-        *reinterpret_cast<float2*>(&wpart[t.pw * VR + col]) = xp[q];
-      }
+      for (int h = 0; h < C2 / 2; ++h)
+        *reinterpret_cast<float4*>(&wpart[t.pw * kWS + lane_col(2 * h)]) =
+            make_float4(xp[2 * h].x, xp[2 * h].y, xp[2 * h + 1].x, xp[2 * h + 1].y);
       __syncwarp();
 #pragma unroll
       for (int j = 0; j < kLaneCols; ++j) {
@@ -319,15 +398,16 @@ __device__ __forceinline__ void solve(const LoopParams& p, const TeamCtx& t) {
         if (col < VR) {
           float x = 0.f;
 #pragma unroll
-          for (int k2 = 0; k2 < PW; ++k2) x += wpart[k2 * VR + col];
+          for (int k2 = 0; k2 < PW; ++k2) x += wpart[k2 * kWS + col];
           wu[col] = rcol[j] * fast_rcp(x);
         }
       }
       __syncwarp();
 #pragma unroll
-      for (int q = 0; q < C2; ++q) {
-        const int col = (q >> 1) * 4 * PI + 4 * t.pi + 2 * (q & 1);
-        u[q] = *reinterpret_cast<const float2*>(&wu[col]);
+      for (int h = 0; h < C2 / 2; ++h) {
+        const float4 uu = *reinterpret_cast<const float4*>(&wu[lane_col(2 * h)]);
+        u[2 * h] = make_float2(uu.x, uu.y);
+        u[2 * h + 1] = make_float2(uu.z, uu.w);
       }
     } else if (!last) {
       // x: sum over the PW row groups of the warp ...
@@ -351,10 +431,8 @@ __device__ __forceinline__ void solve(const LoopParams& p, const TeamCtx& t) {
         // deterministic, then u), and every lane reads back its columns' u
         if (t.pw == 0) {
 #pragma unroll
-          for (int q = 0; q < C2; ++q) {
-            const int col = (q >> 1) * 4 * PI + 4 * t.pi + 2 * (q & 1);
-            *reinterpret_cast<float2*>(&red[t.warp * VR + col]) = xp[q];
-          }
+          for (int q = 0; q < C2; ++q)
+            *reinterpret_cast<float2*>(&red[t.warp * VR + lane_col(q)]) = xp[q];
         }
         team_barrier(1 + t.team, 32 * t.W);
 #pragma unroll
@@ -368,10 +446,7 @@ __device__ __forceinline__ void solve(const LoopParams& p, const TeamCtx& t) {
         }
         team_barrier(1 + t.team, 32 * t.W);
 #pragma unroll
-        for (int q = 0; q < C2; ++q) {
-          const int col = (q >> 1) * 4 * PI + 4 * t.pi + 2 * (q & 1);
-          u[q] = *reinterpret_cast<const float2*>(&ured[col]);
-        }
+        for (int q = 0; q < C2; ++q) u[q] = *reinterpret_cast<const float2*>(&ured[lane_col(q)]);
       }
     }
   }
@@ -408,12 +483,17 @@ __global__ void __launch_bounds__(NW * 32, MINB) sinkhorn_fused_kernel(LoopParam
   constexpr int C = VR / PI;
   constexpr int PW = 32 / PI;
   constexpr int RPW = PW * RMAX;
-  constexpr int S = RMAX / 4;  // resident tiles come in 4 row-count steps
+  // resident tiles come in up to 4 row-count steps of RMAX / 4, each rounded
+  // up to a multiple of the reduce-scatter width
+  constexpr int PX = scatter_lanes(VR);
+  constexpr int R1 = round_up(RMAX / 4, PX), R2 = round_up(RMAX / 2, PX),
+                R3 = round_up(3 * RMAX / 4, PX);
   static_assert(C % 4 == 0, "columns per lane must be a multiple of 4");
   static_assert(RMAX % 4 == 0, "RMAX must split into 4 steps");
+  static_assert(RMAX % PX == 0, "RMAX must split over the reduce-scatter lanes");
 
   __shared__ __align__(16) float red[2 * NW * VR];
-  __shared__ __align__(16) float wpart[VR <= 32 ? NW * (PW + 1) * VR : 4];
+  __shared__ __align__(16) float wpart[VR <= 32 ? NW * (PW + 1) * wpart_stride(VR, PI) : 4];
   __shared__ double wred[NW];
 
   TeamCtx t;
@@ -459,13 +539,10 @@ __global__ void __launch_bounds__(NW * 32, MINB) sinkhorn_fused_kernel(LoopParam
     t.nch = start < t.n ? 1 : 0;
     const int len = t.nch ? min(t.rpw_res, t.n - start) : 0;
     const int reff = (len + PW - 1) / PW;
-    switch ((reff + S - 1) / S) {
-      case 0:
-      case 1: solve<VR, PI, 1 * S, false, KT>(p, t); break;
-      case 2: solve<VR, PI, 2 * S, false, KT>(p, t); break;
-      case 3: solve<VR, PI, 3 * S, false, KT>(p, t); break;
-      default: solve<VR, PI, 4 * S, false, KT>(p, t); break;
-    }
+    if (reff <= R1) solve<VR, PI, R1, false, KT>(p, t);
+    else if (reff <= R2) solve<VR, PI, R2, false, KT>(p, t);
+    else if (reff <= R3) solve<VR, PI, R3, false, KT>(p, t);
+    else solve<VR, PI, RMAX, false, KT>(p, t);
   } else {
     t.rpw_res = 0;
     const int nchunks_total = (t.n + RPW - 1) / RPW;
