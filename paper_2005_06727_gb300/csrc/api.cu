@@ -536,8 +536,15 @@ wmd_status wmd_query(wmd_corpus* c, const int32_t* q_ids, const float* q_w, int3
   std::lock_guard<std::mutex> lock(c->mu);
   DeviceGuard g(c->device);
   if (!c->stream) WMD_CUDA_TRY(cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking));
-  if (!c->h_stage)
+  if (!c->h_stage) {
     WMD_CUDA_TRY(cudaHostAlloc(&c->h_stage, (2 * WMD_MAX_VR + 4) * sizeof(int32_t), cudaHostAllocMapped));
+    const cudaError_t e = cudaHostGetDevicePointer(reinterpret_cast<void**>(&c->dh_stage), c->h_stage, 0);
+    if (e != cudaSuccess) {
+      cudaFreeHost(c->h_stage);
+      c->h_stage = nullptr;
+      return cuda_error(e, "cudaHostGetDevicePointer");
+    }
+  }
   // compact straight into the pinned staging block: ids, then weights
   int32_t* h_ids = c->h_stage;
   float* h_w = reinterpret_cast<float*>(c->h_stage + WMD_MAX_VR);
@@ -561,16 +568,21 @@ wmd_status wmd_query(wmd_corpus* c, const int32_t* q_ids, const float* q_w, int3
     WMD_CUDA_TRY(cudaMalloc(&c->ws, need));
     c->ws_bytes = need;
   }
-  if (!c->h_out)
+  if (!c->h_out) {
     WMD_CUDA_TRY(cudaHostAlloc(&c->h_out, std::max<int64_t>(c->N, 1) * sizeof(double), cudaHostAllocMapped));
+    const cudaError_t e = cudaHostGetDevicePointer(reinterpret_cast<void**>(&c->dh_out), c->h_out, 0);
+    if (e != cudaSuccess) {
+      cudaFreeHost(c->h_out);
+      c->h_out = nullptr;
+      return cuda_error(e, "cudaHostGetDevicePointer");
+    }
+  }
 
   // the query comes from, and the results and the error word go to, host
   // memory directly: the kernels read the mapped staging block (no copy in)
   // and the loop kernel writes the mapped output blocks (no copy back)
-  double* dh_out = nullptr;
-  int32_t* dh_stage = nullptr;
-  WMD_CUDA_TRY(cudaHostGetDevicePointer(reinterpret_cast<void**>(&dh_out), c->h_out, 0));
-  WMD_CUDA_TRY(cudaHostGetDevicePointer(reinterpret_cast<void**>(&dh_stage), c->h_stage, 0));
+  double* dh_out = c->dh_out;
+  int32_t* dh_stage = c->dh_stage;
   int* dh_err = dh_stage + 2 * WMD_MAX_VR;
   // a caller buffer that is pinned and mapped into the device's address space
   // takes the results directly (no copy out of the staging block)

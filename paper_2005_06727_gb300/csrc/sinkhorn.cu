@@ -150,10 +150,15 @@ __device__ __forceinline__ float fast_rcp(float x) {
 __host__ __device__ constexpr int round_up(int a, int b) { return (a + b - 1) / b * b; }
 
 // Row stride (floats) of the per-warp partial sums of x in shared memory.  A
-// quarter warp (two row groups of four lanes for PI = 4) stores 16 bytes per
-// lane at column 16 h + 4 pi: for 32-wide queries a stride of VR + 16 puts the
-// two row groups on different banks; narrower queries need no padding.
-__host__ __device__ constexpr int wpart_stride(int VR, int PI) { return VR / PI >= 8 ? VR + 16 : VR; }
+// quarter warp (8 / PI row groups pw of PI lanes pi) stores 16 bytes per lane
+// at column 4 PI h + 4 pi, i.e. 16-byte piece pw S/4 + PI h + pi of the
+// buffer: a stride S with S/4 = PI (mod 8) puts the eight pieces on distinct
+// banks.
+__host__ __device__ constexpr int wpart_stride(int VR, int PI) {
+  int s4 = VR / 4;
+  while (s4 % 8 != PI % 8) ++s4;
+  return 4 * s4;
+}
 
 // Lanes of the SDDMM reduce-scatter for a query tile VR wide (1 would be the
 // plain butterfly over all PI lanes).
@@ -483,13 +488,12 @@ __global__ void __launch_bounds__(NW * 32, MINB) sinkhorn_fused_kernel(LoopParam
   constexpr int C = VR / PI;
   constexpr int PW = 32 / PI;
   constexpr int RPW = PW * RMAX;
-  // resident tiles come in up to 4 row-count steps of RMAX / 4, each rounded
-  // up to a multiple of the reduce-scatter width
+  // resident tiles come in up to 4 row-count steps of about RMAX / 4, each
+  // rounded up to a multiple of the reduce-scatter width
   constexpr int PX = scatter_lanes(VR);
   constexpr int R1 = round_up(RMAX / 4, PX), R2 = round_up(RMAX / 2, PX),
                 R3 = round_up(3 * RMAX / 4, PX);
   static_assert(C % 4 == 0, "columns per lane must be a multiple of 4");
-  static_assert(RMAX % 4 == 0, "RMAX must split into 4 steps");
   static_assert(RMAX % PX == 0, "RMAX must split over the reduce-scatter lanes");
 
   __shared__ __align__(16) float red[2 * NW * VR];
@@ -555,12 +559,15 @@ __global__ void __launch_bounds__(NW * 32, MINB) sinkhorn_fused_kernel(LoopParam
 // RMAX * (VR / PI) floats of K per lane; the variants trade register tile
 // size (work per cross-lane reduction) against resident warps (latency
 // hiding), and wide queries use 8-warp CTAs so that a team of up to 8 warps
-// keeps a long document's K block resident.  The autotuner (wmd_autotune)
-// picks one per class and precision by timing.
+// keeps a long document's K block resident.  Two lanes per row (no butterfly
+// before the reduce-scatter) pay off for 16-wide queries but not for 32-wide
+// ones (RMAX 6: 2.54 against 2.16 us per iteration).  The autotuner
+// (wmd_autotune) picks one per class and precision by timing.
 template <int CLS, int V> struct Var;
 template <> struct Var<0, 0> { static constexpr int VR = 8, PI = 2, RMAX = 12, MINB = 4, NW = 4; };
 template <> struct Var<0, 1> { static constexpr int VR = 8, PI = 2, RMAX = 24, MINB = 2, NW = 4; };
 template <> struct Var<1, 0> { static constexpr int VR = 16, PI = 4, RMAX = 24, MINB = 3, NW = 4; };
+template <> struct Var<1, 1> { static constexpr int VR = 16, PI = 2, RMAX = 12, MINB = 3, NW = 4; };
 template <> struct Var<2, 0> { static constexpr int VR = 32, PI = 4, RMAX = 12, MINB = 3, NW = 4; };
 template <> struct Var<2, 1> { static constexpr int VR = 32, PI = 4, RMAX = 8, MINB = 4, NW = 4; };
 template <> struct Var<3, 0> { static constexpr int VR = 64, PI = 8, RMAX = 12, MINB = 3, NW = 4; };
@@ -605,7 +612,7 @@ cudaError_t dispatch_loop(int cls, int var, const LoopParams& p, int n_items, in
                           cudaStream_t s) {
   switch (cls) {
     case 0: return var ? launch_var<0, 1, KT>(p, n_items, nq, s) : launch_var<0, 0, KT>(p, n_items, nq, s);
-    case 1: return launch_var<1, 0, KT>(p, n_items, nq, s);
+    case 1: return var ? launch_var<1, 1, KT>(p, n_items, nq, s) : launch_var<1, 0, KT>(p, n_items, nq, s);
     case 2: return var ? launch_var<2, 1, KT>(p, n_items, nq, s) : launch_var<2, 0, KT>(p, n_items, nq, s);
     case 3: return var ? launch_var<3, 1, KT>(p, n_items, nq, s) : launch_var<3, 0, KT>(p, n_items, nq, s);
     case 4: return var ? launch_var<4, 1, KT>(p, n_items, nq, s) : launch_var<4, 0, KT>(p, n_items, nq, s);
@@ -621,7 +628,7 @@ constexpr int rpw() { return (32 / Var<CLS, V>::PI) * Var<CLS, V>::RMAX; }
 int rows_per_warp(int cls, int var) {
   switch (cls) {
     case 0: return var ? rpw<0, 1>() : rpw<0, 0>();
-    case 1: return rpw<1, 0>();
+    case 1: return var ? rpw<1, 1>() : rpw<1, 0>();
     case 2: return var ? rpw<2, 1>() : rpw<2, 0>();
     case 3: return var ? rpw<3, 1>() : rpw<3, 0>();
     case 4: return var ? rpw<4, 1>() : rpw<4, 0>();

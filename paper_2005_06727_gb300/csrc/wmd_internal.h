@@ -37,7 +37,7 @@ inline int vr_class(int v_r) {
 // Fused-loop tile variants per class (sinkhorn.cu) and the rows one warp of
 // variant `var` keeps in registers (row groups x rows per lane).
 constexpr int kMaxVariants = 2;
-constexpr int kClassVariants[kNumClasses] = {2, 1, 2, 2, 2, 2};
+constexpr int kClassVariants[kNumClasses] = {2, 2, 2, 2, 2, 2};
 int rows_per_warp(int cls, int var);
 int warps_per_cta(int cls, int var);  // 4 or 8
 
@@ -94,6 +94,8 @@ struct wmd_corpus {
   size_t ws_bytes = 0;
   int32_t* h_stage = nullptr;  // pinned, mapped: WMD_MAX_VR ids and WMD_MAX_VR weights (read by the cdist kernel), error word (written by the loop kernel)
   double* h_out = nullptr;     // pinned, mapped N doubles: the loop kernel writes the results here (host path)
+  int32_t* dh_stage = nullptr; // device addresses of the two mapped blocks
+  double* dh_out = nullptr;
   // captured host-path sequences, keyed by query shape (second use onwards)
   struct QueryGraph {
     int v_r, T, prec, variant;
