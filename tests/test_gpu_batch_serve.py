@@ -84,9 +84,9 @@ def test_query_into_pinned_output_buffers(wmd, setup):
     ro_ids.setflags(write=False)
     ro_w.setflags(write=False)
     assert np.array_equal(corpus.query(ro_ids, ro_w, 10.0, 15), ref)
-    wide = np.zeros((2, len(q_ids)), np.int32)
-    wide[0] = q_ids
-    assert np.array_equal(corpus.query(wide[0], q_w, 10.0, 15), ref)
+    strided = np.repeat(q_ids, 2)[::2]
+    assert not strided.flags.c_contiguous
+    assert np.array_equal(corpus.query(strided, q_w, 10.0, 15), ref)
     # an output buffer the library could not fill in place is refused
     for bad in (np.empty(c.N, np.float32), np.empty(2 * c.N)[::2], np.empty(c.N - 1)):
         with pytest.raises(ValueError):
