@@ -8,5 +8,6 @@ from .sinkhorn_wmd import (  # noqa: F401
     cdist,
     sinkhorn_wmd_dense,
     sinkhorn_wmd_sparse,
+    sinkhorn_wmd_sparse_until_converged,
     emd_uniform_bruteforce,
 )

@@ -168,6 +168,93 @@ def sinkhorn_wmd_sparse(q_ids, q_w, row_ptr, doc_idx, val, N, vecs, lam, max_ite
 
 
 # --------------------------------------------------------------------------
+# Algorithm 1's stopping rule "while x changes", per document
+# --------------------------------------------------------------------------
+def sinkhorn_wmd_sparse_until_converged(q_ids, q_w, row_ptr, doc_idx, val, N, vecs, lam,
+                                        max_iter, tol, iters=None, docs=None):
+    """The sparse form of Algorithm 1 with its loop condition "while x changes".
+
+    Algorithm 1 repeats its body while x changes; Sec. 3 caps the loop at
+    ``max_iter`` bodies.  Every column j of x depends only on column j of c, so
+    the test is taken per document: after body k (k = 1, 2, ...) has produced
+    x^(k), document j stops iterating when x no longer changes by more than
+    ``tol`` relative to its previous value,
+
+        rho_j^(k) = max_i |x^(k)_ij - x^(k-1)_ij| / x^(k-1)_ij  <=  tol,
+
+    or when k = max_iter.  Its result is then taken as after exactly T_j = k
+    bodies: u = 1/x^(k), one more SDDMM for v, and the WMD reduction.  A
+    stopped document's x is frozen while the others go on.  NaN never passes
+    the test, so an empty document (x^(1) = 0, then 0/0) runs max_iter bodies.
+    ``tol`` is taken in [0, 1).
+
+    ``iters`` (optional, int [N]) replaces the rule: document j then runs
+    exactly iters[j] bodies (0 <= iters[j] <= max_iter).  ``docs`` restricts
+    the computation to a subset of the documents, as in sinkhorn_wmd_sparse.
+
+    Returns (wmd [N], T [N] int, rho [max_iter, N]) where rho[k-1, j] is
+    rho_j^(k) while document j was still running and NaN afterwards.
+    """
+    if not 0.0 <= tol < 1.0:
+        raise ValueError("tol must lie in [0, 1)")
+    ids, r = select_nonzero(q_ids, q_w)
+    v_r = ids.shape[0]
+    row_ptr = np.asarray(row_ptr, dtype=np.int64)
+    V = row_ptr.shape[0] - 1
+    w_nz = np.repeat(np.arange(V, dtype=np.int64), np.diff(row_ptr))
+    j_nz = np.asarray(doc_idx, dtype=np.int64)
+    c_nz = np.asarray(val, dtype=np.float32).astype(np.float64)
+    if docs is not None:
+        docs = np.asarray(docs, dtype=np.int64)
+        pos = np.full(N, -1, dtype=np.int64)
+        pos[docs] = np.arange(docs.shape[0])
+        keep = pos[j_nz] >= 0
+        w_nz, j_nz, c_nz = w_nz[keep], pos[j_nz[keep]], c_nz[keep]
+        N = docs.shape[0]
+        if iters is not None:
+            iters = np.asarray(iters)[docs]
+
+    words = np.unique(w_nz)
+    col = np.searchsorted(words, w_nz)
+    M = cdist(vecs, ids, words)
+    K = np.exp(-lam * M)
+    KM = K * M
+    K_nz = K[:, col]
+
+    def spmm(A, v):
+        vs = sp.csr_matrix((v, (j_nz, col)), shape=(N, words.shape[0]))
+        return np.asarray((vs @ A.T).T)
+
+    x = np.ones((v_r, N)) / v_r
+    T = np.zeros(N, dtype=np.int64)
+    running = np.ones(N, dtype=bool) if iters is None else np.asarray(iters) > 0
+    rho = np.full((max(max_iter, 0), N), np.nan)
+    with np.errstate(divide="ignore", invalid="ignore"):
+        for k in range(1, max_iter + 1):
+            if not running.any():
+                break
+            u = 1.0 / x
+            s = np.sum(K_nz * u[:, j_nz], axis=0)       # SDDMM
+            v = c_nz / s
+            x_new = (1.0 / r)[:, None] * spmm(K, v)     # SpMM with K_over_r
+            change = np.max(np.abs(x_new - x) / x, axis=0) if v_r else np.zeros(N)
+            rho[k - 1, running] = change[running]
+            x[:, running] = x_new[:, running]           # stopped documents keep their x
+            T[running] = k
+            if iters is None:
+                running &= ~(change <= tol)             # "while x changes"
+                if k == max_iter:
+                    running[:] = False
+            else:
+                running &= np.asarray(iters) > k
+        u = 1.0 / x
+        s = np.sum(K_nz * u[:, j_nz], axis=0)
+        v = c_nz / s
+        wmd = np.sum(u * spmm(KM, v), axis=0)
+    return wmd, T, rho
+
+
+# --------------------------------------------------------------------------
 # Exact EMD for tiny equal-size uniform histograms (used to pin the oracle)
 # --------------------------------------------------------------------------
 def emd_uniform_bruteforce(M):

@@ -322,3 +322,119 @@ def test_planted_mistakes_are_caught(monkeypatch):
     want = np.sum(r * Mq) / np.sum(r)
     bad = no_r(q_ids, q_w, cw.row_ptr, cw.doc_idx, cw.val, cw.N, vecs, 10.0, 3)[0]
     assert abs(bad - want) > 1e-6 * want
+
+
+# ---------------------------------------------------------------- "while x changes"
+def _conv(vecs, c, q_ids, q_w, lam, T, tol, **kw):
+    return orc.sinkhorn_wmd_sparse_until_converged(q_ids, q_w, c.row_ptr, c.doc_idx, c.val, c.N,
+                                                   vecs, lam, T, tol, **kw)
+
+
+def test_forced_iteration_counts_equal_fixed_iteration_runs():
+    """Freezing a document after T_j bodies gives exactly the fixed-count
+    result at max_iter = T_j (columns of x are independent, Algorithm 1)."""
+    vecs, c, q_ids, q_w = _small_problem(N=12, seed=31)
+    T = np.random.default_rng(4).integers(0, 9, c.N)
+    T[3] = 0
+    wmd, got_T, _ = _conv(vecs, c, q_ids, q_w, 10.0, 8, 0.0, iters=T)
+    assert np.array_equal(got_T, T)
+    for t in np.unique(T):
+        docs = np.flatnonzero(T == t)
+        want = _sparse(vecs, c, q_ids, q_w, 10.0, int(t), docs=docs)
+        np.testing.assert_allclose(wmd[docs], want, rtol=1e-13)
+
+
+@pytest.mark.parametrize("tol", [1e-2, 1e-3])
+def test_stopping_rule_is_relative_change_of_x(tol):
+    """T_j is the first body k after which max_i |x^(k) - x^(k-1)| / x^(k-1)
+    <= tol; x^(k) is taken independently from fixed-count runs (x = 1/u)."""
+    vecs, c, q_ids, q_w = _small_problem(V=80, N=9, lo=3, hi=12, vr=6, seed=41)
+    T_max = 60
+    wmd, T, rho = _conv(vecs, c, q_ids, q_w, 10.0, T_max, tol)
+    assert T.min() >= 1 and T.min() < T_max          # the rule does stop some documents
+    xs = [np.full((len(q_ids), c.N), 1.0 / len(q_ids))]
+    for k in range(1, T_max + 1):
+        _, st = _sparse(vecs, c, q_ids, q_w, 10.0, k, return_state=True)
+        xs.append(1.0 / st["u"])
+    for j in range(c.N):
+        ch = [np.max(np.abs(xs[k][:, j] - xs[k - 1][:, j]) / xs[k - 1][:, j]) for k in range(1, T[j] + 1)]
+        np.testing.assert_allclose(rho[:T[j], j], ch, rtol=1e-9)
+        assert all(v > tol for v in ch[:-1])
+        assert ch[-1] <= tol or T[j] == T_max
+        assert np.all(np.isnan(rho[T[j]:, j]))
+        np.testing.assert_allclose(wmd[j], _sparse(vecs, c, q_ids, q_w, 10.0, int(T[j]), docs=[j])[0],
+                                   rtol=1e-12)
+
+
+def test_one_query_word_stops_after_one_body():
+    """v_r = 1: x^(1) = x^(0) sum_w c_wj / r, so x stops changing after one body
+    (to the rounding of the float32 weights) and WMD_j = sum_w c_wj m(q, w)."""
+    vecs, c, _, _ = _small_problem(seed=43)
+    q = 11
+    wmd, T, _ = _conv(vecs, c, np.array([q], np.int32), np.array([1.0], np.float32), 10.0, 30, 1e-6)
+    assert np.all(T == 1)
+    M1 = scipy.spatial.distance.cdist(vecs[[q]].astype(np.float64), vecs.astype(np.float64))[0]
+    want = np.array([np.sum(c.doc_vals[c.doc_ptr[j]:c.doc_ptr[j + 1]].astype(np.float64)
+                            * M1[c.doc_words[c.doc_ptr[j]:c.doc_ptr[j + 1]]]) for j in range(c.N)])
+    np.testing.assert_allclose(wmd, want, rtol=1e-12)
+
+
+def test_iterations_grow_as_tolerance_shrinks_and_cap_holds():
+    vecs, c, q_ids, q_w = _small_problem(N=10, seed=47)
+    prev = None
+    for tol in [1e-1, 1e-2, 1e-3, 1e-5]:
+        _, T, _ = _conv(vecs, c, q_ids, q_w, 10.0, 40, tol)
+        assert T.max() <= 40
+        if prev is not None:
+            assert np.all(T >= prev)
+        prev = T
+    with pytest.raises(ValueError):
+        _conv(vecs, c, q_ids, q_w, 10.0, 40, 1.0)
+
+
+def test_converged_stop_matches_entropic_dual_solution():
+    """With a tight tolerance the stopped result is the Sinkhorn fixed point,
+    the same <P*, M> that the L-BFGS dual solution of the test above gives."""
+    V, d = 12, 10
+    vecs = synth.make_vecs(V, d, 4)
+    q_ids = np.array([0, 2, 4], np.int32)
+    q_w = np.array([0.25, 0.5, 0.25], np.float32)
+    c = _one_doc_corpus(V, [5, 7, 9, 11], [0.125, 0.375, 0.25, 0.25])
+    lam = 3.0
+    got, T, _ = _conv(vecs, c, q_ids, q_w, lam, 5000, 1e-14)
+    assert T[0] < 5000
+    r = q_w.astype(np.float64)
+    cv = c.doc_vals.astype(np.float64)
+    M = scipy.spatial.distance.cdist(vecs[q_ids].astype(np.float64), vecs[c.doc_words].astype(np.float64))
+
+    def negdual(z):
+        f, g = z[:3], z[3:]
+        P = np.exp(lam * (f[:, None] + g[None, :] - M))
+        return -(f @ r + g @ cv - P.sum() / lam), -np.concatenate([r - P.sum(1), cv - P.sum(0)])
+
+    res = scipy.optimize.minimize(negdual, np.zeros(7), jac=True, method="L-BFGS-B",
+                                  options=dict(ftol=1e-15, gtol=1e-13, maxiter=10000))
+    f, g = res.x[:3], res.x[3:]
+    P = np.exp(lam * (f[:, None] + g[None, :] - M))
+    np.testing.assert_allclose(got, np.sum(P * M), rtol=1e-7)
+
+
+def test_empty_document_runs_to_the_cap():
+    vecs, c, q_ids, q_w = _small_problem(seed=53)
+    docs = [(c.doc_words[c.doc_ptr[j]:c.doc_ptr[j + 1]], c.doc_vals[c.doc_ptr[j]:c.doc_ptr[j + 1]]) for j in range(c.N)]
+    docs.insert(1, (np.zeros(0, np.int32), np.zeros(0, np.float32)))
+    c2 = synth.corpus_from_docs(c.V, docs)
+    wmd, T, _ = _conv(vecs, c2, q_ids, q_w, 10.0, 25, 1e-2)
+    assert T[1] == 25 and np.isnan(wmd[1])
+
+
+def test_planted_off_by_one_stop_is_caught():
+    """Stopping one body after the rule fires (a classic loop-condition slip)
+    is rejected by the relative-change pin."""
+    vecs, c, q_ids, q_w = _small_problem(V=80, N=9, lo=3, hi=12, vr=6, seed=41)
+    wmd, T, _ = _conv(vecs, c, q_ids, q_w, 10.0, 60, 1e-2)
+    late = np.minimum(T + 1, 60)
+    bad, _, _ = _conv(vecs, c, q_ids, q_w, 10.0, 60, 0.0, iters=late)
+    j = int(np.argmax(T < 60))
+    want = _sparse(vecs, c, q_ids, q_w, 10.0, int(T[j]), docs=[j])[0]
+    assert abs(bad[j] - want) > 1e-12 * abs(want)
