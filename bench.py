@@ -382,6 +382,51 @@ def bench_serving(wmd, device, n_requests=300, seed=11, workload="paper"):
 
 
 # ------------------------------------------------------------------ ours
+def bench_converge(wmd, corpus, dq, w, prec, stream, flush, reps=10):
+    """Algorithm 1's "while x changes" (wmd_query_device_tol) against the
+    fixed-count loop at the same cap, on the bench's corpus and query: time per
+    query (CUDA events, L2 flushed before each), WMDs/s, and how many bodies
+    the documents ran."""
+    import torch
+    N = corpus.N
+    iters = torch.empty(max(N, 1), dtype=torch.int32, device=dq.out.device)
+    rows = []
+    for T, tol in [(15, 1e-3), (100, 1e-2), (100, 1e-3)]:
+        def fixed():
+            corpus.query_device(dq.ids, dq.w, dq.v_r, w.lam, T, prec, dq.ws, dq.ws_bytes, dq.out,
+                                stream)
+
+        def conv():
+            corpus.query_device_tol(dq.ids, dq.w, dq.v_r, w.lam, T, tol, prec, dq.ws, dq.ws_bytes,
+                                    dq.out, iters, stream)
+
+        times = {}
+        for name, fn in (("fixed", fixed), ("until_converged", conv)):
+            for _ in range(3):
+                fn()
+            ts = []
+            for _ in range(reps):
+                flush.zero_()
+                a = torch.cuda.Event(enable_timing=True)
+                b = torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                fn()
+                b.record(stream)
+                b.synchronize()
+                ts.append(a.elapsed_time(b))
+            times[name] = statistics.mean(ts)
+        it = iters[:N].cpu().numpy()
+        rows.append({"max_iter": T, "tol": tol,
+                     "fixed_ms": times["fixed"], "until_converged_ms": times["until_converged"],
+                     "fixed_wmds_per_s": N / (times["fixed"] * 1e-3),
+                     "until_converged_wmds_per_s": N / (times["until_converged"] * 1e-3),
+                     "mean_bodies": float(it.mean()), "max_bodies": int(it.max()),
+                     "stopped_before_cap": float(np.mean(it < T))})
+    return {"what": "per query: cdist + fused loop, stopping each document once "
+                    "max_i |x' - x| / x <= tol (capped at max_iter) vs max_iter bodies for all",
+            "rows": rows}
+
+
 def run_ours(args, w):
     import torch
     import torch.distributed as dist
@@ -519,6 +564,7 @@ def run_ours(args, w):
         out["cpu_baseline"], ref = cpu_baseline(w, vecs, c, q_ids, q_w)
         out["error_vs_oracle"] = error_vs_oracle(out_np, ref, prec)
     if rank == 0 and not args.no_systems:
+        out["converge"] = bench_converge(wmd, corpus, dq, w, prec, stream, flush)
         out["batched"] = bench_batched(wmd, local_rank)
         out["serving"] = bench_serving(wmd, local_rank, args.serve_requests,
                                        workload=args.serving_workload)

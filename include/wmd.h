@@ -191,6 +191,60 @@ wmd_status wmd_query_device(wmd_corpus* corpus, const int32_t* d_q_ids,
                             size_t ws_bytes, double* d_out, void* stream);
 
 /* ---------------------------------------------------------------------------
+ * Convergence-tested query: Algorithm 1's loop condition "while x changes",
+ * with max_iter as the cap that Sec. 3 puts on the loop.
+ *
+ * The test is taken per document j (every column of x depends only on its
+ * own document): after loop body k has produced x^(k), document j stops when
+ *     max_i |x^(k)_ij - x^(k-1)_ij| / x^(k-1)_ij <= tol       (i < v_r),
+ * or when k = max_iter, and its WMD is then formed as after exactly k bodies
+ * (u = 1/x^(k), one more SDDMM for v, the reduction).  x^(0) = 1/v_r.
+ * The test runs in float32 on the GPU: a document whose relative change lies
+ * within float32 rounding of tol may stop one body earlier or later than an
+ * exact evaluation would.  An empty document never settles (x: 1/v_r, 0,
+ * 0/0) and runs max_iter bodies (its WMD is NaN, as in wmd_query).
+ *
+ * Arguments as wmd_query_device (device pointers, the same workspace size
+ * and layout, stream-ordered, asynchronous), plus:
+ *   tol      in [0, 1); 0 stops a document only when x no longer changes at
+ *            all in float32 (the result then equals wmd_query_device's).
+ *   d_iters  device int32[N] or NULL: the number of loop bodies each
+ *            document ran (1..max_iter, 0 when max_iter = 0).
+ * Errors: WMD_ERR_INVALID_ARG for a tol outside [0, 1) or NaN, and every
+ * error of wmd_query_device.
+ * ------------------------------------------------------------------------- */
+wmd_status wmd_query_device_tol(wmd_corpus* corpus, const int32_t* d_q_ids,
+                                const float* d_q_w, int32_t v_r, float lambda,
+                                int32_t max_iter, float tol, wmd_precision prec,
+                                void* d_ws, size_t ws_bytes, double* d_out,
+                                int32_t* d_iters, void* stream);
+
+/* ---------------------------------------------------------------------------
+ * k nearest documents.  The paper uses the WMD to find the documents closest
+ * to a query (k-nearest-neighbour retrieval, Sec. 1 and 2): these calls return
+ * the k smallest WMD values and their document ids.
+ *
+ * wmd_topk: selects from WMD[N] already on the device (d_wmd, e.g. the d_out
+ *   of wmd_query_device).  Output, ascending by value: d_idx[k] (int64
+ *   document ids) and d_val[k] (their WMD values, as stored in d_wmd).  Ties
+ *   go to the lower document id, -0 equals +0, and NaN (empty documents)
+ *   sorts after every number, so the result is unique.  Runs on the calling
+ *   thread's current device, stream-ordered on `stream` (NULL = legacy
+ *   default stream), asynchronous.  1 <= k <= min(N, 1024), else
+ *   WMD_ERR_INVALID_ARG; k = 0 does nothing.  Allocates nothing.
+ * wmd_query_device_topk: wmd_query_device (same arguments; d_out receives
+ *   all N values) followed by wmd_topk on its output, on the corpus's device.
+ * ------------------------------------------------------------------------- */
+wmd_status wmd_topk(const double* d_wmd, int64_t N, int32_t k, int64_t* d_idx, double* d_val,
+                    void* stream);
+
+wmd_status wmd_query_device_topk(wmd_corpus* corpus, const int32_t* d_q_ids,
+                                 const float* d_q_w, int32_t v_r, float lambda,
+                                 int32_t max_iter, wmd_precision prec, void* d_ws,
+                                 size_t ws_bytes, double* d_out, int32_t k, int64_t* d_idx,
+                                 double* d_val, void* stream);
+
+/* ---------------------------------------------------------------------------
  * Tile variants of the fused loop and their autotuner.  Every query width
  * class (v_r rounded up to 8, 16, 32, 64, 128 or 256) has one or more
  * register-tile shapes for the fused SDDMM/SpMM loop (same arithmetic, same

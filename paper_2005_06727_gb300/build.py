@@ -19,7 +19,8 @@ OBJ = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libwmd_gb300.so")
 ROOT = os.path.dirname(HERE)
 
-SOURCES = ["api.cu", "cdist.cu", "cdist_tc.cu", "sinkhorn.cu", "serve.cu", "noalloc.cu"]
+SOURCES = ["api.cu", "cdist.cu", "cdist_tc.cu", "sinkhorn.cu", "sinkhorn_conv.cu", "serve.cu",
+           "topk.cu", "noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          "--expt-relaxed-constexpr", "-I", os.path.join(ROOT, "include")]
@@ -49,7 +50,7 @@ def _stale(target: str, deps: list[str]) -> bool:
 def build(verbose: bool = False, ptxas_verbose: bool = False) -> str:
     """Compile (if needed) and return the path of the shared library."""
     os.makedirs(OBJ, exist_ok=True)
-    headers = [os.path.join(CSRC, h) for h in os.listdir(CSRC) if h.endswith(".h")]
+    headers = [os.path.join(CSRC, h) for h in os.listdir(CSRC) if h.endswith((".h", ".cuh"))]
     headers.append(os.path.join(ROOT, "include", "wmd.h"))
     exe = nvcc()
     jobs = []

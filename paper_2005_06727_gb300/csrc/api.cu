@@ -436,6 +436,52 @@ wmd_status wmd_query_device(wmd_corpus* c, const int32_t* d_q_ids, const float* 
   return wmd_sinkhorn_loop(c, v_r, max_iter, prec, d_ws, ws_bytes, d_out, stream);
 }
 
+wmd_status wmd_query_device_tol(wmd_corpus* c, const int32_t* d_q_ids, const float* d_q_w,
+                                int32_t v_r, float lambda, int32_t max_iter, float tol,
+                                wmd_precision prec, void* d_ws, size_t ws_bytes, double* d_out,
+                                int32_t* d_iters, void* stream) {
+  wmd_status st = check_query_args(c, v_r, lambda, max_iter);
+  if (st != WMD_OK) return st;
+  if (!(tol >= 0.f && tol < 1.f)) return set_error(WMD_ERR_INVALID_ARG, "tol must lie in [0, 1)");
+  if (!d_out && c->N > 0) return set_error(WMD_ERR_INVALID_ARG, "d_out is NULL");
+  st = wmd_build_kernel_matrix(c, d_q_ids, d_q_w, v_r, lambda, prec, d_ws, ws_bytes, stream);
+  if (st != WMD_OK) return st;
+  DeviceGuard g(c->device);
+  const int cls = vr_class(v_r);
+  const int VR = kClassVR[cls];
+  const WsLayout L = ws_layout(c, VR, prec);
+  char* ws = static_cast<char*>(d_ws);
+  const float* r = reinterpret_cast<const float*>(ws + L.r_off);
+  WMD_CUDA_TRY(launch_loop_conv(c, cls, ws + L.k_off, VR, r, r + VR, v_r, max_iter, tol, prec,
+                                d_out, d_iters, static_cast<cudaStream_t>(stream)));
+  return WMD_OK;
+}
+
+wmd_status wmd_topk(const double* d_wmd, int64_t N, int32_t k, int64_t* d_idx, double* d_val,
+                    void* stream) {
+  if (k == 0) return WMD_OK;
+  if (N < 0 || k < 0 || k > N || k > kTopkMaxK)
+    return set_error(WMD_ERR_INVALID_ARG, "k must satisfy 0 <= k <= min(N, 1024)");
+  if (!d_wmd || !d_idx || !d_val) return set_error(WMD_ERR_INVALID_ARG, "NULL pointer");
+  WMD_CUDA_TRY(launch_topk(d_wmd, N, k, d_idx, d_val, static_cast<cudaStream_t>(stream)));
+  return WMD_OK;
+}
+
+wmd_status wmd_query_device_topk(wmd_corpus* c, const int32_t* d_q_ids, const float* d_q_w,
+                                 int32_t v_r, float lambda, int32_t max_iter, wmd_precision prec,
+                                 void* d_ws, size_t ws_bytes, double* d_out, int32_t k,
+                                 int64_t* d_idx, double* d_val, void* stream) {
+  if (!c) return set_error(WMD_ERR_INVALID_ARG, "corpus is NULL");
+  if (k < 0 || k > c->N || k > kTopkMaxK)
+    return set_error(WMD_ERR_INVALID_ARG, "k must satisfy 0 <= k <= min(N, 1024)");
+  if (k > 0 && (!d_idx || !d_val)) return set_error(WMD_ERR_INVALID_ARG, "NULL output pointer");
+  wmd_status st = wmd_query_device(c, d_q_ids, d_q_w, v_r, lambda, max_iter, prec, d_ws, ws_bytes,
+                                   d_out, stream);
+  if (st != WMD_OK) return st;
+  DeviceGuard g(c->device);
+  return wmd_topk(d_out, c->N, k, d_idx, d_val, stream);
+}
+
 int32_t wmd_loop_variant_count(int32_t v_r) {
   const int cls = vr_class(v_r);
   return v_r > 0 && cls >= 0 ? kClassVariants[cls] : 0;

@@ -156,5 +156,16 @@ cudaError_t launch_loop_batch(const wmd_corpus* c, int cls, const void* K, int l
 cudaError_t launch_loop(const wmd_corpus* c, int cls, const void* K, int ldk, int kcol0,
                         const float* r, const float* lam, int v_r, int T, wmd_precision prec,
                         double* out, int* err_out, cudaStream_t s);
+// Top-k selection of WMD[N] (topk.cu): the k smallest values (ties: lower
+// document id first; NaN last) into out_idx / out_val, ascending.
+constexpr int kTopkMaxK = 1024;
+cudaError_t launch_topk(const double* wmd, int64_t N, int k, int64_t* out_idx, double* out_val,
+                        cudaStream_t s);
+// The convergence-tested loop (sinkhorn_conv.cu): at most T bodies, a
+// document stopping once |x' - x| <= tol x for all its query rows; iters
+// (optional, device) receives the bodies run per document.
+cudaError_t launch_loop_conv(const wmd_corpus* c, int cls, const void* K, int ldk,
+                             const float* r, const float* lam, int v_r, int T, float tol,
+                             wmd_precision prec, double* out, int32_t* iters, cudaStream_t s);
 
 }  // namespace wmd

@@ -6,7 +6,7 @@ missing the import of a function raises :class:`WMDError`.
 
 Names follow the C entry points: ``corpus_load`` / :class:`Corpus`,
 ``Corpus.query`` (``wmd_query``), ``Corpus.query_device``
-(``wmd_query_device``), ``Corpus.build_kernel_matrix``,
+(``wmd_query_device``), ``Corpus.query_device_tol`` (``wmd_query_device_tol``), ``Corpus.build_kernel_matrix``,
 ``Corpus.sinkhorn_loop`` and ``compact_query``.
 """
 from __future__ import annotations
@@ -78,6 +78,11 @@ _SIGS = {
     "wmd_sinkhorn_loop": (C.c_int, [_P, C.c_int32, C.c_int32, C.c_int, _P, C.c_size_t, _P, _P]),
     "wmd_query_device": (C.c_int, [_P, _P, _P, C.c_int32, C.c_float, C.c_int32, C.c_int, _P,
                                    C.c_size_t, _P, _P]),
+    "wmd_query_device_tol": (C.c_int, [_P, _P, _P, C.c_int32, C.c_float, C.c_int32, C.c_float,
+                                       C.c_int, _P, C.c_size_t, _P, _P, _P]),
+    "wmd_topk": (C.c_int, [_P, C.c_int64, C.c_int32, _P, _P, _P]),
+    "wmd_query_device_topk": (C.c_int, [_P, _P, _P, C.c_int32, C.c_float, C.c_int32, C.c_int, _P,
+                                        C.c_size_t, _P, C.c_int32, _P, _P, _P]),
     "wmd_query_device_noalloc": (C.c_int, [_P, _P, _P, C.c_int32, C.c_float, C.c_int32, C.c_int,
                                            _P, _P]),
     "wmd_query_batch": (C.c_int, [_P, C.c_int32, _P, _P, _P, _P, C.c_int32, C.c_int, _P]),
@@ -272,6 +277,32 @@ class Corpus:
         _check(lib().wmd_query_device(self._h, _dptr(d_ids), _dptr(d_w), int(v_r), float(lam),
                                       int(max_iter), int(prec), _dptr(ws), int(ws_bytes),
                                       _dptr(d_out), _stream_ptr(stream)))
+
+    def query_device_tol(self, d_ids, d_w, v_r, lam, max_iter, tol, prec, ws, ws_bytes, d_out,
+                         d_iters=None, stream=None):
+        """``wmd_query_device_tol``: stop each document once x stops changing
+        (relative change <= tol), at most max_iter bodies; ``d_iters``
+        (device int32 [N], optional) receives the bodies each document ran."""
+        _check(lib().wmd_query_device_tol(self._h, _dptr(d_ids), _dptr(d_w), int(v_r), float(lam),
+                                          int(max_iter), float(tol), int(prec), _dptr(ws),
+                                          int(ws_bytes), _dptr(d_out), _dptr(d_iters),
+                                          _stream_ptr(stream)))
+
+    def query_device_topk(self, d_ids, d_w, v_r, lam, max_iter, prec, ws, ws_bytes, d_out, k,
+                          d_idx, d_val, stream=None):
+        """``wmd_query_device_topk``: WMD[N] into ``d_out`` and the k nearest
+        documents (ascending) into ``d_idx`` (int64) and ``d_val`` (float64)."""
+        _check(lib().wmd_query_device_topk(self._h, _dptr(d_ids), _dptr(d_w), int(v_r), float(lam),
+                                           int(max_iter), int(prec), _dptr(ws), int(ws_bytes),
+                                           _dptr(d_out), int(k), _dptr(d_idx), _dptr(d_val),
+                                           _stream_ptr(stream)))
+
+
+def topk(d_wmd, N: int, k: int, d_idx, d_val, stream=None):
+    """``wmd_topk``: the k smallest of ``d_wmd[:N]`` (device float64) and their
+    document ids, ascending; ties to the lower id, NaN last."""
+    _check(lib().wmd_topk(_dptr(d_wmd), int(N), int(k), _dptr(d_idx), _dptr(d_val),
+                          _stream_ptr(stream)))
 
 
 def query_device_noalloc(corpus: "Corpus", d_ids, d_w, v_r, lam, max_iter, prec, d_out,
