@@ -427,6 +427,34 @@ def bench_converge(wmd, corpus, dq, w, prec, stream, flush, reps=10):
             "rows": rows}
 
 
+def bench_topk(wmd, dq, N, stream, reps=20):
+    """k nearest documents: wmd_topk on the bench query's WMD[N] (paper shape)
+    and on a WMD-like vector of the serving corpus's size (N = 200000), CUDA
+    events around each call (inputs in L2: one selection follows the loop
+    that wrote them)."""
+    import torch
+    rows = []
+    big = torch.from_numpy(1.2 + 0.3 * np.random.default_rng(0).random(200_000)).to(dq.out.device)
+    for name, src, n in (("paper-shaped WMD output", dq.out, N), ("N=200000 WMD-like values", big, 200_000)):
+        for k in (10, 100, 1024):
+            idx = torch.empty(k, dtype=torch.int64, device=src.device)
+            val = torch.empty(k, dtype=torch.float64, device=src.device)
+            for _ in range(3):
+                wmd.topk(src, n, k, idx, val, stream)
+            ts = []
+            for _ in range(reps):
+                a = torch.cuda.Event(enable_timing=True)
+                b = torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                wmd.topk(src, n, k, idx, val, stream)
+                b.record(stream)
+                b.synchronize()
+                ts.append(a.elapsed_time(b) * 1e3)
+            rows.append({"input": name, "N": n, "k": k, "us": statistics.mean(ts)})
+    return {"what": "one-CTA radix select of the k smallest WMD values (ties to the lower id)",
+            "rows": rows}
+
+
 def run_ours(args, w):
     import torch
     import torch.distributed as dist
@@ -565,6 +593,7 @@ def run_ours(args, w):
         out["error_vs_oracle"] = error_vs_oracle(out_np, ref, prec)
     if rank == 0 and not args.no_systems:
         out["converge"] = bench_converge(wmd, corpus, dq, w, prec, stream, flush)
+        out["topk"] = bench_topk(wmd, dq, c.N, stream)
         out["batched"] = bench_batched(wmd, local_rank)
         out["serving"] = bench_serving(wmd, local_rank, args.serve_requests,
                                        workload=args.serving_workload)

@@ -9,5 +9,6 @@ from .sinkhorn_wmd import (  # noqa: F401
     sinkhorn_wmd_dense,
     sinkhorn_wmd_sparse,
     sinkhorn_wmd_sparse_until_converged,
+    nearest_documents,
     emd_uniform_bruteforce,
 )

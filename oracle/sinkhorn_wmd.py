@@ -255,6 +255,23 @@ def sinkhorn_wmd_sparse_until_converged(q_ids, q_w, row_ptr, doc_idx, val, N, ve
 
 
 # --------------------------------------------------------------------------
+# k nearest documents (the retrieval use of the WMD, Sec. 1 and 2)
+# --------------------------------------------------------------------------
+def nearest_documents(wmd, k):
+    """The k documents with the smallest WMD, nearest first.
+
+    Ordering: by value (-0 equals +0), ties by the lower document id, and
+    every NaN (an empty document) after every number, so the answer is unique.
+    Returns (ids int64 [k], values float64 [k]).
+    """
+    w = np.asarray(wmd, dtype=np.float64)
+    order = sorted(range(w.shape[0]),
+                   key=lambda j: (bool(np.isnan(w[j])), 0.0 if np.isnan(w[j]) else float(w[j]), j))
+    ids = np.array(order[:k], dtype=np.int64)
+    return ids, w[ids]
+
+
+# --------------------------------------------------------------------------
 # Exact EMD for tiny equal-size uniform histograms (used to pin the oracle)
 # --------------------------------------------------------------------------
 def emd_uniform_bruteforce(M):

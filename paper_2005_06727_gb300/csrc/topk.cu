@@ -77,9 +77,17 @@ __global__ void __launch_bounds__(kThreads, 1)
   for (int shift = 56; shift >= 0; shift -= 8) {
     for (int b = tid; b < 256; b += kThreads) hist[b] = 0;
     __syncthreads();
-    for (int64_t i = tid; i < N; i += kThreads) {
-      const unsigned long long key = key_at(i);
-      if ((key & mask) == prefix) atomicAdd(&hist[(key >> shift) & 255u], 1u);
+    // warp-aggregated counts: WMD values share their leading bytes, so most
+    // keys of a pass land in few bins; lanes with the same byte add once
+    for (int64_t base = 0; base < N; base += kThreads) {
+      const int64_t i = base + tid;
+      int digit = -1;
+      if (i < N) {
+        const unsigned long long key = key_at(i);
+        if ((key & mask) == prefix) digit = (int)((key >> shift) & 255u);
+      }
+      const unsigned same = __match_any_sync(0xffffffffu, digit);
+      if (digit >= 0 && (tid & 31) == __ffs(same) - 1) atomicAdd(&hist[digit], (unsigned)__popc(same));
     }
     __syncthreads();
     if (tid < 32) {
@@ -118,6 +126,10 @@ __global__ void __launch_bounds__(kThreads, 1)
   // 3. take every key below kth (exactly k - need of them, in any slot
   //    order) and the first `need` keys equal to it in document order
   if (tid == 0) s_taken = 0;
+  for (int t = tid; t < kTopkMaxK; t += kThreads) {
+    s_key[t] = ~0ull;
+    s_idx[t] = 0;
+  }
   __syncthreads();
   const unsigned n_less = (unsigned)k - need;
   unsigned eq_seen = 0;  // equal keys met in earlier tiles (block-uniform)
@@ -126,16 +138,19 @@ __global__ void __launch_bounds__(kThreads, 1)
     const unsigned long long key = i < N ? key_at(i) : ~0ull;
     if (i < N && key < kth) {
       const unsigned slot = atomicAdd(&s_taken, 1u);
-      s_key[slot] = key;
-      s_idx[slot] = i;
+      if (slot < (unsigned)kTopkMaxK) {  // always: fewer than k keys lie below kth
+        s_key[slot] = key;
+        s_idx[slot] = i;
+      }
     }
     const bool eq = i < N && key == kth && eq_seen < need;
     const int n_eq = __syncthreads_count(eq);
     if (n_eq) {  // block-uniform
       const unsigned r = block_rank(eq, warp_sums, &s_total);
-      if (eq && eq_seen + r < need) {
-        s_key[n_less + eq_seen + r] = key;
-        s_idx[n_less + eq_seen + r] = i;
+      const unsigned slot = n_less + eq_seen + r;
+      if (eq && eq_seen + r < need && slot < (unsigned)kTopkMaxK) {
+        s_key[slot] = key;
+        s_idx[slot] = i;
       }
       eq_seen += (unsigned)n_eq;
     }
@@ -171,8 +186,9 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
   }
   for (int t = tid; t < k; t += kThreads) {
-    out_idx[t] = s_idx[t];
-    out_val[t] = wmd[s_idx[t]];
+    const long long j = s_idx[t];
+    out_idx[t] = j;
+    out_val[t] = (j >= 0 && j < N) ? wmd[j] : __longlong_as_double(0x7ff8000000000000ll);
   }
 }
 

@@ -438,3 +438,38 @@ def test_planted_off_by_one_stop_is_caught():
     j = int(np.argmax(T < 60))
     want = _sparse(vecs, c, q_ids, q_w, 10.0, int(T[j]), docs=[j])[0]
     assert abs(bad[j] - want) > 1e-12 * abs(want)
+
+
+# ---------------------------------------------------------------- k nearest documents
+def test_nearest_documents_against_repeated_minimum():
+    """Brute force: pick the smallest remaining (NaN last, ties to the lower
+    id) k times; -0 and +0 tie."""
+    rng = np.random.default_rng(5)
+    w = rng.choice([0.5, 1.25, 1.25, 2.0, -0.0, 0.0, np.nan, np.inf, -1.0], 40)
+    for k in (1, 5, 17, 40):
+        ids, vals = orc.nearest_documents(w, k)
+        left = list(range(w.size))
+        want = []
+        for _ in range(k):
+            best = left[0]
+            for j in left[1:]:
+                a, b = w[j], w[best]
+                if np.isnan(b) and not np.isnan(a):
+                    best = j
+                elif not np.isnan(a) and not np.isnan(b) and a < b:
+                    best = j
+            want.append(best)
+            left.remove(best)
+        assert ids.tolist() == want
+        assert np.array_equal(vals, w[want], equal_nan=True)
+
+
+def test_nearest_documents_matches_a_stable_sort():
+    """Against numpy's stable argsort (an independent ordering routine): NaN
+    sorts last there too, and a stable sort keeps equal values in id order."""
+    rng = np.random.default_rng(6)
+    w = np.round(rng.random(500) * 20) / 4
+    w[rng.choice(500, 30, replace=False)] = np.nan
+    w[w == 0] = -0.0
+    ids, _ = orc.nearest_documents(w, 200)
+    assert ids.tolist() == np.argsort(w + 0.0, kind="stable")[:200].tolist()
