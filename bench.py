@@ -455,6 +455,49 @@ def bench_topk(wmd, dq, N, stream, reps=20):
             "rows": rows}
 
 
+def bench_dense(wmd, corpus, dq, w, stream, flush, reps=5):
+    """Algorithm 1 in its dense form on the same GPU (wmd_query_dense: cuBLAS
+    SGEMMs for K^T u and K v over the active vocabulary, elementwise c ./ S)
+    against the sparse fused path, same query and max_iter, L2 flushed before
+    each call: the measured version of the paper's dense-versus-sparse
+    argument (Sec. 3, Table 1)."""
+    import torch
+    nbytes = corpus.dense_workspace_bytes(dq.v_r)
+    ws = torch.empty(nbytes, dtype=torch.uint8, device=dq.out.device)
+    corpus.dense_load_c(ws, nbytes, stream)
+    out = torch.empty_like(dq.out)
+
+    def run(fn):
+        for _ in range(2):
+            fn()
+        ts = []
+        for _ in range(reps):
+            flush.zero_()
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            fn()
+            b.record(stream)
+            b.synchronize()
+            ts.append(a.elapsed_time(b))
+        return statistics.mean(ts)
+
+    dense_ms = run(lambda: corpus.query_dense(dq.ids, dq.w, dq.v_r, w.lam, w.max_iter, ws, nbytes,
+                                              out, stream))
+    sparse_ms = run(lambda: corpus.query_device(dq.ids, dq.w, dq.v_r, w.lam, w.max_iter,
+                                                wmd.PREC_FP32, dq.ws, dq.ws_bytes, dq.out, stream))
+    a = out[: corpus.N].cpu().numpy()
+    b = dq.out[: corpus.N].cpu().numpy()
+    rel = float(np.max(np.abs(a - b) / np.maximum(np.abs(b), 1e-7)))
+    U, N = corpus.U, corpus.N
+    return {"what": "dense Algorithm 1 (S = K^T u over all U x N positions, v = c ./ S, x = K v) "
+                    "vs the sparse fused path, per query",
+            "dense_ms": dense_ms, "sparse_ms": sparse_ms, "ratio": dense_ms / sparse_ms,
+            "dense_wmds_per_s": N / (dense_ms * 1e-3), "workspace_bytes": nbytes,
+            "dense_positions": U * N, "nonzeros": corpus.nnz,
+            "max_rel_diff_dense_vs_sparse": rel}
+
+
 def run_ours(args, w):
     import torch
     import torch.distributed as dist
@@ -594,6 +637,8 @@ def run_ours(args, w):
     if rank == 0 and not args.no_systems:
         out["converge"] = bench_converge(wmd, corpus, dq, w, prec, stream, flush)
         out["topk"] = bench_topk(wmd, dq, c.N, stream)
+        if prec == wmd.PREC_FP32:
+            out["dense"] = bench_dense(wmd, corpus, dq, w, stream, flush)
         out["batched"] = bench_batched(wmd, local_rank)
         out["serving"] = bench_serving(wmd, local_rank, args.serve_requests,
                                        workload=args.serving_workload)

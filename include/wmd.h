@@ -245,6 +245,38 @@ wmd_status wmd_query_device_topk(wmd_corpus* corpus, const int32_t* d_q_ids,
                                  double* d_val, void* stream);
 
 /* ---------------------------------------------------------------------------
+ * Dense Algorithm 1 on the GPU: a comparator for the sparse path.  Sec. 3
+ * ("Dense to Sparse Kernel", Table 1) argues that the dense form spends its
+ * time computing K^T u at every (word, document) position although only the
+ * nonzeros of c are used.  These calls run that dense form literally, so the
+ * argument can be measured on one GPU: per loop body S = K^T u (U x N),
+ * v = c .* (1 ./ S), x = diag(1/r) K v, u = 1 ./ x; then the final update and
+ * WMD_j = sum_i u_ij ((K .* M) v)_ij.  U is the corpus's active vocabulary
+ * (the dense c is zero on every other word).  The two GEMMs per body are
+ * cuBLAS SGEMM in FP32; the elementwise steps are this library's kernels.
+ * K is the FP32 K of wmd_build_kernel_matrix; results match wmd_query_device
+ * within the FP32 tolerance (summation order differs).
+ *
+ * wmd_dense_workspace_bytes: device bytes for a query of v_r words, 0 if v_r
+ *   is out of range: 8 U N (dense c and S) + the query workspace + 8 VR N +
+ *   4 VR U, each region 256-byte aligned.
+ * wmd_dense_load_c: writes the dense U x N c (column j = document j) at the
+ *   start of d_ws (asynchronous on `stream`).  Call once per workspace; the
+ *   query calls read it and never write it.
+ * wmd_query_dense: the dense Algorithm 1 for one query (device pointers as
+ *   wmd_query_device, asynchronous on `stream`); d_out receives WMD[N].  The
+ *   first call on a device creates a cuBLAS handle (allocates).  Errors:
+ *   WMD_ERR_INVALID_ARG (arguments, workspace too small), WMD_ERR_UNSUPPORTED
+ *   (U or N above 2^31 - 1), WMD_ERR_CUDA / WMD_ERR_OUT_OF_MEMORY from CUDA or
+ *   cuBLAS.  Calls on one device are serialised by a lock while they enqueue.
+ * ------------------------------------------------------------------------- */
+size_t wmd_dense_workspace_bytes(const wmd_corpus* corpus, int32_t v_r);
+wmd_status wmd_dense_load_c(wmd_corpus* corpus, void* d_ws, size_t ws_bytes, void* stream);
+wmd_status wmd_query_dense(wmd_corpus* corpus, const int32_t* d_q_ids, const float* d_q_w,
+                           int32_t v_r, float lambda, int32_t max_iter, void* d_ws,
+                           size_t ws_bytes, double* d_out, void* stream);
+
+/* ---------------------------------------------------------------------------
  * Tile variants of the fused loop and their autotuner.  Every query width
  * class (v_r rounded up to 8, 16, 32, 64, 128 or 256) has one or more
  * register-tile shapes for the fused SDDMM/SpMM loop (same arithmetic, same

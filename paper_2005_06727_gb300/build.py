@@ -20,7 +20,9 @@ LIB = os.path.join(HERE, "libwmd_gb300.so")
 ROOT = os.path.dirname(HERE)
 
 SOURCES = ["api.cu", "cdist.cu", "cdist_tc.cu", "sinkhorn.cu", "sinkhorn_conv.cu", "serve.cu",
-           "topk.cu", "noalloc.cu"]
+           "topk.cu", "dense.cu", "noalloc.cu"]
+# cuBLAS serves the dense comparator's two plain GEMMs (dense.cu)
+LIBS = ["-lcublas", "-Xlinker", "-rpath,/usr/local/cuda/lib64"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          "--expt-relaxed-constexpr", "-I", os.path.join(ROOT, "include")]
@@ -71,7 +73,7 @@ def build(verbose: bool = False, ptxas_verbose: bool = False) -> str:
     objs = [os.path.join(OBJ, s.replace(".cu", ".o")) for s in _sources()]
     if jobs or _stale(LIB, objs):
         tmp = LIB + ".tmp"
-        cmd = [exe, *ARCH, "-shared", "-o", tmp, *objs]
+        cmd = [exe, *ARCH, "-shared", "-o", tmp, *objs, *LIBS]
         res = subprocess.run(cmd, capture_output=True, text=True)
         if res.returncode != 0:
             sys.stderr.write(" ".join(cmd) + "\n" + res.stdout + res.stderr)

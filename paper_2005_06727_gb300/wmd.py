@@ -83,6 +83,10 @@ _SIGS = {
     "wmd_topk": (C.c_int, [_P, C.c_int64, C.c_int32, _P, _P, _P]),
     "wmd_query_device_topk": (C.c_int, [_P, _P, _P, C.c_int32, C.c_float, C.c_int32, C.c_int, _P,
                                         C.c_size_t, _P, C.c_int32, _P, _P, _P]),
+    "wmd_dense_workspace_bytes": (C.c_size_t, [_P, C.c_int32]),
+    "wmd_dense_load_c": (C.c_int, [_P, _P, C.c_size_t, _P]),
+    "wmd_query_dense": (C.c_int, [_P, _P, _P, C.c_int32, C.c_float, C.c_int32, _P, C.c_size_t, _P,
+                                  _P]),
     "wmd_query_device_noalloc": (C.c_int, [_P, _P, _P, C.c_int32, C.c_float, C.c_int32, C.c_int,
                                            _P, _P]),
     "wmd_query_batch": (C.c_int, [_P, C.c_int32, _P, _P, _P, _P, C.c_int32, C.c_int, _P]),
@@ -296,6 +300,21 @@ class Corpus:
                                            int(max_iter), int(prec), _dptr(ws), int(ws_bytes),
                                            _dptr(d_out), int(k), _dptr(d_idx), _dptr(d_val),
                                            _stream_ptr(stream)))
+
+    # -------------------------------------------------------------- dense comparator
+    def dense_workspace_bytes(self, v_r: int) -> int:
+        """``wmd_dense_workspace_bytes``."""
+        return int(lib().wmd_dense_workspace_bytes(self._h, int(v_r)))
+
+    def dense_load_c(self, ws, ws_bytes, stream=None):
+        """``wmd_dense_load_c``: the dense U x N c at the start of ``ws``."""
+        _check(lib().wmd_dense_load_c(self._h, _dptr(ws), int(ws_bytes), _stream_ptr(stream)))
+
+    def query_dense(self, d_ids, d_w, v_r, lam, max_iter, ws, ws_bytes, d_out, stream=None):
+        """``wmd_query_dense``: Algorithm 1 in its dense form (cuBLAS GEMMs)."""
+        _check(lib().wmd_query_dense(self._h, _dptr(d_ids), _dptr(d_w), int(v_r), float(lam),
+                                     int(max_iter), _dptr(ws), int(ws_bytes), _dptr(d_out),
+                                     _stream_ptr(stream)))
 
 
 def topk(d_wmd, N: int, k: int, d_idx, d_val, stream=None):
