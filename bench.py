@@ -48,6 +48,8 @@ def parse():
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="paper")
     ap.add_argument("--prec", choices=["fp32", "bf16"], default="fp32")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--legs", default="converge,topk,dense,batched,serving",
+                    help="comma-separated extra legs to run after the timed step")
     ap.add_argument("--no-systems", action="store_true",
                     help="skip the batched and served measurements")
     ap.add_argument("--serve-requests", type=int, default=300)
@@ -634,14 +636,19 @@ def run_ours(args, w):
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"], ref = cpu_baseline(w, vecs, c, q_ids, q_w)
         out["error_vs_oracle"] = error_vs_oracle(out_np, ref, prec)
+    legs = set(args.legs.split(",")) if args.legs else set()
     if rank == 0 and not args.no_systems:
-        out["converge"] = bench_converge(wmd, corpus, dq, w, prec, stream, flush)
-        out["topk"] = bench_topk(wmd, dq, c.N, stream)
-        if prec == wmd.PREC_FP32:
+        if "converge" in legs:
+            out["converge"] = bench_converge(wmd, corpus, dq, w, prec, stream, flush)
+        if "topk" in legs:
+            out["topk"] = bench_topk(wmd, dq, c.N, stream)
+        if "dense" in legs and prec == wmd.PREC_FP32:
             out["dense"] = bench_dense(wmd, corpus, dq, w, stream, flush)
-        out["batched"] = bench_batched(wmd, local_rank)
-        out["serving"] = bench_serving(wmd, local_rank, args.serve_requests,
-                                       workload=args.serving_workload)
+        if "batched" in legs:
+            out["batched"] = bench_batched(wmd, local_rank)
+        if "serving" in legs:
+            out["serving"] = bench_serving(wmd, local_rank, args.serve_requests,
+                                           workload=args.serving_workload)
     if rank == 0:
         print(json.dumps(out))
     corpus.close()

@@ -231,7 +231,8 @@ wmd_status wmd_query_device_tol(wmd_corpus* corpus, const int32_t* d_q_ids,
  *   sorts after every number, so the result is unique.  Runs on the calling
  *   thread's current device, stream-ordered on `stream` (NULL = legacy
  *   default stream), asynchronous.  1 <= k <= min(N, 1024), else
- *   WMD_ERR_INVALID_ARG; k = 0 does nothing.  Allocates nothing.
+ *   WMD_ERR_INVALID_ARG; k = 0 does nothing; N above 2^31 - 1 gives
+ *   WMD_ERR_UNSUPPORTED.  Allocates nothing.
  * wmd_query_device_topk: wmd_query_device (same arguments; d_out receives
  *   all N values) followed by wmd_topk on its output, on the corpus's device.
  * ------------------------------------------------------------------------- */

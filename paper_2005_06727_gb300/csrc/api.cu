@@ -463,6 +463,7 @@ wmd_status wmd_topk(const double* d_wmd, int64_t N, int32_t k, int64_t* d_idx, d
   if (N < 0 || k < 0 || k > N || k > kTopkMaxK)
     return set_error(WMD_ERR_INVALID_ARG, "k must satisfy 0 <= k <= min(N, 1024)");
   if (!d_wmd || !d_idx || !d_val) return set_error(WMD_ERR_INVALID_ARG, "NULL pointer");
+  if (N > INT32_MAX) return set_error(WMD_ERR_UNSUPPORTED, "N above 2^31 - 1");
   WMD_CUDA_TRY(launch_topk(d_wmd, N, k, d_idx, d_val, static_cast<cudaStream_t>(stream)));
   return WMD_OK;
 }

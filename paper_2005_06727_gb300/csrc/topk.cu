@@ -3,13 +3,24 @@
 //
 // One CTA of 1024 threads selects from WMD[N] (written by the fused loop):
 //   1. every value is mapped to a 64-bit key whose unsigned order is the
-//      numeric order (-0 counts as +0, every NaN after every number);
-//   2. a radix select over the key's eight bytes, most significant first,
-//      finds the k-th smallest key K* (a 256-bin shared-memory histogram of
-//      the keys that match the bytes chosen so far, per pass);
-//   3. one pass in document order takes every key below K* and the first
-//      keys equal to K* (lowest document ids) until k are taken;
-//   4. a bitonic sort in shared memory orders the k by (key, document id).
+//      numeric order (-0 counts as +0, every NaN after every number); one
+//      sweep finds the smallest and largest key, whose common leading bits
+//      every key shares (WMD values lie close together, so this skips the
+//      sign, the exponent and a few mantissa bits);
+//   2. a radix select over the remaining bits, 8 per pass, most significant
+//      first, finds the k-th smallest key K*: per pass one 256-bin
+//      shared-memory histogram of the keys that match the bits chosen so
+//      far, counted with warp-aggregated atomics (lanes with the same byte
+//      add once; warps without a matching key skip the count) and scanned
+//      by every warp for itself, so a pass needs one
+//      barrier (three histogram buffers rotate, one being cleared while
+//      another fills);
+//   3. a sweep takes every key below K* and the first keys equal to K*
+//      (lowest document ids) until k are taken; when K* occurs exactly as
+//      often as still needed, any order will do and the sweep takes no
+//      barrier per tile;
+//   4. the k taken are ordered by (key, document id): by counting ranks for
+//      k <= 256, else by a bitonic sort.
 // Ties are broken by the lower document id, so the result is unique.  When
 // N keys fit in shared memory (N <= kCacheMax) they are read from global
 // memory once and kept there for all passes.
@@ -18,19 +29,32 @@
 namespace wmd {
 namespace {
 
-constexpr int kThreads = 1024;
-constexpr int kCacheMax = 12288;  // keys kept in shared memory (96 KB)
-static_assert(kTopkMaxK <= kThreads * 4, "sort loop bound");
+// Threads per CTA for keys streamed from global memory and for keys kept in
+// shared memory (256 for the latter was measured slower at N = 5000: 22.6
+// against 21.1 us for k = 10, 50.6 against 42.1 us for k = 1024).
+constexpr int kThreadsStream = 1024;
+constexpr int kThreadsCached = 1024;
+constexpr int kCacheMax = 12288;   // keys kept in shared memory (96 KB)
+constexpr int kUnroll = 8;         // independent key loads in flight per thread
+constexpr int kRankSortMax = 256;  // k up to this: rank counting (one entry per thread), else bitonic
+static_assert(kRankSortMax <= kThreadsCached && kRankSortMax <= kThreadsStream, "rank sort");
+constexpr int kCandMax = 8192;     // candidate list capacity (indices)
+constexpr int kSmall = 256;        // candidates few enough to rank directly
+static_assert(kTopkMaxK * 12 <= kCandMax * 4, "the spare list holds kTopkMaxK keys and ids");
 
-__device__ __forceinline__ unsigned long long order_key(double x) {
-  if (x != x) return ~0ull;          // NaN: after every number
-  if (x == 0.0) x = 0.0;             // -0 and +0 are equal
-  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+// From the value's bits, loaded as an integer: the FP64 pipe of this GPU is
+// too slow to test every value with floating-point compares (and integer tests
+// on a reinterpreted double may be folded back into them by the compiler).
+__device__ __forceinline__ unsigned long long order_key(unsigned long long b) {
+  const unsigned long long mag = b & 0x7fffffffffffffffull;
+  if (mag > 0x7ff0000000000000ull) return ~0ull;  // NaN: after every number
+  if (mag == 0) b = 0;                              // -0 and +0 are equal
   return (b >> 63) ? ~b : (b | 0x8000000000000000ull);
 }
 
 // Block-wide exclusive prefix count of `flag` (every thread calls it);
 // returns this thread's rank and writes the block total to *total.
+template <int NT>
 __device__ __forceinline__ unsigned block_rank(bool flag, unsigned* warp_sums, unsigned* total) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const unsigned ball = __ballot_sync(0xffffffffu, flag);
@@ -38,7 +62,7 @@ __device__ __forceinline__ unsigned block_rank(bool flag, unsigned* warp_sums, u
   if (lane == 0) warp_sums[warp] = __popc(ball);
   __syncthreads();
   if (warp == 0) {
-    const unsigned v = warp_sums[lane];
+    const unsigned v = lane < NT / 32 ? warp_sums[lane] : 0u;
     unsigned s = v;
 #pragma unroll
     for (int off = 1; off < 32; off <<= 1) {
@@ -54,138 +78,306 @@ __device__ __forceinline__ unsigned block_rank(bool flag, unsigned* warp_sums, u
   return r;
 }
 
-template <bool CACHED>
-__global__ void __launch_bounds__(kThreads, 1)
+// Visits the keys of the current candidate set in blocks of NT *
+// kUnroll (every thread runs the same number of iterations, so warp
+// collectives inside `f` are safe).  The set is either the whole array
+// filtered by (key & mask) == prefix (full) or an explicit index list.
+template <bool CACHED, int NT, typename F>
+__device__ __forceinline__ void sweep(const unsigned long long* __restrict__ bits,
+                                      const unsigned long long* cache,
+                                      int64_t N, bool full, const int* list, unsigned nlist,
+                                      unsigned long long mask, unsigned long long prefix, F&& f) {
+  const int64_t n = full ? N : (int64_t)nlist;
+  for (int64_t base = 0; base < n; base += (int64_t)NT * kUnroll) {
+    unsigned long long key[kUnroll];
+    int64_t idx[kUnroll];
+#pragma unroll
+    for (int u = 0; u < kUnroll; ++u) {
+      const int64_t t = base + u * NT + threadIdx.x;
+      idx[u] = t < n ? (full ? t : (int64_t)list[t]) : -1;
+      key[u] = idx[u] >= 0 ? (CACHED ? cache[idx[u]] : order_key(__ldg(bits + idx[u]))) : ~0ull;
+    }
+#pragma unroll
+    for (int u = 0; u < kUnroll; ++u) {
+      const bool in = idx[u] >= 0 && (!full || (key[u] & mask) == prefix);
+      f(in, key[u], idx[u]);
+    }
+  }
+}
+
+template <bool CACHED, int NT>
+__global__ void __launch_bounds__(NT, 1)
     topk_kernel(const double* __restrict__ wmd, int64_t N, int k, int64_t* __restrict__ out_idx,
                 double* __restrict__ out_val) {
-  extern __shared__ unsigned long long cache[];  // N keys when CACHED
-  __shared__ unsigned hist[256];
+  // dynamic: [N keys if CACHED][two candidate lists of kCandMax indices]
+  extern __shared__ __align__(16) unsigned char dyn[];
+  unsigned long long* cache = reinterpret_cast<unsigned long long*>(dyn);
+  int* cand[2];
+  cand[0] = reinterpret_cast<int*>(dyn + (CACHED ? (size_t)N * sizeof(unsigned long long) : 0));
+  cand[1] = cand[0] + kCandMax;
+  __shared__ unsigned hist[3][256];
   __shared__ unsigned warp_sums[32];
-  __shared__ unsigned s_total, s_digit, s_need, s_taken;
+  constexpr int kWarps = NT / 32;
+  __shared__ unsigned long long s_min[kWarps], s_max[kWarps];
+  __shared__ unsigned s_total, s_taken, s_ncand[2];
   __shared__ unsigned long long s_key[kTopkMaxK];
   __shared__ long long s_idx[kTopkMaxK];
-  const int tid = threadIdx.x;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const unsigned long long* bits = reinterpret_cast<const unsigned long long*>(wmd);
+  auto key_at = [&](int64_t i) { return CACHED ? cache[i] : order_key(__ldg(bits + i)); };
 
-  auto key_at = [&](int64_t i) { return CACHED ? cache[i] : order_key(wmd[i]); };
-  if (CACHED) {
-    for (int64_t i = tid; i < N; i += kThreads) cache[i] = order_key(wmd[i]);
-  }
-
-  // 2. radix select of the k-th smallest key, one byte per pass
-  unsigned long long prefix = 0, mask = 0;
-  unsigned need = (unsigned)k;  // rank of the target among the keys matching prefix
-  for (int shift = 56; shift >= 0; shift -= 8) {
-    for (int b = tid; b < 256; b += kThreads) hist[b] = 0;
-    __syncthreads();
-    // warp-aggregated counts: WMD values share their leading bytes, so most
-    // keys of a pass land in few bins; lanes with the same byte add once
-    for (int64_t base = 0; base < N; base += kThreads) {
-      const int64_t i = base + tid;
-      int digit = -1;
+  // 1. smallest and largest key (and the shared-memory copy of the keys)
+  unsigned long long kmin = ~0ull, kmax = 0;
+  for (int64_t base = 0; base < N; base += (int64_t)NT * kUnroll) {
+    unsigned long long key[kUnroll];
+#pragma unroll
+    for (int u = 0; u < kUnroll; ++u) {
+      const int64_t i = base + u * NT + tid;
+      key[u] = i < N ? order_key(__ldg(bits + i)) : ~0ull;
+    }
+#pragma unroll
+    for (int u = 0; u < kUnroll; ++u) {
+      const int64_t i = base + u * NT + tid;
       if (i < N) {
-        const unsigned long long key = key_at(i);
-        if ((key & mask) == prefix) digit = (int)((key >> shift) & 255u);
-      }
-      const unsigned same = __match_any_sync(0xffffffffu, digit);
-      if (digit >= 0 && (tid & 31) == __ffs(same) - 1) atomicAdd(&hist[digit], (unsigned)__popc(same));
-    }
-    __syncthreads();
-    if (tid < 32) {
-      // lane l holds bins 8 l .. 8 l + 7; find the bin where the running
-      // count first reaches `need`
-      unsigned c[8], sum = 0;
-#pragma unroll
-      for (int q = 0; q < 8; ++q) {
-        c[q] = hist[8 * tid + q];
-        sum += c[q];
-      }
-      unsigned incl = sum;
-#pragma unroll
-      for (int off = 1; off < 32; off <<= 1) {
-        const unsigned o = __shfl_up_sync(0xffffffffu, incl, off);
-        if (tid >= off) incl += o;
-      }
-      const unsigned excl = incl - sum;
-      const unsigned hit = __ballot_sync(0xffffffffu, excl < need && need <= incl);
-      if (tid == __ffs(hit) - 1) {
-        unsigned run = excl;
-        int q = 0;
-        while (run + c[q] < need) run += c[q++];
-        s_digit = 8 * tid + q;
-        s_need = need - run;
+        if (CACHED) cache[i] = key[u];
+        kmin = key[u] < kmin ? key[u] : kmin;
+        kmax = key[u] > kmax ? key[u] : kmax;
       }
     }
-    __syncthreads();
-    prefix |= (unsigned long long)s_digit << shift;
-    mask |= 255ull << shift;
-    need = s_need;
-    __syncthreads();
   }
-  const unsigned long long kth = prefix;  // the k-th smallest key
-
-  // 3. take every key below kth (exactly k - need of them, in any slot
-  //    order) and the first `need` keys equal to it in document order
-  if (tid == 0) s_taken = 0;
-  for (int t = tid; t < kTopkMaxK; t += kThreads) {
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    const unsigned long long a = __shfl_xor_sync(0xffffffffu, kmin, off);
+    const unsigned long long b = __shfl_xor_sync(0xffffffffu, kmax, off);
+    kmin = a < kmin ? a : kmin;
+    kmax = b > kmax ? b : kmax;
+  }
+  if (lane == 0) {
+    s_min[warp] = kmin;
+    s_max[warp] = kmax;
+  }
+  for (int t = tid; t < 2 * 256; t += NT) hist[t >> 8][t & 255] = 0;
+  for (int t = tid; t < kTopkMaxK; t += NT) {
     s_key[t] = ~0ull;
     s_idx[t] = 0;
   }
+  if (tid == 0) {
+    s_taken = 0;
+    s_ncand[0] = s_ncand[1] = 0;
+  }
   __syncthreads();
-  const unsigned n_less = (unsigned)k - need;
-  unsigned eq_seen = 0;  // equal keys met in earlier tiles (block-uniform)
-  for (int64_t base = 0; base < N; base += kThreads) {
-    const int64_t i = base + tid;
-    const unsigned long long key = i < N ? key_at(i) : ~0ull;
-    if (i < N && key < kth) {
-      const unsigned slot = atomicAdd(&s_taken, 1u);
-      if (slot < (unsigned)kTopkMaxK) {  // always: fewer than k keys lie below kth
-        s_key[slot] = key;
-        s_idx[slot] = i;
+  kmin = lane < kWarps ? s_min[lane] : ~0ull;  // one warp's total per lane, then a butterfly
+  kmax = lane < kWarps ? s_max[lane] : 0ull;
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    const unsigned long long a = __shfl_xor_sync(0xffffffffu, kmin, off);
+    const unsigned long long b = __shfl_xor_sync(0xffffffffu, kmax, off);
+    kmin = a < kmin ? a : kmin;
+    kmax = b > kmax ? b : kmax;
+  }
+
+  // 2. radix select over the bits below the common prefix of kmin and kmax.
+  //    Each pass histograms the next byte of the current candidates, emits
+  //    the keys of the bins below the k-th key's bin (they are among the k)
+  //    and moves the keys of its bin to the next candidate list, until at
+  //    most kSmall candidates are left or every bit is decided.
+  int hi = kmin == kmax ? 0 : 64 - __clzll((long long)(kmin ^ kmax));  // undecided low bits
+  unsigned long long mask = hi == 64 ? 0ull : ~((1ull << hi) - 1ull);
+  unsigned long long prefix = kmin & mask;
+  unsigned need = (unsigned)k;  // rank of the k-th key among the candidates
+  bool full = true;             // candidates: all keys matching prefix, else cand[cur]
+  int cur = 0;
+  unsigned ncand = (unsigned)N;
+  int pass = 0;
+  while (hi > 0 && (full || ncand > (unsigned)kSmall)) {
+    const int width = hi < 8 ? hi : 8;
+    const int shift = hi - width;
+    const unsigned dmask = (1u << width) - 1u;
+    unsigned* h = hist[pass % 3];
+    for (int t = tid; t < 256; t += NT) hist[(pass + 1) % 3][t] = 0;  // nobody reads it now
+    sweep<CACHED, NT>(bits, cache, N, full, cand[cur], ncand, mask, prefix,
+                  [&](bool in, unsigned long long key, int64_t) {
+                    const int digit = in ? (int)((key >> shift) & dmask) : -1;
+                    // warp-aggregated count: WMD values share leading bits, so
+                    // many lanes land in one bin
+                    if (__any_sync(0xffffffffu, in)) {
+                      const unsigned same = __match_any_sync(0xffffffffu, digit);
+                      if (in && lane == __ffs(same) - 1) atomicAdd(&h[digit], (unsigned)__popc(same));
+                    }
+                  });
+    __syncthreads();
+    // every warp finds the bin where the running count reaches `need`
+    // (lane l holds bins 8 l .. 8 l + 7)
+    unsigned c[8], sum = 0;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      c[q] = h[8 * lane + q];
+      sum += c[q];
+    }
+    unsigned incl = sum;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+      const unsigned o = __shfl_up_sync(0xffffffffu, incl, off);
+      if (lane >= off) incl += o;
+    }
+    const unsigned excl = incl - sum;
+    const unsigned hit = __ballot_sync(0xffffffffu, excl < need && need <= incl);
+    const int src = hit ? __ffs(hit) - 1 : 0;
+    unsigned run = excl;
+    int q = 0;
+#pragma unroll
+    for (int t = 0; t < 7; ++t) {
+      if (q == t && run + c[t] < need) {
+        run += c[t];
+        ++q;
       }
     }
-    const bool eq = i < N && key == kth && eq_seen < need;
-    const int n_eq = __syncthreads_count(eq);
-    if (n_eq) {  // block-uniform
-      const unsigned r = block_rank(eq, warp_sums, &s_total);
-      const unsigned slot = n_less + eq_seen + r;
-      if (eq && eq_seen + r < need && slot < (unsigned)kTopkMaxK) {
-        s_key[slot] = key;
-        s_idx[slot] = i;
+    unsigned cq = c[0];
+#pragma unroll
+    for (int t = 1; t < 8; ++t) cq = q == t ? c[t] : cq;
+    const unsigned bin = (unsigned)__shfl_sync(0xffffffffu, 8 * lane + q, src);
+    const unsigned below = __shfl_sync(0xffffffffu, run, src);
+    const unsigned cnt = __shfl_sync(0xffffffffu, cq, src);
+    // emit the keys below the bin; move the bin's keys to the next list
+    const bool compact = cnt <= (unsigned)kCandMax;
+    int* next = cand[cur ^ 1];
+    unsigned* nnext = &s_ncand[pass & 1];
+    sweep<CACHED, NT>(bits, cache, N, full, cand[cur], ncand, mask, prefix,
+                  [&](bool in, unsigned long long key, int64_t i) {
+                    if (!in) return;
+                    const unsigned digit = (unsigned)(key >> shift) & dmask;
+                    if (digit < bin) {
+                      const unsigned slot = atomicAdd(&s_taken, 1u);
+                      if (slot < (unsigned)kTopkMaxK) {  // always: fewer than k lie below
+                        s_key[slot] = key;
+                        s_idx[slot] = i;
+                      }
+                    } else if (digit == bin && compact) {
+                      const unsigned p = atomicAdd(nnext, 1u);
+                      if (p < (unsigned)kCandMax) next[p] = (int)i;
+                    }
+                  });
+    if (tid == 0) s_ncand[(pass + 1) & 1] = 0;  // the counter of the pass after next
+    __syncthreads();
+    need -= below;
+    prefix |= (unsigned long long)bin << shift;
+    mask |= (unsigned long long)dmask << shift;
+    hi = shift;
+    ncand = cnt;
+    if (compact) {
+      full = false;
+      cur ^= 1;
+    }
+    ++pass;
+  }
+  if (need < 1) need = 1;  // (always in [1, k]; kept there for the slots below)
+  if (need > (unsigned)k) need = (unsigned)k;
+  const unsigned base_slot = (unsigned)k - need;
+
+  // 3. the last `need` of the k among the remaining candidates
+  if (ncand <= (unsigned)kSmall || (!full && ncand <= (unsigned)kTopkMaxK)) {
+    // few candidates: gather them with their keys (into the spare list's
+    // memory) and take those of rank < need by (key, id)
+    unsigned long long* tkey = reinterpret_cast<unsigned long long*>(cand[cur ^ 1]);
+    int* tidx = reinterpret_cast<int*>(tkey + kTopkMaxK);
+    if (tid == 0) s_total = 0;
+    __syncthreads();
+    sweep<CACHED, NT>(bits, cache, N, full, cand[cur], ncand, mask, prefix,
+                  [&](bool in, unsigned long long key, int64_t i) {
+                    if (!in) return;
+                    const unsigned p = atomicAdd(&s_total, 1u);
+                    if (p < (unsigned)kTopkMaxK) {
+                      tkey[p] = key;
+                      tidx[p] = (int)i;
+                    }
+                  });
+    __syncthreads();
+    const unsigned m = s_total < (unsigned)kTopkMaxK ? s_total : (unsigned)kTopkMaxK;
+    for (unsigned t = tid; t < m; t += NT) {
+      const unsigned long long kt = tkey[t];
+      const int it = tidx[t];
+      unsigned rank = 0;
+      for (unsigned j = 0; j < m; ++j) {
+        const unsigned long long kj = tkey[j];
+        rank += (kj < kt || (kj == kt && tidx[j] < it)) ? 1u : 0u;
       }
-      eq_seen += (unsigned)n_eq;
+      if (rank < need && base_slot + rank < (unsigned)kTopkMaxK) {
+        s_key[base_slot + rank] = kt;
+        s_idx[base_slot + rank] = it;
+      }
+    }
+  } else {
+    // every bit decided and many keys equal to the k-th: the lowest ids win,
+    // so take them in document order
+    unsigned eq_seen = 0;  // block-uniform
+    for (int64_t base = 0; base < N; base += NT) {
+      const int64_t i = base + tid;
+      const bool eq = i < N && key_at(i) == prefix && eq_seen < need;
+      const int cnt = __syncthreads_count(eq);
+      if (cnt) {  // block-uniform
+        const unsigned r = block_rank<NT>(eq, warp_sums, &s_total);
+        const unsigned slot = base_slot + eq_seen + r;
+        if (eq && eq_seen + r < need && slot < (unsigned)kTopkMaxK) {
+          s_key[slot] = prefix;
+          s_idx[slot] = i;
+        }
+        eq_seen += (unsigned)cnt;
+      }
     }
   }
   __syncthreads();
 
-  // 4. bitonic sort of the k taken (padded to a power of two) by (key, id)
-  int P = 1;
-  while (P < k) P <<= 1;
-  for (int t = k + tid; t < P; t += kThreads) {
-    s_key[t] = ~0ull;
-    s_idx[t] = 0x7fffffffffffffffll;
-  }
-  __syncthreads();
-  for (int size = 2; size <= P; size <<= 1) {
-    for (int stride = size >> 1; stride > 0; stride >>= 1) {
-      for (int a = tid; a < P; a += kThreads) {
-        const int b = a ^ stride;
-        if (b > a) {
-          const bool up = (a & size) == 0;
-          const unsigned long long ka = s_key[a], kb = s_key[b];
-          const long long ia = s_idx[a], ib = s_idx[b];
-          const bool a_after = ka > kb || (ka == kb && ia > ib);
-          if (a_after == up) {
-            s_key[a] = kb;
-            s_key[b] = ka;
-            s_idx[a] = ib;
-            s_idx[b] = ia;
+  // 4. order the k taken by (key, document id)
+  if (k <= kRankSortMax) {
+    // the rank of an entry is the number of entries before it (all distinct)
+    unsigned long long kt = 0;
+    long long it = 0;
+    int rank = 0;
+    if (tid < k) {
+      kt = s_key[tid];
+      it = s_idx[tid];
+      for (int j = 0; j < k; ++j) {
+        const unsigned long long kj = s_key[j];
+        const long long ij = s_idx[j];
+        rank += (kj < kt || (kj == kt && ij < it)) ? 1 : 0;
+      }
+    }
+    __syncthreads();
+    if (tid < k) {
+      s_key[rank] = kt;
+      s_idx[rank] = it;
+    }
+    __syncthreads();
+  } else {
+    int P = 1;
+    while (P < k) P <<= 1;
+    for (int t = k + tid; t < P; t += NT) {
+      s_key[t] = ~0ull;
+      s_idx[t] = 0x7fffffffffffffffll;
+    }
+    __syncthreads();
+    for (int size = 2; size <= P; size <<= 1) {
+      for (int stride = size >> 1; stride > 0; stride >>= 1) {
+        for (int a = tid; a < P; a += NT) {
+          const int b = a ^ stride;
+          if (b > a) {
+            const bool up = (a & size) == 0;
+            const unsigned long long ka = s_key[a], kb = s_key[b];
+            const long long ia = s_idx[a], ib = s_idx[b];
+            const bool a_after = ka > kb || (ka == kb && ia > ib);
+            if (a_after == up) {
+              s_key[a] = kb;
+              s_key[b] = ka;
+              s_idx[a] = ib;
+              s_idx[b] = ia;
+            }
           }
         }
+        __syncthreads();
       }
-      __syncthreads();
     }
   }
-  for (int t = tid; t < k; t += kThreads) {
+  for (int t = tid; t < k; t += NT) {
     const long long j = s_idx[t];
     out_idx[t] = j;
     out_val[t] = (j >= 0 && j < N) ? wmd[j] : __longlong_as_double(0x7ff8000000000000ll);
@@ -197,18 +389,25 @@ __global__ void __launch_bounds__(kThreads, 1)
 cudaError_t launch_topk(const double* wmd, int64_t N, int k, int64_t* out_idx, double* out_val,
                         cudaStream_t s) {
   if (k <= 0) return cudaSuccess;
+  const size_t lists = 2 * (size_t)kCandMax * sizeof(int);
+  static std::once_flag once;
+  static cudaError_t attr_err = cudaSuccess;
+  std::call_once(once, [lists] {
+    attr_err = cudaFuncSetAttribute(topk_kernel<true, kThreadsCached>,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)(kCacheMax * sizeof(unsigned long long) + lists));
+    if (attr_err == cudaSuccess)
+      attr_err = cudaFuncSetAttribute(topk_kernel<false, kThreadsStream>,
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lists);
+  });
+  if (attr_err != cudaSuccess) return attr_err;
   if (N <= kCacheMax) {
-    const size_t smem = (size_t)N * sizeof(unsigned long long);
-    static std::once_flag once;
-    static cudaError_t attr_err = cudaSuccess;
-    std::call_once(once, [] {
-      attr_err = cudaFuncSetAttribute(topk_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)(kCacheMax * sizeof(unsigned long long)));
-    });
-    if (attr_err != cudaSuccess) return attr_err;
-    topk_kernel<true><<<1, kThreads, smem, s>>>(wmd, N, k, out_idx, out_val);
+    topk_kernel<true, kThreadsCached>
+        <<<1, kThreadsCached, (size_t)N * sizeof(unsigned long long) + lists, s>>>(wmd, N, k,
+                                                                                 out_idx, out_val);
   } else {
-    topk_kernel<false><<<1, kThreads, 0, s>>>(wmd, N, k, out_idx, out_val);
+    topk_kernel<false, kThreadsStream><<<1, kThreadsStream, lists, s>>>(wmd, N, k, out_idx,
+                                                                       out_val);
   }
   return cudaGetLastError();
 }
