@@ -104,7 +104,7 @@ wmd_status cuda_error(cudaError_t e, const char* what) {
 WsLayout ws_layout(const wmd_corpus* c, int VR, wmd_precision prec) {
   WsLayout L;
   size_t o = 0;
-  L.r_off = o;    o = align_up(o + (size_t)(VR + 1) * sizeof(float), 256);
+  L.r_off = o;    o = align_up(o + (size_t)(VR + 4) * sizeof(float), 256);  // r, lambda, scale
   const size_t kelem = prec == WMD_PREC_BF16_K ? 2 : 4;
   const size_t kbytes = align_up((size_t)std::max<int64_t>(c->U, 1) * VR * kelem, 256);
   L.k_off = o;

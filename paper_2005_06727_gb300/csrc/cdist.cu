@@ -72,7 +72,12 @@ __global__ void __launch_bounds__(256) cdist_kernel(
   if (r_out && blockIdx.x == 0) {
     for (int i = tid + c0; i < c0 + VRB; i += 256) r_out[i] = i < v_r ? q_w[i] : 0.f;
   }
-  if (lam_out && blockIdx.x == 0 && blockIdx.y == 0 && tid == 0) *lam_out = lambda;
+  if (lam_out && blockIdx.x == 0 && blockIdx.y == 0 && tid == 0) {
+    // lambda, and the final step's scale -ln 2 / lambda as a double two
+    // floats further on (8-byte aligned), for the loop kernel
+    *lam_out = lambda;
+    *reinterpret_cast<double*>(lam_out + 2) = -0.69314718055994530942 / (double)lambda;
+  }
   __syncthreads();
 
   float acc[4][TC];

@@ -392,7 +392,12 @@ __global__ void __launch_bounds__(kThreads, 1)
       }
     }
     if (p.r_out && blockIdx.x == 0 && bt < p.VR) p.r_out[bt] = bt < p.v_r ? p.q_w[bt] : 0.f;
-    if (p.lam_out && blockIdx.x == 0 && bt == 0) *p.lam_out = p.lambda;
+    if (p.lam_out && blockIdx.x == 0 && bt == 0) {
+      // lambda, and the final step's scale -ln 2 / lambda as a double two
+      // floats further on (8-byte aligned), for the loop kernel
+      *p.lam_out = p.lambda;
+      *reinterpret_cast<double*>(p.lam_out + 2) = -0.69314718055994530942 / (double)p.lambda;
+    }
     asm volatile("bar.sync 1, %0;" ::"r"(kBuildThreads) : "memory");
     if (tid == 0) TC_TRACE(6, 0);
     // every 16-byte chunk of B goes straight from global to shared memory

@@ -195,6 +195,7 @@ wmd_status enqueue_batch(wmd_corpus* c, Slot& s, const std::vector<const Req*>& 
     d.kcol0 = L.col0[q];
     d.v_r = qs[q]->v_r;
     d.lambda = qs[q]->lambda;
+    d.scale = -0.69314718055994530942 / (double)qs[q]->lambda;
   }
   cudaStream_t st = s.stream;
   WMD_CUDA_TRY(cudaMemcpyAsync(s.d_ids, s.h_ids, L.words * sizeof(int32_t), cudaMemcpyHostToDevice, st));

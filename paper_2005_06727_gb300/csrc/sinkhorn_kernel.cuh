@@ -70,7 +70,8 @@ struct LoopParams {
   int ldk;
   int kcol0;
   const float* r;
-  const float* lam;  // lambda of the single query (written by the cdist kernel)
+  const float* lam;  // lambda of the single query, then the double -ln 2 / lambda at
+                     // lam + 2 (both written by the cdist kernel)
   int v_r;
   int T;
   const WarpTask* tasks;  // [item][warp]
@@ -163,7 +164,6 @@ __device__ __forceinline__ float2 k_log2k(float2 k) {
   return __fmul2_rn(k, l);
 }
 
-constexpr double kLn2 = 0.69314718055994530942;  // ln 2
 
 // Knuth's TwoSum: s + e == a + b exactly (s = fl(a + b)).
 __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
@@ -289,7 +289,6 @@ __device__ __forceinline__ void solve(const LoopParams& p, const TeamCtx& t) {
     }
     return;
   }
-  const float lam = p.queries ? t.q.lambda : *p.lam;
 
   // query weights and the initial u = 1 / x = v_r for my columns; one lane
   // per column seeds the SpMM sums of padding columns with 1 so that 1/x stays
@@ -536,17 +535,23 @@ __device__ __forceinline__ void solve(const LoopParams& p, const TeamCtx& t) {
     two_sum(hi, h2, sh, se);
     two_sum(sh, se + (lo + l2), hi, lo);
   }
-  const double wsum = (double)hi + (double)lo;
+  // (float64 only in lane 0: this GPU's FP64 pipe is narrow).  The factor
+  // -ln 2 / lambda was computed once per query outside this kernel (a float64
+  // division per document would load that pipe) and is read only here, so
+  // that it occupies no registers during the loop.
+  auto scale = [&]() {
+    return p.queries ? p.queries[blockIdx.y].scale : *reinterpret_cast<const double*>(p.lam + 2);
+  };
   if (t.W > 1) {
-    if (t.lane == 0) t.wred[t.warp] = wsum;
+    if (t.lane == 0) t.wred[t.warp] = (double)hi + (double)lo;
     team_barrier(1 + t.team, 32 * t.W);
     if (t.kw == 0 && t.lane == 0) {
       double acc = 0.0;
       for (int k2 = 0; k2 < t.W; ++k2) acc += t.wred[t.team * t.W + k2];
-      t.q.out[t.doc] = acc * (-kLn2 / (double)lam);
+      t.q.out[t.doc] = acc * scale();
     }
   } else if (t.lane == 0) {
-    t.q.out[t.doc] = wsum * (-kLn2 / (double)lam);
+    t.q.out[t.doc] = ((double)hi + (double)lo) * scale();
   }
 }
 

@@ -112,7 +112,8 @@ struct wmd_corpus {
 namespace wmd {
 
 // Workspace carve-up for one query of class VR: the padded query weights r
-// (VR floats) followed by lambda, and the word-major K (U x VR).
+// (VR floats) followed by lambda (float VR), the final step's scale
+// -ln 2 / lambda (a double at float VR + 2), and the word-major K (U x VR).
 struct WsLayout {
   size_t r_off, k_off, total;
 };
@@ -148,6 +149,7 @@ struct QueryDesc {
   int kcol0;
   int v_r;
   float lambda;
+  double scale;  // -ln 2 / lambda, the final step's factor
 };
 cudaError_t launch_loop_batch(const wmd_corpus* c, int cls, const void* K, int ldk,
                               const QueryDesc* d_queries, int nq, int T, wmd_precision prec,
