@@ -214,6 +214,66 @@ def cpu_baseline(w, vecs, c, q_ids, q_w, budget_s=10.0):
                       f"FP64 numpy/scipy oracle, single thread, mean {t:.2f} s per run"}, docs, ref
 
 
+_ORACLE_WORKER = {}
+
+
+def _oracle_worker_init(cfg: int, root: str):
+    """Pool initializer: rebuild the seeded workload in the worker (cheaper
+    than shipping the arrays, and the same bits)."""
+    if root not in sys.path:
+        sys.path.insert(0, root)
+    from paper_2005_06727_gb300 import synth as s
+    w = s.WORKLOADS[cfg]
+    vecs, c, qs = s.make_workload(w, 1)
+    _ORACLE_WORKER.update(w=w, vecs=vecs, c=c, q=qs[0])
+
+
+def _oracle_worker_run(docs):
+    from oracle import sinkhorn_wmd as orc
+    st = _ORACLE_WORKER
+    w, c = st["w"], st["c"]
+    t0 = time.perf_counter()
+    orc.sinkhorn_wmd_sparse(st["q"][0], st["q"][1], c.row_ptr, c.doc_idx, c.val, c.N, st["vecs"],
+                            w.lam, w.max_iter, docs=np.asarray(docs))
+    return time.perf_counter() - t0
+
+
+def cpu_baseline_all_cores(w, c, docs=None, timeout_s=300.0):
+    """The same oracle on every host core: the documents (all, or the sample
+    of a large corpus) split into one slice per core, each slice run by a
+    single-threaded worker process (spawned: the parent already holds a CUDA
+    context), timed from the first slice's start to the last one's end."""
+    import concurrent.futures as cf
+    import multiprocessing as mp
+    n = os.cpu_count() or 1
+    ids = np.arange(c.N) if docs is None else np.asarray(docs)
+    chunks = [ch for ch in np.array_split(ids, n) if ch.size]
+    saved = {k: os.environ.get(k) for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")}
+    for k in saved:
+        os.environ[k] = "1"
+    try:
+        # an executor (not multiprocessing.Pool): a worker that cannot start
+        # raises BrokenProcessPool instead of being respawned for ever
+        with cf.ProcessPoolExecutor(len(chunks), mp_context=mp.get_context("spawn"),
+                                    initializer=_oracle_worker_init,
+                                    initargs=(w.cfg, ROOT)) as pool:
+            list(pool.map(_oracle_worker_run, [ch[:4] for ch in chunks], timeout=timeout_s))
+            t0 = time.perf_counter()
+            list(pool.map(_oracle_worker_run, chunks, timeout=timeout_s))
+            wall = time.perf_counter() - t0
+    finally:
+        for k, v in saved.items():
+            if v is None:
+                os.environ.pop(k, None)
+            else:
+                os.environ[k] = v
+    what = f"all {c.N} documents" if docs is None else f"{ids.size} of {c.N} documents (seeded sample)"
+    return {"value": ids.size / wall, "unit": UNIT, "cores": len(chunks), "kind": "oracle",
+            "sample": f"the bench query over {what}, split into {len(chunks)} slices run by "
+                      f"single-threaded worker processes at once, FP64 numpy/scipy oracle, "
+                      f"{wall:.2f} s wall"}
+
+
 def error_vs_oracle(got, ref, prec):
     """Largest per-document relative error of the GPU result against the FP64
     oracle (absolute floor 1e-7), beside the tolerance the tests enforce."""
@@ -660,6 +720,10 @@ def run_ours(args, w):
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"], docs, ref = cpu_baseline(w, vecs, c, q_ids, q_w)
         out["error_vs_oracle"] = error_vs_oracle(out_np if docs is None else out_np[docs], ref, prec)
+        try:
+            out["cpu_baseline_all_cores"] = cpu_baseline_all_cores(w, c, docs)
+        except Exception as e:  # a host without spawn support: report, do not fail the bench
+            out["cpu_baseline_all_cores"] = {"unavailable": f"{type(e).__name__}: {e}"}
     legs = set(args.legs.split(",")) if args.legs else set()
     if rank == 0 and not args.no_systems:
         if "converge" in legs:
