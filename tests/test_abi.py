@@ -96,3 +96,28 @@ def test_missing_library_fails_loudly(monkeypatch, tmp_path):
     monkeypatch.setattr(wmd, "LIB_PATH", str(tmp_path / "absent.so"))
     with pytest.raises(wmd.WMDError):
         wmd.lib()
+
+
+def test_new_entry_points_validate_on_host(lib):
+    """k nearest documents, the convergence-tested query and the dense
+    comparator reject bad arguments before any CUDA call (the pointers below
+    are never dereferenced)."""
+    fake = ctypes.c_void_p(0x1000)
+    bad, unsupported, ok = wmd.WMD_ERR_INVALID_ARG, wmd.WMD_ERR_UNSUPPORTED, wmd.WMD_OK
+    # wmd_topk: 0 <= k <= min(N, 1024), non-NULL pointers, N below 2^31
+    assert lib.wmd_topk(fake, 10, 11, fake, fake, None) == bad
+    assert lib.wmd_topk(fake, 10, -1, fake, fake, None) == bad
+    assert lib.wmd_topk(fake, 5000, 1025, fake, fake, None) == bad
+    assert lib.wmd_topk(None, 10, 3, fake, fake, None) == bad
+    assert lib.wmd_topk(fake, 10, 3, fake, None, None) == bad
+    assert lib.wmd_topk(fake, 1 << 32, 3, fake, fake, None) == unsupported
+    assert lib.wmd_topk(fake, 10, 0, None, None, None) == ok          # nothing to select
+    # entry points that take a corpus refuse a NULL one
+    assert lib.wmd_query_device_tol(None, fake, fake, 5, 10.0, 15, 1e-3, 0, fake, 1 << 20, fake,
+                                    None, None) == bad
+    assert lib.wmd_query_device_topk(None, fake, fake, 5, 10.0, 15, 0, fake, 1 << 20, fake, 3,
+                                     fake, fake, None) == bad
+    assert lib.wmd_query_dense(None, fake, fake, 5, 10.0, 15, fake, 1 << 20, fake, None) == bad
+    assert lib.wmd_dense_load_c(None, fake, 1 << 20, None) == bad
+    assert lib.wmd_dense_workspace_bytes(None, 5) == 0
+    assert b"corpus" in lib.wmd_last_error()
