@@ -8,17 +8,16 @@
 //      every key shares (WMD values lie close together, so this skips the
 //      sign, the exponent and a few mantissa bits);
 //   2. a radix select over the remaining bits, 8 per pass, most significant
-//      first, finds the k-th smallest key K*: per pass one 256-bin
-//      shared-memory histogram of the keys that match the bits chosen so
-//      far, counted with warp-aggregated atomics (lanes with the same byte
-//      add once; warps without a matching key skip the count) and scanned
-//      by every warp for itself, so a pass needs one
-//      barrier (three histogram buffers rotate, one being cleared while
-//      another fills);
-//   3. a sweep takes every key below K* and the first keys equal to K*
-//      (lowest document ids) until k are taken; when K* occurs exactly as
-//      often as still needed, any order will do and the sweep takes no
-//      barrier per tile;
+//      first: each pass builds a 256-bin shared-memory histogram of the
+//      current candidates (warp-aggregated atomics: lanes with the same byte
+//      add once), every warp scans it for itself and finds the bin of the
+//      k-th smallest key (one barrier per pass; three histogram buffers
+//      rotate), and a second sweep emits the keys of the lower bins (they
+//      are among the k) and moves the keys of that bin to a shared-memory
+//      index list, the next pass's candidates;
+//   3. once at most kSmall candidates remain (or every bit is decided), the
+//      rest of the k are the candidates of smallest (key, document id); with
+//      many exact ties they are taken in document order instead;
 //   4. the k taken are ordered by (key, document id): by counting ranks for
 //      k <= 256, else by a bitonic sort.
 // Ties are broken by the lower document id, so the result is unique.  When
