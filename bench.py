@@ -721,7 +721,9 @@ def run_ours(args, w):
         out["cpu_baseline"], docs, ref = cpu_baseline(w, vecs, c, q_ids, q_w)
         out["error_vs_oracle"] = error_vs_oracle(out_np if docs is None else out_np[docs], ref, prec)
     legs = set(args.legs.split(",")) if args.legs else set()
-    if rank == 0 and not args.no_systems:
+    # the extra legs run on single-GPU runs only: under torchrun the other
+    # ranks are done after the timed region, and the scaling runs need only it
+    if rank == 0 and world == 1 and not args.no_systems:
         if "converge" in legs:
             out["converge"] = bench_converge(wmd, corpus, dq, w, prec, stream, flush)
         if "topk" in legs:
