@@ -9,8 +9,10 @@
 //      sign, the exponent and a few mantissa bits);
 //   2. a radix select over the remaining bits, 8 per pass, most significant
 //      first: each pass builds a 256-bin shared-memory histogram of the
-//      current candidates (warp-aggregated atomics: lanes with the same byte
-//      add once), every warp scans it for itself and finds the bin of the
+//      current candidates (plain shared-memory atomics: below the common
+//      prefix the keys spread over many bins, and aggregating equal bytes per
+//      warp with match.any cost more than the collisions it saved), every
+//      warp scans it for itself and finds the bin of the
 //      k-th smallest key (one barrier per pass; three histogram buffers
 //      rotate), and a second sweep emits the keys of the lower bins (they
 //      are among the k) and moves the keys of that bin to a shared-memory
@@ -196,13 +198,7 @@ __global__ void __launch_bounds__(NT, 1)
     for (int t = tid; t < 256; t += NT) hist[(pass + 1) % 3][t] = 0;  // nobody reads it now
     sweep<CACHED, NT>(bits, cache, N, full, cand[cur], ncand, mask, prefix,
                   [&](bool in, unsigned long long key, int64_t) {
-                    const int digit = in ? (int)((key >> shift) & dmask) : -1;
-                    // warp-aggregated count: WMD values share leading bits, so
-                    // many lanes land in one bin
-                    if (__any_sync(0xffffffffu, in)) {
-                      const unsigned same = __match_any_sync(0xffffffffu, digit);
-                      if (in && lane == __ffs(same) - 1) atomicAdd(&h[digit], (unsigned)__popc(same));
-                    }
+                    if (in) atomicAdd(&h[(unsigned)(key >> shift) & dmask], 1u);
                   });
     __syncthreads();
     // every warp finds the bin where the running count reaches `need`
