@@ -6,8 +6,11 @@ missing the import of a function raises :class:`WMDError`.
 
 Names follow the C entry points: ``corpus_load`` / :class:`Corpus`,
 ``Corpus.query`` (``wmd_query``), ``Corpus.query_device``
-(``wmd_query_device``), ``Corpus.query_device_tol`` (``wmd_query_device_tol``), ``Corpus.build_kernel_matrix``,
-``Corpus.sinkhorn_loop`` and ``compact_query``.
+(``wmd_query_device``), ``Corpus.query_device_tol`` (``wmd_query_device_tol``),
+``Corpus.query_device_topk`` and ``topk`` (``wmd_query_device_topk``,
+``wmd_topk``), ``Corpus.query_dense`` (``wmd_query_dense``),
+``Corpus.build_kernel_matrix``, ``Corpus.sinkhorn_loop``, ``query_batch``,
+:class:`Server` and ``compact_query``.
 """
 from __future__ import annotations
 
