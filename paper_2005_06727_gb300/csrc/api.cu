@@ -154,6 +154,7 @@ wmd_status wmd_compact_query(const int32_t* q_ids, const float* q_w, int32_t n_q
 wmd_status wmd_corpus_load(const float* vecs, int64_t V, int32_t d, const int64_t* row_ptr,
                            const int32_t* doc_idx, const float* val, int64_t N, int64_t nnz,
                            int32_t device, wmd_corpus** out) {
+  wmd::NvtxRange nvtx_range("wmd_corpus_load");
   if (!out) return set_error(WMD_ERR_INVALID_ARG, "out is NULL");
   *out = nullptr;
   if (V <= 0 || V > INT32_MAX) return set_error(WMD_ERR_INVALID_ARG, "V must be in [1, 2^31)");
@@ -382,6 +383,7 @@ size_t wmd_workspace_bytes(const wmd_corpus* c, int32_t v_r, wmd_precision prec)
 wmd_status wmd_build_kernel_matrix(wmd_corpus* c, const int32_t* d_q_ids, const float* d_q_w,
                                    int32_t v_r, float lambda, wmd_precision prec, void* d_ws,
                                    size_t ws_bytes, void* stream) {
+  wmd::NvtxRange nvtx_range("K1 cdist + K");
   wmd_status st = check_query_args(c, v_r, lambda, 0);
   if (st != WMD_OK) return st;
   if (!d_q_ids || !d_q_w) return set_error(WMD_ERR_INVALID_ARG, "NULL query pointer");
@@ -423,12 +425,14 @@ wmd_status sinkhorn_loop(wmd_corpus* c, int32_t v_r, int32_t max_iter, wmd_preci
 
 wmd_status wmd_sinkhorn_loop(wmd_corpus* c, int32_t v_r, int32_t max_iter, wmd_precision prec,
                              void* d_ws, size_t ws_bytes, double* d_out, void* stream) {
+  wmd::NvtxRange nvtx_range("K2+K3 fused loop");
   return sinkhorn_loop(c, v_r, max_iter, prec, d_ws, ws_bytes, d_out, nullptr, stream);
 }
 
 wmd_status wmd_query_device(wmd_corpus* c, const int32_t* d_q_ids, const float* d_q_w,
                             int32_t v_r, float lambda, int32_t max_iter, wmd_precision prec,
                             void* d_ws, size_t ws_bytes, double* d_out, void* stream) {
+  wmd::NvtxRange nvtx_range("wmd_query_device");
   wmd_status st = check_query_args(c, v_r, lambda, max_iter);
   if (st != WMD_OK) return st;
   st = wmd_build_kernel_matrix(c, d_q_ids, d_q_w, v_r, lambda, prec, d_ws, ws_bytes, stream);
@@ -440,6 +444,7 @@ wmd_status wmd_query_device_tol(wmd_corpus* c, const int32_t* d_q_ids, const flo
                                 int32_t v_r, float lambda, int32_t max_iter, float tol,
                                 wmd_precision prec, void* d_ws, size_t ws_bytes, double* d_out,
                                 int32_t* d_iters, void* stream) {
+  wmd::NvtxRange nvtx_range("wmd_query_device_tol");
   wmd_status st = check_query_args(c, v_r, lambda, max_iter);
   if (st != WMD_OK) return st;
   if (!(tol >= 0.f && tol < 1.f)) return set_error(WMD_ERR_INVALID_ARG, "tol must lie in [0, 1)");
@@ -459,6 +464,7 @@ wmd_status wmd_query_device_tol(wmd_corpus* c, const int32_t* d_q_ids, const flo
 
 wmd_status wmd_topk(const double* d_wmd, int64_t N, int32_t k, int64_t* d_idx, double* d_val,
                     void* stream) {
+  wmd::NvtxRange nvtx_range("wmd_topk");
   if (k == 0) return WMD_OK;
   if (N < 0 || k < 0 || k > N || k > kTopkMaxK)
     return set_error(WMD_ERR_INVALID_ARG, "k must satisfy 0 <= k <= min(N, 1024)");
@@ -472,6 +478,7 @@ wmd_status wmd_query_device_topk(wmd_corpus* c, const int32_t* d_q_ids, const fl
                                  int32_t v_r, float lambda, int32_t max_iter, wmd_precision prec,
                                  void* d_ws, size_t ws_bytes, double* d_out, int32_t k,
                                  int64_t* d_idx, double* d_val, void* stream) {
+  wmd::NvtxRange nvtx_range("wmd_query_device_topk");
   if (!c) return set_error(WMD_ERR_INVALID_ARG, "corpus is NULL");
   if (k < 0 || k > c->N || k > kTopkMaxK)
     return set_error(WMD_ERR_INVALID_ARG, "k must satisfy 0 <= k <= min(N, 1024)");
@@ -502,6 +509,7 @@ wmd_status wmd_set_loop_variant(wmd_corpus* c, int32_t v_r, wmd_precision prec, 
 
 wmd_status wmd_autotune(wmd_corpus* c, const int32_t* q_ids, const float* q_w, int32_t n_q,
                         float lambda, int32_t max_iter, wmd_precision prec, int32_t* chosen) {
+  wmd::NvtxRange nvtx_range("wmd_autotune");
   if (!c) return set_error(WMD_ERR_INVALID_ARG, "corpus is NULL");
   std::vector<int32_t> ids(std::max(n_q, 1));
   std::vector<float> w(std::max(n_q, 1));
@@ -569,6 +577,7 @@ wmd_status wmd_autotune(wmd_corpus* c, const int32_t* q_ids, const float* q_w, i
 
 wmd_status wmd_query(wmd_corpus* c, const int32_t* q_ids, const float* q_w, int32_t n_q,
                      float lambda, int32_t max_iter, wmd_precision prec, double* out_wmd) {
+  wmd::NvtxRange nvtx_range("wmd_query");
   if (!c) return set_error(WMD_ERR_INVALID_ARG, "corpus is NULL");
   if (!out_wmd && c->N > 0) return set_error(WMD_ERR_INVALID_ARG, "out_wmd is NULL");
   if (n_q > WMD_MAX_VR) {

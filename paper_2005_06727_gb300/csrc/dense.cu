@@ -155,6 +155,7 @@ size_t wmd_dense_workspace_bytes(const wmd_corpus* c, int32_t v_r) {
 }
 
 wmd_status wmd_dense_load_c(wmd_corpus* c, void* d_ws, size_t ws_bytes, void* stream) {
+  wmd::NvtxRange nvtx_range("wmd_dense_load_c");
   if (!c) return set_error(WMD_ERR_INVALID_ARG, "corpus is NULL");
   const DenseLayout L = dense_layout(c, 8);
   if (!d_ws || ws_bytes < L.s_off) return set_error(WMD_ERR_INVALID_ARG, "workspace too small");
@@ -179,6 +180,7 @@ wmd_status wmd_dense_load_c(wmd_corpus* c, void* d_ws, size_t ws_bytes, void* st
 wmd_status wmd_query_dense(wmd_corpus* c, const int32_t* d_q_ids, const float* d_q_w,
                            int32_t v_r, float lambda, int32_t max_iter, void* d_ws,
                            size_t ws_bytes, double* d_out, void* stream) {
+  wmd::NvtxRange nvtx_range("wmd_query_dense");
   if (!c) return set_error(WMD_ERR_INVALID_ARG, "corpus is NULL");
   if (v_r <= 0 || v_r > WMD_MAX_VR) return set_error(WMD_ERR_INVALID_ARG, "v_r out of range");
   const int VR = kClassVR[vr_class(v_r)];

@@ -165,6 +165,7 @@ Layout plan(const wmd_corpus* c, const std::vector<const Req*>& qs, wmd_precisio
 // class, D2H of the nq x N results into the slot's pinned buffer.
 wmd_status enqueue_batch(wmd_corpus* c, Slot& s, const std::vector<const Req*>& qs,
                          const Layout& L, int T, wmd_precision prec) {
+  wmd::NvtxRange nvtx_range("batch enqueue");
   const size_t nq = qs.size();
   const size_t N1 = (size_t)std::max<int64_t>(c->N, 1);
   WMD_CUDA_TRY(grow_dev(&s.d_ids, &s.ids_cap, L.words));
@@ -452,6 +453,7 @@ extern "C" {
 wmd_status wmd_query_batch(wmd_corpus* c, int32_t nq, const int64_t* q_ptr, const int32_t* q_ids,
                            const float* q_w, const float* lambda, int32_t max_iter,
                            wmd_precision prec, double* out) {
+  wmd::NvtxRange nvtx_range("wmd_query_batch");
   if (!c) return set_error(WMD_ERR_INVALID_ARG, "corpus is NULL");
   if (nq < 0) return set_error(WMD_ERR_INVALID_ARG, "nq < 0");
   if (nq == 0) return WMD_OK;

@@ -3,6 +3,7 @@
 
 #include <cuda_runtime.h>
 #include <cuda_bf16.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <cstdint>
 #include <mutex>
@@ -12,6 +13,17 @@
 #include "../../include/wmd.h"
 
 namespace wmd {
+
+// ---------------------------------------------------------------- tracing
+// A named NVTX range over a host-side scope: profilers (nsys, ncu --nvtx)
+// show the library's phases under these names.  NVTX is header-only here and
+// costs a few nanoseconds per range when no tool is attached.
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 // ---------------------------------------------------------------- errors
 wmd_status set_error(wmd_status st, const std::string& msg);
