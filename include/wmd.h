@@ -13,6 +13,13 @@
  *                           (SDDMM);  x = diag(1/r) K v  (SpMM)
  *   u = 1/x;  v = c ./ (K^T u);  WMD_j = sum_i u_ij ((K .* M) v)_ij.
  *
+ * Besides that fixed-count form (single, device-resident, batched and served
+ * queries), the library offers Algorithm 1's own loop condition "while x
+ * changes" per document (wmd_query_device_tol), the k nearest documents of a
+ * query (wmd_topk, wmd_query_device_topk), Algorithm 1 in its dense form as a
+ * measured comparator (wmd_query_dense), and a device query for callers that
+ * cannot allocate (wmd_query_device_noalloc).
+ *
  * Conventions shared by every entry point:
  *  - All functions return a wmd_status; on failure wmd_last_error() returns a
  *    thread-local message describing the first error.  No entry point aborts
