@@ -23,7 +23,7 @@ Every step follows the paper, in its order and notation:
 * Sec. 3 ("Dense to Sparse Kernel") evaluates K^T u only at the nonzeros of c
   (SDDMM) and forms x with a dense-times-sparse product (SpMM).
 
-Readings where the paper is silent or ambiguous (each is listed in the design doc):
+Readings where the paper is silent or ambiguous:
 m(i, j) is unsquared (the sqrt formula of Sec. 2 wins over the "||.||^2"
 notation); lambda is passed positive and K = exp(-lambda M) (Algorithm 1; the
 paper's Python negates lambda before the call); r and c are used as given, no
