@@ -274,7 +274,7 @@ wmd_status wmd_query_device_topk(wmd_corpus* corpus, const int32_t* d_q_ids,
  * wmd_query_dense: the dense Algorithm 1 for one query (device pointers as
  *   wmd_query_device, asynchronous on `stream`); d_out receives WMD[N].  The
  *   first call on a device creates a cuBLAS handle (allocates).  Errors:
- *   WMD_ERR_INVALID_ARG (arguments, workspace too small), WMD_ERR_UNSUPPORTED
+ *   WMD_ERR_INVALID_ARG (arguments, max_iter < 0, workspace too small), WMD_ERR_UNSUPPORTED
  *   (U or N above 2^31 - 1), WMD_ERR_CUDA / WMD_ERR_OUT_OF_MEMORY from CUDA or
  *   cuBLAS.  Calls on one device are serialised by a lock while they enqueue.
  * ------------------------------------------------------------------------- */

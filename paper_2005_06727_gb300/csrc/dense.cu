@@ -183,6 +183,7 @@ wmd_status wmd_query_dense(wmd_corpus* c, const int32_t* d_q_ids, const float* d
   wmd::NvtxRange nvtx_range("wmd_query_dense");
   if (!c) return set_error(WMD_ERR_INVALID_ARG, "corpus is NULL");
   if (v_r <= 0 || v_r > WMD_MAX_VR) return set_error(WMD_ERR_INVALID_ARG, "v_r out of range");
+  if (max_iter < 0) return set_error(WMD_ERR_INVALID_ARG, "max_iter must be >= 0");
   const int VR = kClassVR[vr_class(v_r)];
   const DenseLayout L = dense_layout(c, VR);
   if (!d_ws || ws_bytes < L.total) return set_error(WMD_ERR_INVALID_ARG, "workspace too small");
