@@ -35,7 +35,6 @@ METRIC = "query x doc WMDs/sec @15 iters, HBM GB/s % of peak; served p50/p99 lat
 UNIT = "WMDs/s"
 L2_FLUSH_BYTES = 512 << 20
 FP32_LANES_PER_SM = 128
-NUM_SMS = 152
 WORKLOADS = {"paper": synth.PAPER, "tiny": synth.TINY, "large": synth.LARGE}
 
 
@@ -48,14 +47,15 @@ def parse():
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="paper")
     ap.add_argument("--prec", choices=["fp32", "bf16"], default="fp32")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--legs", default="converge,topk,dense,batched,serving",
+    ap.add_argument("--legs", default="converge,topk,dense,large,batched,serving",
                     help="comma-separated extra legs to run after the timed step")
     ap.add_argument("--no-systems", action="store_true",
                     help="skip the batched and served measurements")
-    ap.add_argument("--serve-requests", type=int, default=300)
-    ap.add_argument("--serving-workload", choices=["paper", "serving"], default="paper",
-                    help="corpus of the serving leg: the paper-shaped one (default, minutes) or "
-                         "the full serving configuration (V = N = 200,000)")
+    ap.add_argument("--serve-requests", type=int, default=1000,
+                    help="Poisson requests per offered rate (a fifth of them at 0.1x capacity)")
+    ap.add_argument("--serving-workload", choices=["paper", "serving"], default="serving",
+                    help="corpus of the serving leg: the full serving configuration (default, "
+                         "V = N = 200,000) or the paper-shaped one")
     ap.add_argument("--loop-variant", type=int, default=-1,
                     help="fused-loop tile variant (default: chosen by the autotuner)")
     return ap.parse_args()
@@ -279,8 +279,12 @@ def error_vs_oracle(got, ref, prec):
     oracle (absolute floor 1e-7), beside the tolerance the tests enforce."""
     got = np.asarray(got, np.float64)
     ref = np.asarray(ref, np.float64)
-    rel = np.abs(got - ref) / np.maximum(np.abs(ref), 1e-7)
-    return {"max_rel": float(np.max(rel)), "mean_rel": float(np.mean(rel)), "docs": int(ref.size),
+    ok = ~np.isnan(ref)
+    rel = np.abs(got[ok] - ref[ok]) / np.maximum(np.abs(ref[ok]), 1e-7)
+    nan_mismatch = int(np.sum(np.isnan(got) != np.isnan(ref)))
+    return {"max_rel": float(np.max(rel)) if rel.size else 0.0,
+            "mean_rel": float(np.mean(rel)) if rel.size else 0.0, "docs": int(ref.size),
+            "nan_mismatch": nan_mismatch,
             "tolerance": 1e-5 if prec == wmd_prec_fp32() else 5e-3}
 
 
@@ -337,7 +341,7 @@ def run_reference(args, w):
 
 
 # ------------------------------------------------------------------ batched and served
-def bench_batched(wmd, device, reps=2):
+def bench_batched(wmd, device, reps=2, with_oracle=True):
     """256 queries of v_r ~ U[5,128] against N=20000 documents: one at a time
     through wmd_query versus one wmd_query_batch call (graph replayed)."""
     wb = synth.BATCHED
@@ -364,26 +368,55 @@ def bench_batched(wmd, device, reps=2):
     assert np.array_equal(res[-1], out), "batched and single results differ"
     units = len(qs) * c.N
     corpus.close()
-    return {"workload": (f"{wb.name}: V={wb.V} d={wb.d} N={wb.N} docs of {wb.doc_lo}-{wb.doc_hi} "
-                         f"words, {len(qs)} queries v_r U[{wb.vr_lo},{wb.vr_hi}], lambda={wb.lam:g}, "
-                         f"max_iter={wb.max_iter}"),
-            "one_at_a_time": {"value": units / t_single, "unit": UNIT, "seconds": t_single},
-            "batched": {"value": units / t_batch, "unit": UNIT, "seconds": t_batch,
-                        "path": "wmd_query_batch (captured CUDA graph replay)"},
-            "speedup": t_single / t_batch}
+    rec = {"workload": (f"{wb.name}: V={wb.V} d={wb.d} N={wb.N} docs of {wb.doc_lo}-{wb.doc_hi} "
+                        f"words, {len(qs)} queries v_r U[{wb.vr_lo},{wb.vr_hi}], lambda={wb.lam:g}, "
+                        f"max_iter={wb.max_iter}"),
+           "one_at_a_time": {"value": units / t_single, "unit": UNIT, "seconds": t_single},
+           "batched": {"value": units / t_batch, "unit": UNIT, "seconds": t_batch,
+                       "path": "wmd_query_batch (captured CUDA graph replay)"},
+           "speedup": t_single / t_batch}
+    if with_oracle:
+        # every query of the batch against the FP64 oracle on a document
+        # sample (after the timing: the workers load the host cores)
+        rec["error_vs_oracle"] = batch_errors_vs_oracle(wb, c, qs, res)
+    return rec
 
 
-def bench_serving(wmd, device, n_requests=300, seed=11, workload="paper"):
-    """Poisson arrivals (v_r ~ U[5,200]) against the paper-shaped corpus (or
-    the full serving corpus): latency p50/p99 and throughput of the
-    continuous-batching server at 0.1x to 1.2x of its measured capacity, and
-    the one-query-at-a-time capacity."""
+def batch_errors_vs_oracle(w, c, qs, res, n_docs=200):
+    """Largest relative error over every query of a batch, each against the
+    FP64 oracle on the same seeded sample of documents (the 20 longest and
+    shortest included), run in spawned single-threaded workers."""
+    from oracle.pool import OraclePool, sample_documents
+    docs = sample_documents(c.doc_ptr, n_docs)
+    worst, worst_q = 0.0, -1
+    t0 = time.perf_counter()
+    with OraclePool(w.cfg) as pool:
+        futs = [pool.submit(q[0], q[1], w.lam, w.max_iter, docs) for q in qs]
+        for k, f in enumerate(futs):
+            ref, _ = f.result(timeout=3600)
+            e = error_vs_oracle(res[k][docs], ref, wmd_prec_fp32())
+            if e["max_rel"] > worst:
+                worst, worst_q = e["max_rel"], k
+        workers = pool.workers
+    return {"max_rel": worst, "worst_query": worst_q, "queries": len(qs), "documents": int(docs.size),
+            "tolerance": 1e-5, "oracle_workers": workers, "oracle_wall_s": time.perf_counter() - t0,
+            "sample": f"every query on {docs.size} seeded documents (20 longest and 20 shortest included)"}
+
+
+def bench_serving(wmd, device, n_requests=1000, seed=11, workload="serving", n_checked=16):
+    """Poisson arrivals (v_r ~ U[5,200]) against the full serving corpus (or
+    the paper-shaped one): latency p50/p99 and throughput of the
+    continuous-batching server at 0.1x to 1.2x of its measured capacity, the
+    one-query-at-a-time capacity, and the served results of n_checked
+    distinct queries (v_r = 200 among them) against the FP64 oracle."""
     import threading as th
     w = synth.SERVING if workload == "serving" else synth.PAPER
-    vecs, c, _ = synth.make_workload(w)
+    vecs, c, _ = synth.make_workload(w, 0)
     corpus = wmd.Corpus.from_synth(vecs, c, device=device)
     rng = np.random.default_rng(seed)
-    qs = [synth.make_query(w.V, int(rng.integers(5, 201)), 50_000 + i) for i in range(64)]
+    qs = [synth.make_query(w.V, 200 if i == 0 else int(rng.integers(5, 201)), 50_000 + i)
+          for i in range(64)]
+    served = {}   # query index -> its first served result (n_checked distinct queries)
     for vr in (8, 16, 32, 64, 128, 256):
         q = next((q for q in qs if (len(q[0]) <= vr and len(q[0]) > vr // 2)), None)
         if q is not None:
@@ -407,8 +440,9 @@ def bench_serving(wmd, device, n_requests=300, seed=11, workload="paper"):
         rates = []
         for frac in (0.1, 0.5, 0.9, 1.2):
             rate = frac * capacity
-            arrivals = np.cumsum(rng.exponential(1.0 / rate, n_requests))
-            sub_t, done_t, tickets = {}, {}, []
+            n_rate = max(n_requests // 5, 16) if frac < 0.5 else n_requests
+            arrivals = np.cumsum(rng.exponential(1.0 / rate, n_rate))
+            sub_t, done_t, tickets, qidx = {}, {}, [], {}
             lock = th.Lock()
             finished = th.Event()
 
@@ -423,6 +457,7 @@ def bench_serving(wmd, device, n_requests=300, seed=11, workload="paper"):
                     with lock:
                         sub_t[tk] = time.perf_counter()
                         tickets.append(tk)
+                        qidx[tk] = k % len(qs)
                 finished.set()
 
             th_sub = th.Thread(target=submitter)
@@ -447,6 +482,10 @@ def bench_serving(wmd, device, n_requests=300, seed=11, workload="paper"):
                         raise
                     done_t[tk] = time.perf_counter()
                     pending.remove(tk)
+                    with lock:
+                        qk = qidx[tk]
+                    if qk < n_checked and qk not in served:
+                        served[qk] = buf.copy()
                 time.sleep(0.0002)
             th_sub.join()
             lat = np.array([done_t[t] - sub_t[t] for t in done_t]) * 1e3
@@ -459,12 +498,101 @@ def bench_serving(wmd, device, n_requests=300, seed=11, workload="paper"):
     finally:
         srv.close()
         corpus.close()
-    return {"workload": (f"serving against {w.name} corpus: queries v_r U[5,200], lambda={w.lam:g}, "
-                         f"max_iter={w.max_iter}, Poisson arrivals, {n_requests} requests per rate"),
+    err = None
+    if served:
+        # after the timed rates: the oracle workers load the host cores
+        from oracle.pool import OraclePool, sample_documents
+        docs = sample_documents(c.doc_ptr, 200)
+        worst, worst_q, t0 = 0.0, -1, time.perf_counter()
+        with OraclePool(w.cfg) as pool:
+            futs = {k: pool.submit(qs[k][0], qs[k][1], w.lam, w.max_iter, docs) for k in served}
+            for k, f in futs.items():
+                ref, _ = f.result(timeout=3600)
+                e = error_vs_oracle(served[k][docs], ref, wmd_prec_fp32())
+                if e["max_rel"] > worst:
+                    worst, worst_q = e["max_rel"], k
+        err = {"max_rel": worst, "worst_request_query": worst_q, "requests": len(served),
+               "documents": int(docs.size), "tolerance": 1e-5,
+               "v_r": sorted(int(len(qs[k][0])) for k in served),
+               "oracle_wall_s": time.perf_counter() - t0,
+               "sample": f"the first served result of {len(served)} distinct queries, each on "
+                         f"{docs.size} seeded documents (20 longest and 20 shortest included)"}
+    return {"workload": (f"serving against {w.name} corpus: V={w.V} N={w.N} docs of "
+                         f"{w.doc_lo}-{w.doc_hi} words, queries v_r U[5,200], lambda={w.lam:g}, "
+                         f"max_iter={w.max_iter}, Poisson arrivals, {n_requests} requests per rate "
+                         f"({max(n_requests // 5, 16)} at 0.1x)"),
+            "error_vs_oracle": err,
             "one_at_a_time_qps": single_qps, "capacity_qps": capacity,
             "capacity_wmds_per_s": capacity * c.N, "one_at_a_time_wmds_per_s": single_qps * c.N,
             "rates": rates, "server": {"max_batch": 32, "slots": 3, "batches": stats["batches"],
                                        "max_batch_seen": stats["max_batch_seen"]}}
+
+
+def alu_peak_tflops(device, sm_max_mhz):
+    """FP32 FMA peak: the device's SM count x 128 FP32 lanes x 2 flop x the
+    maximum SM clock."""
+    import torch
+    sms = torch.cuda.get_device_properties(device).multi_processor_count
+    return sms * FP32_LANES_PER_SM * 2 * sm_max_mhz * 1e6 / 1e12, sms
+
+
+def bench_large(wmd, device, steps=5):
+    """The large workload (V = N = 100,000, 20-200 Zipf words per document,
+    about 11 M nonzeros, v_r = 64): one query per step (cdist + fused loop,
+    CUDA events on the launching stream, L2 flushed between steps) with K
+    stored in float32 and in bfloat16 (float32 arithmetic), each compared with
+    the FP64 oracle on the same seeded document sample."""
+    import torch
+    w = synth.LARGE
+    vecs, c, qs = synth.make_workload(w)
+    q_ids, q_w = qs[0]
+    dev = torch.device("cuda", device)
+    stream = torch.cuda.current_stream(dev)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    corpus = wmd.Corpus.from_synth(vecs, c, device=device)
+    peaks, _ = measured_peaks()
+    alu, _ = alu_peak_tflops(dev, peaks.get("sm_max_mhz", 2070.0))
+    flops = 4.0 * len(q_ids) * c.nnz * (w.max_iter + 1)
+    rec, results = {}, {}
+    for name, prec in (("fp32", wmd.PREC_FP32), ("bf16_k", wmd.PREC_BF16_K)):
+        variant = corpus.autotune(q_ids, q_w, w.lam, w.max_iter, prec)
+        dq = wmd.DeviceQuery(corpus, q_ids, q_w, prec)
+        ev = []
+        for k in range(steps + 2):
+            flush.zero_()
+            e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+            e[0].record(stream)
+            corpus.build_kernel_matrix(dq.ids, dq.w, dq.v_r, w.lam, prec, dq.ws, dq.ws_bytes, stream)
+            e[1].record(stream)
+            corpus.sinkhorn_loop(dq.v_r, w.max_iter, prec, dq.ws, dq.ws_bytes, dq.out, stream)
+            e[2].record(stream)
+            if k >= 2:
+                ev.append(e)
+        torch.cuda.synchronize()
+        cd = statistics.mean(a.elapsed_time(b) for a, b, _ in ev)
+        lp = statistics.mean(b.elapsed_time(cc) for _, b, cc in ev)
+        st = statistics.mean(a.elapsed_time(cc) for a, _, cc in ev)
+        results[name] = dq.out[: c.N].cpu().numpy()
+        rec[name] = {"ms_per_step": st, "cdist_ms": cd, "loop_ms": lp, "value": c.N / (st * 1e-3),
+                     "unit": UNIT, "loop_tflops": flops / (lp * 1e-3) / 1e12,
+                     "loop_alu_frac": flops / (lp * 1e-3) / 1e12 / alu, "loop_variant": variant}
+    corpus.close()
+    docs = oracle_docs(c)
+    from oracle.pool import OraclePool
+    t0 = time.perf_counter()
+    with OraclePool(w.cfg) as pool:
+        chunks = [ch for ch in np.array_split(docs, pool.workers) if ch.size]
+        futs = [pool.submit(q_ids, q_w, w.lam, w.max_iter, ch) for ch in chunks]
+        ref = np.concatenate([f.result(timeout=3600)[0] for f in futs])
+    rec["fp32"]["error_vs_oracle"] = error_vs_oracle(results["fp32"][docs], ref, wmd.PREC_FP32)
+    rec["bf16_k"]["error_vs_oracle"] = error_vs_oracle(results["bf16_k"][docs], ref, wmd.PREC_BF16_K)
+    rec["workload"] = (f"{w.name}: V={w.V} d={w.d} N={w.N} docs of {w.doc_lo}-{w.doc_hi} Zipf(1.1) "
+                       f"words ({c.nnz} nonzeros), v_r={len(q_ids)}, lambda={w.lam:g}, "
+                       f"max_iter={w.max_iter}")
+    rec["oracle_sample"] = (f"{docs.size} of {c.N} documents (seeded, 20 longest and 20 shortest "
+                            f"included), oracle in {time.perf_counter() - t0:.1f} s on spawned workers")
+    rec["l2"] = "flushed between steps (512 MiB write)"
+    return rec
 
 
 # ------------------------------------------------------------------ ours
@@ -678,7 +806,8 @@ def run_ours(args, w):
     # fp16 hi + lo rows of the active vocabulary, K, norms and row scales, the query rows
     cdist_bytes = U * ldv * 4 + U * VR * kelem + U * 8 + v_r * ldv * 4
     loop_flops = 4.0 * v_r * c.nnz * (w.max_iter + 1)
-    alu_peak = NUM_SMS * FP32_LANES_PER_SM * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6
+    alu_tf, num_sms = alu_peak_tflops(dev, peaks.get("sm_max_mhz", 2070.0))
+    alu_peak = alu_tf * 1e12
     kernels = {
         "cdist_k": {"ms": cdist_ms, "bound": "hbm", "bytes": cdist_bytes,
                     "achieved_gbs": cdist_bytes / (cdist_ms * 1e-3) / 1e9},
@@ -697,15 +826,16 @@ def run_ours(args, w):
         pk = alu_peak / 1e12
         roof = {"kernel": "sinkhorn_fused", "bound": "alu", "achieved": ach, "peak": pk,
                 "unit": "TFLOP/s", "frac": ach / pk, "traffic": recorded_traffic("sinkhorn_fused", w.name, loop_variant),
-                "peak_source": "152 SMs x 128 FP32 lanes x 2 flop x max SM clock"}
+                "peak_source": f"{num_sms} SMs (from the device) x 128 FP32 lanes x 2 flop x max SM clock"}
 
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": max(args.warmup, 3), "ms_per_step": step_ms_max, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32" if prec == wmd.PREC_FP32 else "bf16-K/f32",
         "data": "synthetic (seeded Zipf(1.1) corpus, N(0,1/d) embeddings)",
-        "config": {"workload": workload_name(w), "v_r": v_r, "nnz": c.nnz, "active_words": U,
-                   "loop_variant": loop_variant,
+        "config": {"workload": workload_name(w), "V": w.V, "d": w.d, "N": w.N, "v_r": v_r,
+                   "lambda": w.lam, "max_iter": w.max_iter, "nnz": c.nnz, "active_words": U,
+                   "loop_variant": loop_variant, "cdist_kernel": corpus.cdist_kernel,
                    "l2": "flushed between steps (512 MiB write)",
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(v_r * 8),
@@ -730,8 +860,10 @@ def run_ours(args, w):
             out["topk"] = bench_topk(wmd, dq, c.N, stream)
         if "dense" in legs and prec == wmd.PREC_FP32:
             out["dense"] = bench_dense(wmd, corpus, dq, w, stream, flush)
+        if "large" in legs:
+            out["large"] = bench_large(wmd, local_rank)
         if "batched" in legs:
-            out["batched"] = bench_batched(wmd, local_rank)
+            out["batched"] = bench_batched(wmd, local_rank, with_oracle=not args.no_cpu_baseline)
         if "serving" in legs:
             out["serving"] = bench_serving(wmd, local_rank, args.serve_requests,
                                            workload=args.serving_workload)

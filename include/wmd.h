@@ -39,8 +39,15 @@
  *    when max_iter == 0.
  *  - Arithmetic: float32 for the loop (the BF16_K precision stores K in
  *    bfloat16 and still accumulates in float32), float64 for the final
- *    per-document sum.  Valid while lambda * max(M) < 87 so that K stays a
- *    normal float32.
+ *    per-document sum.  Valid while lambda * M < 87.3 for every query word
+ *    and active vocabulary word, so that K = exp(-lambda M) stays a normal
+ *    float32.  The cdist kernel checks this for every entry it writes; a
+ *    query that leaves the range gets NaN for every document, and the host
+ *    entry points (wmd_query, wmd_query_batch, the server) report
+ *    WMD_ERR_RANGE.
+ *  - Device-side errors are per query: every query (or batch) clears its
+ *    own error words, kept in its workspace, before its first kernel, so a
+ *    failed query never affects a later one or one running beside it.
  */
 #ifndef WMD_GB300_H
 #define WMD_GB300_H
@@ -61,7 +68,9 @@ typedef enum wmd_status {
   WMD_ERR_NOT_READY = 4,     /* a served request has not finished yet          */
   WMD_ERR_TIMEOUT = 5,       /* a bounded wait ran out                         */
   WMD_ERR_SHUTDOWN = 6,      /* the server is shutting down                    */
-  WMD_ERR_UNSUPPORTED = 7    /* e.g. v_r above WMD_MAX_VR                      */
+  WMD_ERR_UNSUPPORTED = 7,   /* e.g. v_r above WMD_MAX_VR                      */
+  WMD_ERR_RANGE = 8          /* lambda * M reached 87.3 for some word pair: K
+                                would leave the float32 range (results NaN)   */
 } wmd_status;
 
 typedef enum wmd_precision {
@@ -83,7 +92,64 @@ typedef struct wmd_corpus_info {
   int64_t U;        /* active vocabulary: words that occur in some document  */
   int32_t device;   /* CUDA device holding the corpus                        */
   size_t device_bytes; /* device memory held by the corpus                   */
+  int32_t cdist_kernel; /* which kernel builds K for this corpus:
+                           WMD_CDIST_TENSOR_CORES (tcgen05, the default) or
+                           WMD_CDIST_CUDA_CORES (chosen by the options, or
+                           because the tensor map of the vocabulary could not
+                           be built)                                          */
 } wmd_corpus_info;
+
+#define WMD_CDIST_TENSOR_CORES 0
+#define WMD_CDIST_CUDA_CORES 1
+
+/* ---------------------------------------------------------------------------
+ * Library options, given to wmd_corpus_load (NULL = the defaults that
+ * wmd_options_default writes).  They configure the services around the
+ * method, not the method itself.
+ *
+ * device            CUDA device ordinal that holds the corpus (default 0).
+ * use_graphs        1 (default): wmd_query and wmd_query_batch capture their
+ *                   kernel sequence into a CUDA graph on the second call of a
+ *                   query shape and replay it afterwards; 0: always launch
+ *                   the kernels one by one.
+ * cdist_kernel      WMD_CDIST_TENSOR_CORES (default) or WMD_CDIST_CUDA_CORES
+ *                   (the float32 FMA kernel; for comparison and for widths
+ *                   the tensor-core kernel cannot hold).  The environment
+ *                   variable WMD_CDIST_KERNEL=simt also selects it.
+ * autotune_cache    path of a text file of tuned fused-loop tile variants
+ *                   (NULL: the environment variable WMD_AUTOTUNE_CACHE, else
+ *                   no file).  wmd_corpus_load applies the entries recorded
+ *                   for a corpus of the same shape (V, d, N, nnz, active
+ *                   words); wmd_autotune appends its choice.  A missing or
+ *                   unreadable file is ignored; a line that does not parse is
+ *                   skipped.
+ * wait_limit_cycles limit, in SM clock cycles, of each device-side wait of
+ *                   the tensor-core cdist kernel between its roles (0: the
+ *                   default, 4e9 cycles, about 2 s).  A wait that runs out
+ *                   makes the query return WMD_ERR_TIMEOUT with NaN results;
+ *                   the kernel still retires every copy and tensor-core
+ *                   operation it issued before it returns.  Tests set it low
+ *                   to exercise that path.
+ * server            defaults of wmd_server_create(corpus, NULL, ...).
+ * ------------------------------------------------------------------------- */
+typedef struct wmd_server_options {
+  int32_t max_batch;   /* most requests in one batch (default 64)              */
+  int32_t slots;       /* batches in flight at once (default 2, at most 16)    */
+  size_t mem_budget;   /* device bytes shared by all slots (default 8 GiB)     */
+  int64_t max_pending; /* waiting requests before submit refuses (default 65536) */
+} wmd_server_options;
+
+typedef struct wmd_options {
+  int32_t device;
+  int32_t use_graphs;
+  int32_t cdist_kernel;
+  const char* autotune_cache;
+  int64_t wait_limit_cycles;
+  wmd_server_options server;
+} wmd_options;
+
+/* Writes the defaults listed above into *opt. */
+void wmd_options_default(wmd_options* opt);
 
 /* Thread-local description of the last failure in this thread ("" if none). */
 const char* wmd_last_error(void);
@@ -111,7 +177,8 @@ wmd_status wmd_compact_query(const int32_t* q_ids, const float* q_w, int32_t n_q
  *          row_ptr[0] = 0, non-decreasing, row_ptr[V] = nnz), doc_idx[nnz]
  *          (int32 document ids in [0, N), strictly increasing within a row),
  *          val[nnz] (float32, finite and > 0).  All host.
- * device:  CUDA device ordinal that will hold the corpus.
+ * opt:     library options (device, graphs, cdist kernel, autotune cache,
+ *          device wait limit, server defaults); NULL = wmd_options_default.
  * On success *out receives a corpus that keeps resident on the device, until
  * wmd_corpus_free: vecs (rows permuted so that words occurring in some
  * document come first), the row norms, the same rows as fp16 hi/lo pairs with
@@ -124,13 +191,19 @@ wmd_status wmd_compact_query(const int32_t* q_ids, const float* q_w, int32_t n_q
 wmd_status wmd_corpus_load(const float* vecs, int64_t V, int32_t d,
                            const int64_t* row_ptr, const int32_t* doc_idx,
                            const float* val, int64_t N, int64_t nnz,
-                           int32_t device, wmd_corpus** out);
+                           const wmd_options* opt, wmd_corpus** out);
 
 /* Frees a corpus (NULL is accepted).  The caller must not free a corpus that
  * a server or an in-flight device call still uses. */
 void wmd_corpus_free(wmd_corpus* corpus);
 
 wmd_status wmd_corpus_get_info(const wmd_corpus* corpus, wmd_corpus_info* out);
+
+/* Changes the corpus's wait_limit_cycles (see wmd_options; 0 = the default)
+ * for every later query, and drops the CUDA graphs captured with the old
+ * limit.  Not thread-safe against queries running on this corpus or a server
+ * using it. */
+wmd_status wmd_corpus_set_wait_limit(wmd_corpus* corpus, int64_t cycles);
 
 /* ---------------------------------------------------------------------------
  * One query, host buffers, synchronous (Sec. 3 `sinkhorn_wmd(r, c, vecs,
@@ -292,14 +365,19 @@ wmd_status wmd_query_dense(wmd_corpus* corpus, const int32_t* d_q_ids, const flo
  * resident warps.  wmd_loop_variant_count: how many exist for queries of v_r
  * words.  wmd_set_loop_variant: use `variant` for v_r's class and `prec` on
  * this corpus (all later calls; not thread-safe against running queries).
+ * wmd_get_loop_variant: the variant in use for v_r's class and `prec` (-1
+ * for a NULL corpus, v_r out of range or an unknown precision).
  * wmd_autotune: synchronous; builds K for the given query (host buffers, as
  * wmd_query), times every variant of its class on this corpus with CUDA
  * events, keeps the fastest for that class and precision and writes its
- * index to *chosen (may be NULL).  Allocates a temporary workspace.
+ * index to *chosen (may be NULL).  Allocates a temporary workspace.  With an
+ * autotune cache (wmd_options) the choice is appended to the cache file, and
+ * corpora of the same shape loaded later start from it.
  * ------------------------------------------------------------------------- */
 int32_t wmd_loop_variant_count(int32_t v_r);
 wmd_status wmd_set_loop_variant(wmd_corpus* corpus, int32_t v_r, wmd_precision prec,
                                 int32_t variant);
+int32_t wmd_get_loop_variant(const wmd_corpus* corpus, int32_t v_r, wmd_precision prec);
 wmd_status wmd_autotune(wmd_corpus* corpus, const int32_t* q_ids, const float* q_w,
                         int32_t n_q, float lambda, int32_t max_iter, wmd_precision prec,
                         int32_t* chosen);
@@ -343,13 +421,9 @@ wmd_status wmd_query_batch(wmd_corpus* corpus, int32_t nq, const int64_t* q_ptr,
  * requests already wait, WMD_ERR_SHUTDOWN during wmd_server_destroy.
  * wmd_server_destroy finishes the batches on the GPU, fails the requests
  * still waiting with WMD_ERR_SHUTDOWN and frees the server (not the corpus).
+ * Device-side errors (WMD_ERR_TIMEOUT, WMD_ERR_RANGE) are kept per slot and
+ * cleared before each batch: they fail the requests of that batch only.
  * ------------------------------------------------------------------------- */
-typedef struct wmd_server_options {
-  int32_t max_batch;   /* most requests in one batch (default 64)              */
-  int32_t slots;       /* batches in flight at once (default 2, at most 16)    */
-  size_t mem_budget;   /* device bytes shared by all slots (default 8 GiB)     */
-  int64_t max_pending; /* waiting requests before submit refuses (default 65536) */
-} wmd_server_options;
 
 typedef struct wmd_server_stats {
   int64_t submitted;
@@ -361,7 +435,7 @@ typedef struct wmd_server_stats {
   int64_t in_flight_batches;
 } wmd_server_stats;
 
-/* opt: NULL for the defaults. */
+/* opt: NULL for the defaults given to wmd_corpus_load (wmd_options.server). */
 wmd_status wmd_server_create(wmd_corpus* corpus, const wmd_server_options* opt,
                              wmd_server** out);
 wmd_status wmd_serve_submit(wmd_server* server, const int32_t* q_ids, const float* q_w,
@@ -383,12 +457,15 @@ void wmd_server_destroy(wmd_server* server);
  * d_ws: the workspace is a 16 MiB scratch array compiled into the library
  * (every GPU that loads the library holds it until the process exits).
  * Queries whose workspace (wmd_workspace_bytes) exceeds 16 MiB are rejected
- * with WMD_ERR_UNSUPPORTED.  The first call on a device looks up the array's
- * device address for that device; make that first call before any stream
- * capture.  All calls share the one array and each call overwrites what it
- * reads, so calls whose kernels overlap on the GPU (different streams, or
- * different corpora on the same device) race and must be serialised by the
- * caller.  Allocates no memory: no cudaMalloc, no cudaFree.
+ * with WMD_ERR_UNSUPPORTED.  wmd_corpus_load, which allocates anyway, looks
+ * up the array's device address on the corpus's device, so the driver
+ * reserves the array there at load time and this call itself never touches
+ * the allocator; the call only reads that recorded address.  Every call
+ * clears the array's error words before its first kernel.  All calls share
+ * the one array and each call overwrites what it reads, so calls whose
+ * kernels overlap on the GPU (different streams, or different corpora on the
+ * same device) race and must be serialised by the caller.  Allocates no
+ * memory: no cudaMalloc, no cudaFree.
  * ------------------------------------------------------------------------- */
 wmd_status wmd_query_device_noalloc(wmd_corpus* corpus, const int32_t* d_q_ids,
                                     const float* d_q_w, int32_t v_r, float lambda,

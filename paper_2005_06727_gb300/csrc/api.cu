@@ -55,7 +55,6 @@ void free_corpus_device(wmd_corpus* c) {
   cudaFree(c->doc_ptr);
   cudaFree(c->doc_words);
   cudaFree(c->doc_vals);
-  cudaFree(c->d_err);
   for (auto& sc : c->sched)
     for (auto& s : sc) cudaFree(s.d_tasks);
   cudaFree(c->ws);
@@ -65,6 +64,40 @@ void free_corpus_device(wmd_corpus* c) {
     if (g.exec) cudaGraphExecDestroy(g.exec);
   c->qgraphs.clear();
   if (c->stream) cudaStreamDestroy(c->stream);
+}
+
+// ---------------------------------------------------------------- autotune cache
+// One line per tuned choice: "wmd-loop V d N nnz U class precision variant".
+// A corpus applies the lines recorded for its own shape; the last one wins.
+void load_autotune_cache(wmd_corpus* c) {
+  if (c->autotune_cache.empty()) return;
+  FILE* f = std::fopen(c->autotune_cache.c_str(), "r");
+  if (!f) return;
+  char line[256];
+  while (std::fgets(line, sizeof line, f)) {
+    long long V, N, nnz, U;
+    int d, cls, prec, var;
+    if (std::sscanf(line, "wmd-loop %lld %d %lld %lld %lld %d %d %d", &V, &d, &N, &nnz, &U, &cls,
+                    &prec, &var) != 8)
+      continue;
+    if (V != c->V || d != c->d || N != c->N || nnz != c->nnz || U != c->U) continue;
+    if (cls < 0 || cls >= kNumClasses || prec < 0 || prec > 1 || var < 0 ||
+        var >= kClassVariants[cls])
+      continue;
+    c->loop_variant[cls][prec] = var;
+  }
+  std::fclose(f);
+}
+
+void save_autotune_choice(const wmd_corpus* c, int cls, int prec, int var) {
+  if (c->autotune_cache.empty()) return;
+  static std::mutex mu;
+  std::lock_guard<std::mutex> lock(mu);
+  FILE* f = std::fopen(c->autotune_cache.c_str(), "a");
+  if (!f) return;
+  std::fprintf(f, "wmd-loop %lld %d %lld %lld %lld %d %d %d\n", (long long)c->V, (int)c->d,
+               (long long)c->N, (long long)c->nnz, (long long)c->U, cls, prec, var);
+  std::fclose(f);
 }
 
 wmd_status check_query_args(const wmd_corpus* c, int v_r, float lambda, int T) {
@@ -101,10 +134,32 @@ wmd_status cuda_error(cudaError_t e, const char* what) {
   return e == cudaErrorMemoryAllocation ? WMD_ERR_OUT_OF_MEMORY : WMD_ERR_CUDA;
 }
 
+wmd_status device_error(int err) {
+  if (err & 0x40000000) {
+    static const char* roles[] = {"?", "producer (stage free)", "?",
+                                  "MMA (accumulator free)", "MMA (tile landed)",
+                                  "epilogue (accumulator full)", "?",
+                                  "producer (query gathers in flight)"};
+    const int role = (err >> 24) & 0x3f;
+    char msg[160];
+    std::snprintf(msg, sizeof msg,
+                  "a device-side wait in the cdist kernel timed out: %s, iteration %d (code 0x%08x)",
+                  roles[role < 8 ? role : 0], err & 0xffffff, (unsigned)err);
+    return set_error(WMD_ERR_TIMEOUT, msg);
+  }
+  if (err & kRangeFlag)
+    return set_error(WMD_ERR_RANGE,
+                     "lambda * M reached 87.3 for some query word and vocabulary word: "
+                     "K = exp(-lambda M) leaves the float32 range (lower lambda)");
+  return WMD_OK;
+}
+
 WsLayout ws_layout(const wmd_corpus* c, int VR, wmd_precision prec) {
   WsLayout L;
   size_t o = 0;
-  L.r_off = o;    o = align_up(o + (size_t)(VR + 4) * sizeof(float), 256);  // r, lambda, scale
+  L.r_off = o;
+  L.err_off = o + (size_t)(VR + 4) * sizeof(float);
+  o = align_up(o + (size_t)(VR + 4 + kErrWords) * sizeof(float), 256);  // r, lambda, scale, errors
   const size_t kelem = prec == WMD_PREC_BF16_K ? 2 : 4;
   const size_t kbytes = align_up((size_t)std::max<int64_t>(c->U, 1) * VR * kelem, 256);
   L.k_off = o;
@@ -121,7 +176,21 @@ extern "C" {
 
 const char* wmd_last_error(void) { return g_last_error.c_str(); }
 
-const char* wmd_version(void) { return "wmd-gb300 0.1 (sm_103a)"; }
+const char* wmd_version(void) { return "wmd-gb300 0.2 (sm_103a)"; }
+
+void wmd_options_default(wmd_options* opt) {
+  if (!opt) return;
+  std::memset(opt, 0, sizeof(*opt));
+  opt->device = 0;
+  opt->use_graphs = 1;
+  opt->cdist_kernel = WMD_CDIST_TENSOR_CORES;
+  opt->autotune_cache = nullptr;
+  opt->wait_limit_cycles = 0;
+  opt->server.max_batch = 64;
+  opt->server.slots = 2;
+  opt->server.mem_budget = size_t(8) << 30;
+  opt->server.max_pending = 65536;
+}
 
 wmd_status wmd_compact_query(const int32_t* q_ids, const float* q_w, int32_t n_q, int64_t V,
                              int32_t* out_ids, float* out_w, int32_t* out_vr) {
@@ -153,10 +222,21 @@ wmd_status wmd_compact_query(const int32_t* q_ids, const float* q_w, int32_t n_q
 
 wmd_status wmd_corpus_load(const float* vecs, int64_t V, int32_t d, const int64_t* row_ptr,
                            const int32_t* doc_idx, const float* val, int64_t N, int64_t nnz,
-                           int32_t device, wmd_corpus** out) {
+                           const wmd_options* opt, wmd_corpus** out) {
   wmd::NvtxRange nvtx_range("wmd_corpus_load");
   if (!out) return set_error(WMD_ERR_INVALID_ARG, "out is NULL");
   *out = nullptr;
+  wmd_options o;
+  wmd_options_default(&o);
+  if (opt) o = *opt;
+  if (o.device < 0) return set_error(WMD_ERR_INVALID_ARG, "device ordinal < 0");
+  if (o.cdist_kernel != WMD_CDIST_TENSOR_CORES && o.cdist_kernel != WMD_CDIST_CUDA_CORES)
+    return set_error(WMD_ERR_INVALID_ARG, "unknown cdist kernel");
+  if (o.wait_limit_cycles < 0) return set_error(WMD_ERR_INVALID_ARG, "wait_limit_cycles < 0");
+  if (o.server.max_batch <= 0 || o.server.slots <= 0 || o.server.slots > 16 ||
+      o.server.mem_budget == 0 || o.server.max_pending <= 0)
+    return set_error(WMD_ERR_INVALID_ARG, "server options out of range");
+  const int32_t device = o.device;
   if (V <= 0 || V > INT32_MAX) return set_error(WMD_ERR_INVALID_ARG, "V must be in [1, 2^31)");
   if (d <= 0) return set_error(WMD_ERR_INVALID_ARG, "d must be positive");
   if (N < 0 || N > INT32_MAX) return set_error(WMD_ERR_INVALID_ARG, "N must be in [0, 2^31)");
@@ -182,6 +262,14 @@ wmd_status wmd_corpus_load(const float* vecs, int64_t V, int32_t d, const int64_
   wmd_corpus* c = new (std::nothrow) wmd_corpus();
   if (!c) return set_error(WMD_ERR_OUT_OF_MEMORY, "host allocation failed");
   c->device = device;
+  c->use_graphs = o.use_graphs != 0;
+  c->wait_cycles = o.wait_limit_cycles;
+  c->server_defaults = o.server;
+  if (o.autotune_cache) {
+    c->autotune_cache = o.autotune_cache;
+  } else if (const char* env = std::getenv("WMD_AUTOTUNE_CACHE")) {
+    c->autotune_cache = env;
+  }
   c->V = V;
   c->N = N;
   c->nnz = nnz;
@@ -289,18 +377,18 @@ wmd_status wmd_corpus_load(const float* vecs, int64_t V, int32_t d, const int64_
   if (e == cudaSuccess) e = upload(&c->doc_ptr, dptr.data(), dptr.size(), &bytes);
   if (e == cudaSuccess) e = upload(&c->doc_words, dwords.data(), dwords.size(), &bytes);
   if (e == cudaSuccess) e = upload(&c->doc_vals, dvals.data(), dvals.size(), &bytes);
-  if (e == cudaSuccess) {
-    const int zero = 0;
-    e = upload(&c->d_err, &zero, 1, &bytes);
-  }
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device);
   if (e == cudaSuccess) {
-    // WMD_CDIST_KERNEL=simt keeps cdist on the CUDA cores (used by the tests
-    // that compare both kernels); otherwise the tensor-core kernel is used
+    // the options (or WMD_CDIST_KERNEL=simt, used by the tests that compare
+    // both kernels) keep cdist on the CUDA cores; otherwise the tensor-core
+    // kernel is used wherever its tensor map can be built
     const char* kern = std::getenv("WMD_CDIST_KERNEL");
-    const bool simt = kern && std::strcmp(kern, "simt") == 0;
+    const bool simt = o.cdist_kernel == WMD_CDIST_CUDA_CORES || (kern && std::strcmp(kern, "simt") == 0);
     c->tmap_ok = !simt && make_vecs_tensor_map(c);
   }
+  // the no-allocation entry point's scratch array is reserved now, while
+  // allocating is allowed anyway (its first query then allocates nothing)
+  if (e == cudaSuccess) e = noalloc_reserve(device);
 
   // per query-width class and tile variant: team size per document and CTA
   // work items (a CTA's 4/W teams take consecutive documents of one team size)
@@ -348,6 +436,7 @@ wmd_status wmd_corpus_load(const float* vecs, int64_t V, int32_t d, const int64_
     delete c;
     return st;
   }
+  load_autotune_cache(c);
   *out = c;
   return WMD_OK;
 }
@@ -363,6 +452,21 @@ void wmd_corpus_free(wmd_corpus* c) {
   delete c;
 }
 
+wmd_status wmd_corpus_set_wait_limit(wmd_corpus* c, int64_t cycles) {
+  if (!c) return set_error(WMD_ERR_INVALID_ARG, "corpus is NULL");
+  if (cycles < 0) return set_error(WMD_ERR_INVALID_ARG, "wait limit < 0");
+  std::lock_guard<std::mutex> lock(c->mu);
+  DeviceGuard g(c->device);
+  // captured sequences hold the old limit in their kernel parameters
+  if (c->stream) cudaStreamSynchronize(c->stream);
+  for (auto& q : c->qgraphs)
+    if (q.exec) cudaGraphExecDestroy(q.exec);
+  c->qgraphs.clear();
+  release_batch_state(c);
+  c->wait_cycles = cycles;
+  return WMD_OK;
+}
+
 wmd_status wmd_corpus_get_info(const wmd_corpus* c, wmd_corpus_info* out) {
   if (!c || !out) return set_error(WMD_ERR_INVALID_ARG, "NULL pointer");
   out->V = c->V;
@@ -372,6 +476,7 @@ wmd_status wmd_corpus_get_info(const wmd_corpus* c, wmd_corpus_info* out) {
   out->U = c->U;
   out->device = c->device;
   out->device_bytes = c->device_bytes;
+  out->cdist_kernel = cdist_tc_max_width(c) > 0 ? WMD_CDIST_TENSOR_CORES : WMD_CDIST_CUDA_CORES;
   return WMD_OK;
 }
 
@@ -394,9 +499,11 @@ wmd_status wmd_build_kernel_matrix(wmd_corpus* c, const int32_t* d_q_ids, const 
   char* ws = static_cast<char*>(d_ws);
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   float* r = reinterpret_cast<float*>(ws + L.r_off);
+  int* err = reinterpret_cast<int*>(ws + L.err_off);
   const L2Prefetch pf = loop_inputs(c, vr_class(v_r), prec);
+  WMD_CUDA_TRY(clear_errors(err, s));
   WMD_CUDA_TRY(launch_cdist(c, d_q_ids, d_q_w, v_r, VR, lambda, prec, ws + L.k_off, VR, 0, r,
-                            r + VR, &pf, s));
+                            r + VR, err, &pf, s));
   return WMD_OK;
 }
 
@@ -416,8 +523,9 @@ wmd_status sinkhorn_loop(wmd_corpus* c, int32_t v_r, int32_t max_iter, wmd_preci
   const WsLayout L = ws_layout(c, VR, prec);
   char* ws = static_cast<char*>(d_ws);
   const float* r = reinterpret_cast<const float*>(ws + L.r_off);
+  const int* err = reinterpret_cast<const int*>(ws + L.err_off);
   WMD_CUDA_TRY(launch_loop(c, cls, ws + L.k_off, VR, 0, r, r + VR, v_r, max_iter, prec, d_out,
-                           err_out, static_cast<cudaStream_t>(stream)));
+                           err, err_out, static_cast<cudaStream_t>(stream)));
   return WMD_OK;
 }
 
@@ -435,6 +543,11 @@ wmd_status wmd_query_device(wmd_corpus* c, const int32_t* d_q_ids, const float* 
   wmd::NvtxRange nvtx_range("wmd_query_device");
   wmd_status st = check_query_args(c, v_r, lambda, max_iter);
   if (st != WMD_OK) return st;
+  // every argument is checked before the first launch, so that a refused call
+  // writes nothing (not even the workspace)
+  if (!d_out && c->N > 0) return set_error(WMD_ERR_INVALID_ARG, "d_out is NULL");
+  if (!d_q_ids || !d_q_w) return set_error(WMD_ERR_INVALID_ARG, "NULL query pointer");
+  if ((st = check_ws(c, v_r, prec, d_ws, ws_bytes)) != WMD_OK) return st;
   st = wmd_build_kernel_matrix(c, d_q_ids, d_q_w, v_r, lambda, prec, d_ws, ws_bytes, stream);
   if (st != WMD_OK) return st;
   return wmd_sinkhorn_loop(c, v_r, max_iter, prec, d_ws, ws_bytes, d_out, stream);
@@ -449,6 +562,8 @@ wmd_status wmd_query_device_tol(wmd_corpus* c, const int32_t* d_q_ids, const flo
   if (st != WMD_OK) return st;
   if (!(tol >= 0.f && tol < 1.f)) return set_error(WMD_ERR_INVALID_ARG, "tol must lie in [0, 1)");
   if (!d_out && c->N > 0) return set_error(WMD_ERR_INVALID_ARG, "d_out is NULL");
+  if (!d_q_ids || !d_q_w) return set_error(WMD_ERR_INVALID_ARG, "NULL query pointer");
+  if ((st = check_ws(c, v_r, prec, d_ws, ws_bytes)) != WMD_OK) return st;
   st = wmd_build_kernel_matrix(c, d_q_ids, d_q_w, v_r, lambda, prec, d_ws, ws_bytes, stream);
   if (st != WMD_OK) return st;
   DeviceGuard g(c->device);
@@ -457,8 +572,9 @@ wmd_status wmd_query_device_tol(wmd_corpus* c, const int32_t* d_q_ids, const flo
   const WsLayout L = ws_layout(c, VR, prec);
   char* ws = static_cast<char*>(d_ws);
   const float* r = reinterpret_cast<const float*>(ws + L.r_off);
+  const int* err = reinterpret_cast<const int*>(ws + L.err_off);
   WMD_CUDA_TRY(launch_loop_conv(c, cls, ws + L.k_off, VR, r, r + VR, v_r, max_iter, tol, prec,
-                                d_out, d_iters, static_cast<cudaStream_t>(stream)));
+                                d_out, d_iters, err, static_cast<cudaStream_t>(stream)));
   return WMD_OK;
 }
 
@@ -505,6 +621,12 @@ wmd_status wmd_set_loop_variant(wmd_corpus* c, int32_t v_r, wmd_precision prec, 
     return set_error(WMD_ERR_INVALID_ARG, "no such variant for this query width");
   c->loop_variant[cls][prec == WMD_PREC_BF16_K] = variant;
   return WMD_OK;
+}
+
+int32_t wmd_get_loop_variant(const wmd_corpus* c, int32_t v_r, wmd_precision prec) {
+  const int cls = v_r > 0 ? vr_class(v_r) : -1;
+  if (!c || cls < 0 || (prec != WMD_PREC_FP32 && prec != WMD_PREC_BF16_K)) return -1;
+  return c->loop_variant[cls][prec == WMD_PREC_BF16_K];
 }
 
 wmd_status wmd_autotune(wmd_corpus* c, const int32_t* q_ids, const float* q_w, int32_t n_q,
@@ -560,6 +682,7 @@ wmd_status wmd_autotune(wmd_corpus* c, const int32_t* q_ids, const float* q_w, i
       }
     }
     c->loop_variant[cls][prec == WMD_PREC_BF16_K] = (st == WMD_OK && e == cudaSuccess) ? best : keep;
+    if (st == WMD_OK && e == cudaSuccess) save_autotune_choice(c, cls, prec == WMD_PREC_BF16_K, best);
   }
   if (s) cudaStreamSynchronize(s);
   if (e0) cudaEventDestroy(e0);
@@ -688,7 +811,13 @@ wmd_status wmd_query(wmd_corpus* c, const int32_t* q_ids, const float* q_w, int3
     qg = &c->qgraphs.back();
   }
   qg->last = ++c->qtick;
-  if (qg->exec) {
+  if (!c->use_graphs) {
+    st = enqueue();
+    if (st != WMD_OK) {
+      cudaStreamSynchronize(c->stream);
+      return st;
+    }
+  } else if (qg->exec) {
     WMD_CUDA_TRY(cudaGraphLaunch(qg->exec, c->stream));
   } else if (qg->uses >= 1) {
     cudaGraph_t graph = nullptr;
@@ -718,18 +847,7 @@ wmd_status wmd_query(wmd_corpus* c, const int32_t* q_ids, const float* q_w, int3
   WMD_CUDA_TRY(cudaStreamSynchronize(c->stream));
   if (c->N > 0 && !direct) std::memcpy(out_wmd, c->h_out, c->N * sizeof(double));
   const int err = *reinterpret_cast<volatile int32_t*>(h_err);
-  if (err) {
-    static const char* roles[] = {"?", "producer (stage free)", "?",
-                                  "MMA (accumulator free)", "MMA (tile landed)",
-                                  "epilogue (accumulator full)", "?",
-                                  "producer (query gathers in flight)"};
-    const int role = (err >> 24) & 0x3f;
-    char msg[160];
-    std::snprintf(msg, sizeof msg,
-                  "a device-side wait in the cdist kernel timed out: %s, iteration %d (code 0x%08x)",
-                  roles[role < 8 ? role : 0], err & 0xffffff, (unsigned)err);
-    return set_error(WMD_ERR_TIMEOUT, msg);
-  }
+  if (err) return device_error(err);
   return WMD_OK;
 }
 

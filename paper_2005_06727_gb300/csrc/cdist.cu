@@ -32,10 +32,10 @@ constexpr int kAStride = kTileW + 4;
 
 template <int VRB, typename KT>
 __global__ void __launch_bounds__(256) cdist_kernel(
-    const float* __restrict__ vecs, int ldv, const float* __restrict__ norms, int64_t U,
+    const float* __restrict__ vecs, int ldv, int d, const float* __restrict__ norms, int64_t U,
     const int32_t* __restrict__ perm, int64_t V, const int32_t* __restrict__ q_ids,
     const float* __restrict__ q_w, int v_r, int VR, float lambda, KT* __restrict__ K, int ldk,
-    int kcol0, float* __restrict__ r_out, float* __restrict__ lam_out) {
+    int kcol0, float* __restrict__ r_out, float* __restrict__ lam_out, int* __restrict__ err) {
   constexpr int TC = VRB / 8;
   constexpr int BStride = VRB + 4;
   __shared__ __align__(16) float As[kSlab][kAStride];
@@ -168,8 +168,10 @@ __global__ void __launch_bounds__(256) cdist_kernel(
     }
   }
 
-  // epilogue: M^2 = |a|^2 + |b|^2 - 2 a.b, clamp, sqrt, exact zero on the
-  // query's own word, K = exp(-lambda M)
+  // epilogue: M^2 = |a|^2 + |b|^2 - 2 a.b (by direct differences for near
+  // pairs, where that form has cancelled more than two bits), clamp, sqrt,
+  // exact zero on the query's own word, K = exp(-lambda M)
+  bool out_of_range = false;
   float qnv[TC];
   int qrw[TC];
 #pragma unroll
@@ -193,8 +195,12 @@ __global__ void __launch_bounds__(256) cdist_kernel(
         } else if (qrw[q] == -2) {
           kv = __int_as_float(0x7fc00000);  // id outside [0, V): NaN column
         } else {
-          const float m2 = (nw + qnv[q]) - 2.f * acc[a][q];
-          kv = expf(-lambda * sqrtf(fmaxf(m2, 0.f)));
+          const float nsum = nw + qnv[q];
+          float m2 = nsum - 2.f * acc[a][q];
+          if (m2 < kNearPair * nsum && qrw[q] >= 0) m2 = direct_m2(vecs, ldv, d, w, qrw[q]);
+          const float lm = lambda * sqrtf(fmaxf(m2, 0.f));
+          out_of_range |= qrw[q] >= 0 && lm > kRangeLimit;
+          kv = expf(-lm);
         }
       } else {
         kv = 0.f;
@@ -205,29 +211,31 @@ __global__ void __launch_bounds__(256) cdist_kernel(
 #pragma unroll
     for (int q = 0; q < TC; ++q) K[o + q] = outk[q];
   }
+  if (out_of_range) atomicOr(err + 1, kRangeFlag);
 }
 
 template <int VRB, typename KT>
 cudaError_t launch_cdist_t(const wmd_corpus* c, const int32_t* q_ids, const float* q_w, int v_r,
                            int VR, float lambda, KT* K, int ldk, int kcol0, float* r_out, float* lam_out,
-                           cudaStream_t s) {
+                           int* err, cudaStream_t s) {
   // at least one CTA row so that r_out is written even without active words
   const int64_t tiles = std::max<int64_t>((c->U + kTileW - 1) / kTileW, 1);
   dim3 grid((unsigned)tiles, (unsigned)(VR / VRB));
-  cdist_kernel<VRB, KT><<<grid, 256, 0, s>>>(c->vecs, c->ldv, c->norms, c->U, c->perm, c->V,
-                                            q_ids, q_w, v_r, VR, lambda, K, ldk, kcol0, r_out, lam_out);
+  cdist_kernel<VRB, KT><<<grid, 256, 0, s>>>(c->vecs, c->ldv, c->d, c->norms, c->U, c->perm, c->V,
+                                            q_ids, q_w, v_r, VR, lambda, K, ldk, kcol0, r_out, lam_out,
+                                            err);
   return cudaGetLastError();
 }
 
 template <typename KT>
 cudaError_t dispatch_cdist(const wmd_corpus* c, const int32_t* q_ids, const float* q_w, int v_r,
                            int VR, float lambda, KT* K, int ldk, int kcol0, float* r_out, float* lam_out,
-                           cudaStream_t s) {
+                           int* err, cudaStream_t s) {
   switch (VR) {
-    case 8: return launch_cdist_t<8, KT>(c, q_ids, q_w, v_r, VR, lambda, K, ldk, kcol0, r_out, lam_out, s);
-    case 16: return launch_cdist_t<16, KT>(c, q_ids, q_w, v_r, VR, lambda, K, ldk, kcol0, r_out, lam_out, s);
-    case 32: return launch_cdist_t<32, KT>(c, q_ids, q_w, v_r, VR, lambda, K, ldk, kcol0, r_out, lam_out, s);
-    default: return launch_cdist_t<64, KT>(c, q_ids, q_w, v_r, VR, lambda, K, ldk, kcol0, r_out, lam_out, s);
+    case 8: return launch_cdist_t<8, KT>(c, q_ids, q_w, v_r, VR, lambda, K, ldk, kcol0, r_out, lam_out, err, s);
+    case 16: return launch_cdist_t<16, KT>(c, q_ids, q_w, v_r, VR, lambda, K, ldk, kcol0, r_out, lam_out, err, s);
+    case 32: return launch_cdist_t<32, KT>(c, q_ids, q_w, v_r, VR, lambda, K, ldk, kcol0, r_out, lam_out, err, s);
+    default: return launch_cdist_t<64, KT>(c, q_ids, q_w, v_r, VR, lambda, K, ldk, kcol0, r_out, lam_out, err, s);
   }
 }
 
@@ -235,7 +243,8 @@ cudaError_t dispatch_cdist(const wmd_corpus* c, const int32_t* q_ids, const floa
 
 cudaError_t launch_cdist(const wmd_corpus* c, const int32_t* q_ids, const float* q_w, int v_r,
                          int VR, float lambda, wmd_precision prec, void* K, int ldk, int kcol0,
-                         float* r_out, float* lam_out, const L2Prefetch* pf, cudaStream_t s) {
+                         float* r_out, float* lam_out, int* err, const L2Prefetch* pf,
+                         cudaStream_t s) {
   // tensor cores (cdist_tc.cu): the query's columns in slices as wide as the
   // resident query operand allows (128 at most); every slice streams the
   // active vocabulary once
@@ -243,7 +252,7 @@ cudaError_t launch_cdist(const wmd_corpus* c, const int32_t* q_ids, const float*
   const int width = cdist_tc_max_width(c);
   if (width >= VR || (width > 0 && VR <= 16)) {
     e = launch_cdist_tc(c, q_ids, q_w, v_r, VR, lambda, prec, K, ldk, kcol0, r_out, lam_out,
-                        c->d_err, pf, s);
+                        err, pf, s);
   } else if (width > 0) {
     const size_t esz = prec == WMD_PREC_BF16_K ? 2 : 4;
     for (int j0 = 0; j0 < VR; j0 += width) {
@@ -251,7 +260,7 @@ cudaError_t launch_cdist(const wmd_corpus* c, const int32_t* q_ids, const float*
       // a slice past the last query word still writes its zero padding
       e = launch_cdist_tc(c, q_ids + std::min(j0, v_r), q_w + std::min(j0, v_r), vr_slice, width,
                           lambda, prec, static_cast<char*>(K) + (size_t)j0 * esz, ldk, kcol0,
-                          r_out ? r_out + j0 : nullptr, j0 == 0 ? lam_out : nullptr, c->d_err,
+                          r_out ? r_out + j0 : nullptr, j0 == 0 ? lam_out : nullptr, err,
                           j0 == 0 ? pf : nullptr, s);
       if (e != cudaSuccess) break;
     }
@@ -260,9 +269,9 @@ cudaError_t launch_cdist(const wmd_corpus* c, const int32_t* q_ids, const float*
   if (prec == WMD_PREC_BF16_K)
     return dispatch_cdist<__nv_bfloat16>(c, q_ids, q_w, v_r, VR, lambda,
                                          static_cast<__nv_bfloat16*>(K), ldk, kcol0, r_out,
-                                         lam_out, s);
+                                         lam_out, err, s);
   return dispatch_cdist<float>(c, q_ids, q_w, v_r, VR, lambda, static_cast<float*>(K), ldk,
-                               kcol0, r_out, lam_out, s);
+                               kcol0, r_out, lam_out, err, s);
 }
 
 }  // namespace wmd

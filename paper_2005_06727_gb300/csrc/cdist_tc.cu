@@ -50,7 +50,7 @@ constexpr int kStageBytes = 2 * kHalfBytes;
 constexpr int kThreads = 320;             // 10 warps
 constexpr int kBuildThreads = 288;        // warps 0..7 and 9 gather the query operand
 constexpr int kPrime = 2;                 // stages issued before the query gathers
-constexpr long long kWaitCycles = 4000000000ll;  // ~2 s at 2 GHz
+constexpr long long kWaitCycles = 4000000000ll;  // ~2 s at 2 GHz (drains; default role limit)
 constexpr float kLoScale = 1.f / 2048.f;  // 2^-11
 
 struct Params {
@@ -59,6 +59,8 @@ struct Params {
   const float* rscale;  // 2^-e per row
   int ldv;
   const float* norms;
+  const float* vecs;    // the float32 rows (near pairs are recomputed from them)
+  int d;
   int64_t U;
   const int32_t* perm;
   int64_t V;
@@ -75,7 +77,8 @@ struct Params {
   int num_tiles;
   int KB;
   int S;  // stages of the A ring
-  int* err;
+  int* err;              // the query's error words: [0] timeout, [1] range
+  long long wait_cycles; // limit of every wait between roles (drains keep kWaitCycles)
   // read-only data the next kernel (the fused loop) starts from: prefetched
   // into L2 with the evict-last priority while the vocabulary streams
   const void* pf_ptr[3];
@@ -130,16 +133,36 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
   return ok != 0;
 }
 
+// Non-blocking probe of the same phase (mbarrier.test_wait never suspends).
+__device__ __forceinline__ bool mbar_test_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n"
+      " .reg .pred p;\n"
+      " mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n"
+      "}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Limits below this many cycles poll with test_wait: try_wait may suspend the
+// thread for longer than such a limit, which would then never run out.
+constexpr long long kPollBelow = 1000000;
+
 // Bounded wait: false if the phase did not complete in time or another role
 // of the CTA gave up (the shared abort flag).  The first wait that runs out
 // records which role and iteration gave up in the abort flag:
 // 0x40000000 | role << 24 | (iteration & 0xffffff).
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag,
-                                         int role, int iter) {
+                                         int role, int iter, long long limit) {
   const long long t0 = clock64();
-  while (!mbar_try_wait(bar, parity)) {
+  const bool poll = limit < kPollBelow;
+  while (!(poll ? mbar_test_wait(bar, parity) : mbar_try_wait(bar, parity))) {
     if (*abort_flag) return false;
-    if (clock64() - t0 > kWaitCycles) {
+    if (clock64() - t0 > limit) {
       atomicCAS(const_cast<int*>(abort_flag), 0, 0x40000000 | (role << 24) | (iter & 0xffffff));
       return false;
     }
@@ -453,7 +476,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                 ok = false;
                 break;
               }
-              if (clock64() - t0 > kWaitCycles) {
+              if (clock64() - t0 > p.wait_cycles) {
                 atomicCAS(const_cast<int*>(abort_flag), 0, 0x40000000 | (7 << 24));
                 ok = false;
                 break;
@@ -463,7 +486,7 @@ __global__ void __launch_bounds__(kThreads, 1)
           }
           const int s = it % S;
           const uint32_t ph = (uint32_t)(it / S) & 1u;
-          if (!mbar_wait(&empty[s], ph ^ 1u, abort_flag, 1, it)) {
+          if (!mbar_wait(&empty[s], ph ^ 1u, abort_flag, 1, it, p.wait_cycles)) {
             ok = false;
             break;
           }
@@ -490,7 +513,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       for (int lt = 0; lt < nlt && ok; ++lt) {
         const int ab = lt & 1;
         const uint32_t tph = (uint32_t)(lt >> 1) & 1u;
-        if (!mbar_wait(&tempty[ab], tph ^ 1u, abort_flag, 3, lt)) break;
+        if (!mbar_wait(&tempty[ab], tph ^ 1u, abort_flag, 3, lt, p.wait_cycles)) break;
         tc_fence_after();
         // columns [0, N): a_hi . b_hi; [N, 2N): a_hi . b_lo + a_lo . b_hi (scaled 2^11)
         const uint32_t d_tmem = tmem_base + (uint32_t)(ab * 2 * N);
@@ -500,7 +523,7 @@ __global__ void __launch_bounds__(kThreads, 1)
           const uint32_t a_hi = smem_u32(Abuf + s * kStageBytes);
           const uint32_t a_lo = a_hi + kHalfBytes;
           const uint32_t b_cat = smem_u32(Bcat + kb * bblock);  // rows 0..N-1 are b_hi
-          if (!mbar_wait(&full[s], ph, abort_flag, 4, it)) {
+          if (!mbar_wait(&full[s], ph, abort_flag, 4, it, p.wait_cycles)) {
             ok = false;
             break;
           }
@@ -542,6 +565,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     const int c0 = (warp >> 2) * kHalfN;
     const int row_in_tile = q * 32 + lane;
     const int ncols = min(N, p.VR);             // columns this launch owns in K
+    bool out_of_range = false;                  // some lambda m reached the float32 limit of K
     for (int lt = 0; lt < nlt; ++lt) {
       const int ab = lt & 1;
       const uint32_t tph = (uint32_t)(lt >> 1) & 1u;
@@ -549,7 +573,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       const bool live = w < p.U;
       const float nw = live ? p.norms[w] : 0.f;  // issued before the wait
       const float rsw = live ? p.rscale[w] : 0.f;
-      if (!mbar_wait(&tfull[ab], tph, abort_flag, 5, lt)) break;
+      if (!mbar_wait(&tfull[ab], tph, abort_flag, 5, lt, p.wait_cycles)) break;
       if (tid == 0) TC_TRACE(3, lt);
       tc_fence_after();
       const uint32_t taddr = tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(ab * 2 * N);
@@ -566,21 +590,31 @@ __global__ void __launch_bounds__(kThreads, 1)
         if (live && c < ncols) {
           // a.b = 2^-(e_w + e_q) (big + 2^-11 small); m^2 = |a|^2 + |b|^2 - 2 a.b
           // (clamped), K = exp(-lambda m); the query's own word is exactly
-          // m = 0 (K = 1); padding columns are 0 and an id outside [0, V) gives NaN
+          // m = 0 (K = 1); padding columns are 0 and an id outside [0, V) gives
+          // NaN.  Where the GEMM form has cancelled more than two bits (m^2
+          // below a quarter of |a|^2 + |b|^2: a near pair, Sec. 5), m^2 is
+          // recomputed from the float32 rows by direct differences (Sec. 2).
           float kv[CH];
 #pragma unroll
           for (int j = 0; j < CH; ++j) {
             const int col = c + j;
             const float dot = (fmaf(small[j], kLoScale, big[j]) * rsw) * qrs_s[col];
-            const float e = expf(-p.lambda * sqrtf(fmaxf((nw + qn_s[col]) - 2.f * dot, 0.f)));
             const int qr = qrow_s[col];
+            const float nsum = nw + qn_s[col];
+            float m2 = nsum - 2.f * dot;
+            if (m2 < kNearPair * nsum && qr >= 0 && qr != (int)w && col < p.v_r)
+              m2 = direct_m2(p.vecs, p.ldv, p.d, w, qr);
+            const float lm = p.lambda * sqrtf(fmaxf(m2, 0.f));
+            const float e = expf(-lm);
             const float k = qr == (int)w ? 1.f : (qr == -2 ? __int_as_float(0x7fc00000) : e);
+            out_of_range |= col < p.v_r && qr >= 0 && qr != (int)w && lm > kRangeLimit;
             kv[j] = col < p.v_r ? k : 0.f;
           }
           store_chunk<CH>(static_cast<KT*>(p.K) + (size_t)w * p.ldk + p.kcol0 + c, kv, ncols - c);
         }
       }
     }
+    if (out_of_range) atomicOr(p.err + 1, kRangeFlag);
   }
 
   if (warp == 0 && lane == 0) TC_TRACE(4, 0);
@@ -699,6 +733,8 @@ cudaError_t launch_cdist_tc(const wmd_corpus* c, const int32_t* q_ids, const flo
   p.rscale = c->rscale;
   p.ldv = c->ldv;
   p.norms = c->norms;
+  p.vecs = c->vecs;
+  p.d = c->d;
   p.U = c->U;
   p.perm = c->perm;
   p.V = c->V;
@@ -716,6 +752,7 @@ cudaError_t launch_cdist_tc(const wmd_corpus* c, const int32_t* q_ids, const flo
   p.KB = tc::num_kblocks(c);
   p.S = 0;
   p.err = err;
+  p.wait_cycles = c->wait_cycles > 0 ? c->wait_cycles : tc::kWaitCycles;
   for (int r = 0; r < 3; ++r) {
     p.pf_ptr[r] = pf ? pf->ptr[r] : nullptr;
     p.pf_bytes[r] = pf ? pf->bytes[r] : 0;

@@ -11,7 +11,10 @@
 // holds its kWmdScratchBytes until the process exits.  Host code may not use
 // the array's name as a device address (on the host it is only a stand-in
 // symbol), so the device address is looked up with cudaGetSymbolAddress once
-// per device, with that device current, on the first call for that device.
+// per device, with that device current.  The lookup happens in
+// wmd_corpus_load (noalloc_reserve), which allocates anyway: with lazy module
+// loading the driver reserves the array at that lookup, so it must not be the
+// no-allocation call that triggers it.
 #include <mutex>
 
 #include "wmd_internal.h"
@@ -30,6 +33,24 @@ void* g_scratch_ptr[kMaxDevices] = {};
 
 }  // namespace
 
+namespace wmd {
+
+cudaError_t noalloc_reserve(int device) {
+  if (device < 0 || device >= kMaxDevices) return cudaSuccess;  // the entry point refuses such devices
+  std::lock_guard<std::mutex> lock(g_scratch_mu);
+  if (g_scratch_ptr[device]) return cudaSuccess;
+  int prev = -1;
+  cudaGetDevice(&prev);
+  void* ptr = nullptr;
+  cudaError_t e = cudaSetDevice(device);
+  if (e == cudaSuccess) e = cudaGetSymbolAddress(&ptr, g_wmd_scratch);
+  if (prev >= 0 && prev != device) cudaSetDevice(prev);
+  if (e == cudaSuccess) g_scratch_ptr[device] = ptr;
+  return e;
+}
+
+}  // namespace wmd
+
 extern "C" wmd_status wmd_query_device_noalloc(wmd_corpus* corpus, const int32_t* d_q_ids,
                                                const float* d_q_w, int32_t v_r, float lambda,
                                                int32_t max_iter, wmd_precision prec,
@@ -46,22 +67,16 @@ extern "C" wmd_status wmd_query_device_noalloc(wmd_corpus* corpus, const int32_t
                               std::to_string(kWmdScratchBytes) +
                               " (use wmd_query_device with a larger workspace)");
 
+  // the address was recorded when the corpus was loaded on this device
   void* scratch = nullptr;
   {
     std::lock_guard<std::mutex> lock(g_scratch_mu);
     scratch = g_scratch_ptr[corpus->device];
-    if (!scratch) {
-      int prev = -1;
-      cudaGetDevice(&prev);
-      cudaError_t e = cudaSetDevice(corpus->device);
-      if (e == cudaSuccess) e = cudaGetSymbolAddress(&scratch, g_wmd_scratch);
-      if (prev >= 0 && prev != corpus->device) cudaSetDevice(prev);
-      if (e != cudaSuccess) return wmd::cuda_error(e, "cudaGetSymbolAddress(scratch)");
-      g_scratch_ptr[corpus->device] = scratch;
-    }
   }
-  // The kernels overwrite every byte of the scratch they read (r, lambda, K),
-  // so nothing has to be cleared between calls.
+  if (!scratch) return wmd::set_error(WMD_ERR_CUDA, "scratch array not reserved on this device");
+  // The kernels overwrite every byte of the scratch they read (r, lambda, K);
+  // the error words, which must start at zero, are cleared by a memset node at
+  // the start of every call (stream-ordered, no allocation).
   return wmd_query_device(corpus, d_q_ids, d_q_w, v_r, lambda, max_iter, prec, scratch,
                           kWmdScratchBytes, d_out, stream);
 }

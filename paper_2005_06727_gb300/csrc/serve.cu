@@ -83,6 +83,8 @@ struct Slot {
   float* h_w = nullptr;
   QueryDesc* h_desc = nullptr;
   double* h_out = nullptr;
+  int* h_err = nullptr;  // pinned copy of every query's error words (read after `done`)
+  size_t h_err_cap = 0;
   size_t h_ids_cap = 0, h_w_cap = 0, h_desc_cap = 0, h_out_cap = 0;
 
   void release() {
@@ -96,6 +98,7 @@ struct Slot {
     cudaFreeHost(h_w);
     cudaFreeHost(h_desc);
     cudaFreeHost(h_out);
+    cudaFreeHost(h_err);
     if (done) cudaEventDestroy(done);
     if (stream) cudaStreamDestroy(stream);
     *this = Slot();
@@ -129,7 +132,7 @@ struct Layout {
   std::vector<int> col0;
   int ldk = 0;
   size_t words = 0;
-  size_t r_off = 0, k_off = 0, ws_bytes = 0;
+  size_t r_off = 0, err_off = 0, k_off = 0, ws_bytes = 0;
   std::vector<int> desc_of;        // query -> index in the descriptor table
   int cls_begin[kNumClasses + 1];  // descriptor ranges per class
 };
@@ -145,7 +148,8 @@ Layout plan(const wmd_corpus* c, const std::vector<const Req*>& qs, wmd_precisio
   }
   L.ldk = std::max(col, 8);
   L.r_off = 0;
-  L.k_off = round_up((size_t)L.ldk * 4, 256);
+  L.err_off = (size_t)L.ldk * 4;  // every query's error words, after every query's r
+  L.k_off = round_up(L.err_off + qs.size() * kErrWords * sizeof(int), 256);
   const size_t kb = round_up((size_t)std::max<int64_t>(c->U, 1) * L.ldk * k_elem(prec), 256);
   L.ws_bytes = L.k_off + kb;
   // descriptors grouped by width class
@@ -177,6 +181,7 @@ wmd_status enqueue_batch(wmd_corpus* c, Slot& s, const std::vector<const Req*>& 
   WMD_CUDA_TRY(grow_host(&s.h_w, &s.h_w_cap, L.words));
   WMD_CUDA_TRY(grow_host(&s.h_desc, &s.h_desc_cap, nq));
   WMD_CUDA_TRY(grow_host(&s.h_out, &s.h_out_cap, nq * N1));
+  WMD_CUDA_TRY(grow_host(&s.h_err, &s.h_err_cap, nq * kErrWords));
 
   // staging: compacted words of every query, and the descriptor table
   size_t off = 0;
@@ -189,8 +194,10 @@ wmd_status enqueue_batch(wmd_corpus* c, Slot& s, const std::vector<const Req*>& 
   }
   char* ws = s.d_ws;
   float* r_all = reinterpret_cast<float*>(ws + L.r_off);
+  int* err = reinterpret_cast<int*>(ws + L.err_off);  // [nq][kErrWords]
   for (size_t q = 0; q < nq; ++q) {
     QueryDesc& d = s.h_desc[L.desc_of[q]];
+    d.err = err + q * kErrWords;
     d.r = r_all + L.col0[q];
     d.out = s.d_out + q * N1;
     d.kcol0 = L.col0[q];
@@ -202,12 +209,15 @@ wmd_status enqueue_batch(wmd_corpus* c, Slot& s, const std::vector<const Req*>& 
   WMD_CUDA_TRY(cudaMemcpyAsync(s.d_ids, s.h_ids, L.words * sizeof(int32_t), cudaMemcpyHostToDevice, st));
   WMD_CUDA_TRY(cudaMemcpyAsync(s.d_w, s.h_w, L.words * sizeof(float), cudaMemcpyHostToDevice, st));
   WMD_CUDA_TRY(cudaMemcpyAsync(s.d_desc, s.h_desc, nq * sizeof(QueryDesc), cudaMemcpyHostToDevice, st));
+  // every query's error words start clear: a failure fails that query only
+  WMD_CUDA_TRY(cudaMemsetAsync(err, 0, nq * kErrWords * sizeof(int), st));
   // the first cdist launch prefetches the loop's document CSR into L2
   const L2Prefetch pf = loop_inputs(c, vr_class(qs[0]->v_r), prec);
   for (size_t q = 0; q < nq; ++q)
     WMD_CUDA_TRY(launch_cdist(c, s.d_ids + word_off[q], s.d_w + word_off[q], qs[q]->v_r, qs[q]->VR,
                               qs[q]->lambda, prec, ws + L.k_off, L.ldk, L.col0[q],
-                              r_all + L.col0[q], nullptr, q == 0 ? &pf : nullptr, st));
+                              r_all + L.col0[q], nullptr, err + q * kErrWords,
+                              q == 0 ? &pf : nullptr, st));
   for (int cls = 0; cls < kNumClasses; ++cls) {
     const int n = L.cls_begin[cls + 1] - L.cls_begin[cls];
     if (n)
@@ -216,6 +226,7 @@ wmd_status enqueue_batch(wmd_corpus* c, Slot& s, const std::vector<const Req*>& 
   }
   if (c->N > 0)
     WMD_CUDA_TRY(cudaMemcpyAsync(s.h_out, s.d_out, nq * N1 * sizeof(double), cudaMemcpyDeviceToHost, st));
+  WMD_CUDA_TRY(cudaMemcpyAsync(s.h_err, err, nq * kErrWords * sizeof(int), cudaMemcpyDeviceToHost, st));
   return WMD_OK;
 }
 
@@ -340,21 +351,19 @@ void wmd_server::retire_finished(std::unique_lock<std::mutex>& lock, bool block)
       ++i;
       continue;
     }
-    int err = 0;
-    if (e == cudaSuccess) {
-      DevGuard g(corpus->device);
-      cudaMemcpy(&err, corpus->d_err, sizeof(int), cudaMemcpyDeviceToHost);
-    }
     const size_t N1 = (size_t)std::max<int64_t>(corpus->N, 1);
     auto& reqs = inflight[i].reqs;
     for (size_t q = 0; q < reqs.size(); ++q) {
       Request& r = *reqs[q];
+      // the request's own error words (copied back with the results)
+      const int* ew = s.h_err + q * kErrWords;
+      const int err = e == cudaSuccess ? (ew[0] ? ew[0] : ew[1]) : 0;
       if (e != cudaSuccess) {
         r.status = WMD_ERR_CUDA;
         r.error = std::string("batch failed: ") + cudaGetErrorString(e);
       } else if (err) {
-        r.status = WMD_ERR_TIMEOUT;
-        r.error = "a device-side wait in the cdist kernel timed out";
+        r.status = device_error(err);
+        r.error = wmd_last_error();
       } else {
         r.result.assign(s.h_out + q * N1, s.h_out + q * N1 + corpus->N);
         r.status = WMD_OK;
@@ -493,7 +502,10 @@ wmd_status wmd_query_batch(wmd_corpus* c, int32_t nq, const int64_t* q_ptr, cons
     if (g2.shape == shape && g2.lambdas == lams && g2.T == max_iter && g2.prec == (int)prec) ge = &g2;
   // buffers must not move under a captured graph: size them before capture
   const bool fresh = !ge;
-  if (fresh) {
+  if (!c->use_graphs) {
+    wmd_status st = enqueue_batch(c, s, qs, L, max_iter, prec);
+    if (st != WMD_OK) return st;
+  } else if (fresh) {
     // run once eagerly (allocates and sizes every buffer), then capture
     wmd_status st = enqueue_batch(c, s, qs, L, max_iter, prec);
     if (st != WMD_OK) return st;
@@ -533,11 +545,16 @@ wmd_status wmd_query_batch(wmd_corpus* c, int32_t nq, const int64_t* q_ptr, cons
     }
     WMD_CUDA_TRY(cudaGraphLaunch(ge->exec, s.stream));
   }
-  ge->last_use = ++B->tick;
+  if (ge) ge->last_use = ++B->tick;
   WMD_CUDA_TRY(cudaStreamSynchronize(s.stream));
-  int err = 0;
-  WMD_CUDA_TRY(cudaMemcpy(&err, c->d_err, sizeof(int), cudaMemcpyDeviceToHost));
-  if (err) return set_error(WMD_ERR_TIMEOUT, "a device-side wait in the cdist kernel timed out");
+  for (int q = 0; q < nq; ++q) {
+    const int* ew = s.h_err + (size_t)q * kErrWords;
+    if (ew[0] | ew[1]) {
+      device_error(ew[0] ? ew[0] : ew[1]);
+      return set_error(ew[0] ? WMD_ERR_TIMEOUT : WMD_ERR_RANGE,
+                       "query " + std::to_string(q) + " of the batch: " + wmd_last_error());
+    }
+  }
   const size_t N1 = (size_t)std::max<int64_t>(c->N, 1);
   for (int q = 0; q < nq; ++q)
     if (c->N > 0) std::memcpy(out + (size_t)q * c->N, s.h_out + q * N1, c->N * sizeof(double));
@@ -547,11 +564,7 @@ wmd_status wmd_query_batch(wmd_corpus* c, int32_t nq, const int64_t* q_ptr, cons
 wmd_status wmd_server_create(wmd_corpus* c, const wmd_server_options* opt, wmd_server** out) {
   if (!c || !out) return set_error(WMD_ERR_INVALID_ARG, "NULL pointer");
   *out = nullptr;
-  wmd_server_options o;
-  o.max_batch = 64;
-  o.slots = 2;
-  o.mem_budget = size_t(8) << 30;
-  o.max_pending = 65536;
+  wmd_server_options o = c->server_defaults;
   if (opt) o = *opt;
   if (o.max_batch <= 0 || o.slots <= 0 || o.slots > 16 || o.mem_budget == 0 || o.max_pending <= 0)
     return set_error(WMD_ERR_INVALID_ARG, "server options out of range");

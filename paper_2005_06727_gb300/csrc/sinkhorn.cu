@@ -46,9 +46,9 @@ L2Prefetch loop_inputs(const wmd_corpus* c, int cls, wmd_precision prec) {
 
 cudaError_t launch_loop(const wmd_corpus* c, int cls, const void* K, int ldk, int kcol0,
                         const float* r, const float* lam, int v_r, int T, wmd_precision prec,
-                        double* out, int* err_out, cudaStream_t s) {
+                        double* out, const int* err, int* err_out, cudaStream_t s) {
   const int var = c->loop_variant[cls][prec == WMD_PREC_BF16_K];
-  LoopParams p = base_params(c, cls, var, K, ldk, T);
+  LoopParams p = base_params(c, cls, var, K, ldk, T, err);
   p.kcol0 = kcol0;
   p.r = r;
   p.lam = lam;
@@ -64,7 +64,7 @@ cudaError_t launch_loop_batch(const wmd_corpus* c, int cls, const void* K, int l
                               const QueryDesc* d_queries, int nq, int T, wmd_precision prec,
                               cudaStream_t s) {
   const int var = c->loop_variant[cls][prec == WMD_PREC_BF16_K];
-  LoopParams p = base_params(c, cls, var, K, ldk, T);
+  LoopParams p = base_params(c, cls, var, K, ldk, T, nullptr);  // errors: per query descriptor
   p.queries = d_queries;
   const int n_items = c->sched[cls][var].n_items;
   if (prec == WMD_PREC_BF16_K) return dispatch_loop<false, __nv_bfloat16>(cls, var, p, n_items, nq, s);

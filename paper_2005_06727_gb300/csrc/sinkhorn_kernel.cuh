@@ -46,7 +46,7 @@
 // The kernel is launched as a programmatic dependent of the cdist kernel: a
 // warp reads its task record and its rows' word ids and weights (corpus data,
 // which cdist prefetched into L2) and only then waits for cdist's K, r,
-// lambda and timeout word.
+// lambda and error words.
 //
 // K .* M for the final step is recovered from the K block already in
 // registers: M = -ln(K) / lambda = -log2(K) ln 2 / lambda, exact for K = 1
@@ -76,8 +76,10 @@ struct LoopParams {
   int T;
   const WarpTask* tasks;  // [item][warp]
   double* out;
-  const int* err;  // set by a cdist kernel that gave up waiting: results are NaN
-  int* err_out;    // optional copy of *err for the host (block 0 writes it)
+  const int* err;  // the query's error words (a cdist wait ran out, or K left the
+                   // float32 range): when either is set, every result is NaN
+                   // (batched launches: each query's own, in its descriptor)
+  int* err_out;    // optional summary of err for the host (block 0 writes it)
   const QueryDesc* queries;  // blockIdx.y selects the query; NULL: the fields above
   // convergence-tested instances (CONV) only, single query: a document stops
   // once x changes by at most tol relative to its previous value, and
@@ -113,7 +115,7 @@ __device__ __forceinline__ void load_krow(const KT* __restrict__ Kb, int64_t row
 
 // Programmatic dependent launch: the kernel may start while the cdist
 // kernel before it in the stream still runs; from this wait on, everything
-// that kernel wrote (K, r, lambda, the timeout word) is visible.  A no-op when
+// that kernel wrote (K, r, lambda, the error words) is visible.  A no-op when
 // the launch has no programmatic predecessor.
 __device__ __forceinline__ void wait_for_producer() {
   asm volatile("griddepcontrol.wait;" ::: "memory");
@@ -282,7 +284,8 @@ __device__ __forceinline__ void solve(const LoopParams& p, const TeamCtx& t) {
     }
   }
   wait_for_producer();
-  if (*p.err) {  // the cdist kernel gave up waiting: no result (whole teams leave together)
+  if (t.q.err[0] | t.q.err[1]) {  // cdist gave up waiting, or K left the float32 range:
+                              // no result (whole teams leave together)
     if (t.kw == 0 && t.lane == 0) {
       t.q.out[t.doc] = __longlong_as_double(0x7ff8000000000000ll);
       if (CONV && p.iters) p.iters[t.doc] = p.T;
@@ -579,7 +582,7 @@ __global__ void __launch_bounds__(NW * 32, MINB) sinkhorn_fused_kernel(LoopParam
   t.pw = t.lane / PI;
   if (p.err_out && blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) {
     wait_for_producer();
-    *p.err_out = *p.err;
+    *p.err_out = p.err[0] ? p.err[0] : p.err[1];
   }
   const WarpTask task = p.tasks[blockIdx.x * NW + t.warp];
   t.W = task.n_w >> kTaskWShift;
@@ -596,11 +599,12 @@ __global__ void __launch_bounds__(NW * 32, MINB) sinkhorn_fused_kernel(LoopParam
     t.q.out = p.out;
     t.q.kcol0 = p.kcol0;
     t.q.v_r = p.v_r;
+    t.q.err = p.err;
   }
   if (t.n == 0) {
     wait_for_producer();  // the timeout word comes from the cdist kernel
     if (t.kw == 0 && t.lane == 0) {
-      t.q.out[t.doc] = *p.err || p.T >= 1 ? __longlong_as_double(0x7ff8000000000000ll) : 0.0;
+      t.q.out[t.doc] = (t.q.err[0] | t.q.err[1]) || p.T >= 1 ? __longlong_as_double(0x7ff8000000000000ll) : 0.0;
       // x of an empty document goes 1/v_r -> 0 -> 0/0: it never settles
       if (CONV && p.iters) p.iters[t.doc] = p.T;
     }
@@ -697,7 +701,7 @@ cudaError_t dispatch_loop(int cls, int var, const LoopParams& p, int n_items, in
 
 // Parameters shared by every launch of the loop for query class cls.
 inline LoopParams base_params(const wmd_corpus* c, int cls, int var, const void* K, int ldk,
-                              int T) {
+                              int T, const int* err) {
   LoopParams p;
   p.doc_ptr = c->doc_ptr;
   p.doc_words = c->doc_words;
@@ -711,7 +715,7 @@ inline LoopParams base_params(const wmd_corpus* c, int cls, int var, const void*
   p.T = T;
   p.tasks = c->sched[cls][var].d_tasks;
   p.out = nullptr;
-  p.err = c->d_err;
+  p.err = err;
   p.err_out = nullptr;
   p.queries = nullptr;
   p.tol = 0.f;

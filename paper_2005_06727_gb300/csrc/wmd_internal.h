@@ -94,8 +94,12 @@ struct wmd_corpus {
   int loop_variant[wmd::kNumClasses][2] = {};  // chosen variant per class and precision
   size_t device_bytes = 0;
   int num_sms = 0;
-  int* d_err = nullptr;        // device-side timeout flag (sticky); also read by wmd_query
   bool tmap_ok = false;        // tensor-core cdist available (TMA descriptors built)
+  // options (wmd_options)
+  bool use_graphs = true;
+  long long wait_cycles = 0;   // device-side wait limit of the tensor-core cdist (0: default)
+  std::string autotune_cache;  // file of tuned loop variants ("" = none)
+  wmd_server_options server_defaults{};
   alignas(64) unsigned char tmap_hi[128];  // CUtensorMap of vecs_hi (128-byte tiles of 128 rows)
   alignas(64) unsigned char tmap_lo[128];  // CUtensorMap of vecs_lo
 
@@ -125,10 +129,22 @@ namespace wmd {
 
 // Workspace carve-up for one query of class VR: the padded query weights r
 // (VR floats) followed by lambda (float VR), the final step's scale
-// -ln 2 / lambda (a double at float VR + 2), and the word-major K (U x VR).
+// -ln 2 / lambda (a double at float VR + 2), the query's two device-side error
+// words (ints at float VR + 4 and VR + 5, cleared before every query), and the
+// word-major K (U x VR).
 struct WsLayout {
-  size_t r_off, k_off, total;
+  size_t r_off, err_off, k_off, total;
 };
+// The two error words of a query or batch: [0] the first cdist wait that ran
+// out (0x40000000 | role << 24 | iteration), [1] kRangeFlag once some
+// lambda * M reached the float32 range limit of K.
+constexpr int kErrWords = 2;
+constexpr int kRangeFlag = 0x20000000;
+constexpr float kRangeLimit = 87.33654f;  // -ln(FLT_MIN): K = exp(-lambda M) below is subnormal
+// Clears the error words on `s` (a memset node; no allocation).
+inline cudaError_t clear_errors(int* err, cudaStream_t s) {
+  return cudaMemsetAsync(err, 0, kErrWords * sizeof(int), s);
+}
 WsLayout ws_layout(const wmd_corpus* c, int VR, wmd_precision prec);
 
 // Read-only regions (up to three) that the kernel after cdist starts from;
@@ -141,10 +157,11 @@ struct L2Prefetch {
 // document-major CSR.
 L2Prefetch loop_inputs(const wmd_corpus* c, int cls, wmd_precision prec);
 
-// Kernel launchers (cdist.cu / sinkhorn.cu).
+// Kernel launchers (cdist.cu / sinkhorn.cu).  err: the query's error words.
 cudaError_t launch_cdist(const wmd_corpus* c, const int32_t* q_ids, const float* q_w, int v_r,
                          int VR, float lambda, wmd_precision prec, void* K, int ldk, int kcol0,
-                         float* r_out, float* lam_out, const L2Prefetch* pf, cudaStream_t s);
+                         float* r_out, float* lam_out, int* err, const L2Prefetch* pf,
+                         cudaStream_t s);
 cudaError_t launch_cdist_tc(const wmd_corpus* c, const int32_t* q_ids, const float* q_w, int v_r,
                             int VR, float lambda, wmd_precision prec, void* K, int ldk, int kcol0,
                             float* r_out, float* lam_out, int* err, const L2Prefetch* pf,
@@ -154,22 +171,25 @@ bool make_vecs_tensor_map(wmd_corpus* c);
 int cdist_tc_max_width(const wmd_corpus* c);
 void release_batch_state(const wmd_corpus* c);  // serve.cu: cached batch buffers and graphs
 // One query of a batched loop launch: its padded weights r, output row, first
-// column of its block in the word-major K, and its number of words.
+// column of its block in the word-major K, its number of words and its error
+// words (so that one failed query of a batch fails no other).
 struct QueryDesc {
   const float* r;
   double* out;
   int kcol0;
   int v_r;
   float lambda;
-  double scale;  // -ln 2 / lambda, the final step's factor
+  double scale;    // -ln 2 / lambda, the final step's factor
+  const int* err;  // the query's own error words
 };
 cudaError_t launch_loop_batch(const wmd_corpus* c, int cls, const void* K, int ldk,
                               const QueryDesc* d_queries, int nq, int T, wmd_precision prec,
                               cudaStream_t s);
-// err_out (optional, device-visible): receives the cdist timeout word
+// err: the query's error words; err_out (optional, device-visible): receives
+// their summary (the timeout code if set, else the range flag, else 0)
 cudaError_t launch_loop(const wmd_corpus* c, int cls, const void* K, int ldk, int kcol0,
                         const float* r, const float* lam, int v_r, int T, wmd_precision prec,
-                        double* out, int* err_out, cudaStream_t s);
+                        double* out, const int* err, int* err_out, cudaStream_t s);
 // Top-k selection of WMD[N] (topk.cu): the k smallest values (ties: lower
 // document id first; NaN last) into out_idx / out_val, ascending.
 constexpr int kTopkMaxK = 1024;
@@ -180,6 +200,28 @@ cudaError_t launch_topk(const double* wmd, int64_t N, int k, int64_t* out_idx, d
 // (optional, device) receives the bodies run per document.
 cudaError_t launch_loop_conv(const wmd_corpus* c, int cls, const void* K, int ldk,
                              const float* r, const float* lam, int v_r, int T, float tol,
-                             wmd_precision prec, double* out, int32_t* iters, cudaStream_t s);
+                             wmd_precision prec, double* out, int32_t* iters, const int* err,
+                             cudaStream_t s);
+// Host-side message for a nonzero error word summary (timeout or range).
+wmd_status device_error(int code);
+// Looks up the no-allocation entry point's scratch array on `device` (once
+// per device; the lookup makes the driver reserve the array there).
+cudaError_t noalloc_reserve(int device);
+// The squared distance of two embedding rows by direct differences (Sec. 2),
+// used by the cdist kernels where the GEMM form |a|^2 + |b|^2 - 2 a.b has
+// cancelled more than two bits (near pairs, Sec. 5's concern).
+__device__ __forceinline__ float direct_m2(const float* __restrict__ vecs, int ldv, int d,
+                                           int64_t a, int64_t b) {
+  const float* pa = vecs + a * ldv;
+  const float* pb = vecs + b * ldv;
+  float acc = 0.f;
+  for (int k = 0; k < d; ++k) {
+    const float t = __ldg(pa + k) - __ldg(pb + k);
+    acc = fmaf(t, t, acc);
+  }
+  return acc;
+}
+// Below this fraction of |a|^2 + |b|^2 the GEMM form is replaced by direct_m2.
+constexpr float kNearPair = 0.25f;
 
 }  // namespace wmd

@@ -32,13 +32,17 @@ WMD_ERR_NOT_READY = 4
 WMD_ERR_TIMEOUT = 5
 WMD_ERR_SHUTDOWN = 6
 WMD_ERR_UNSUPPORTED = 7
+WMD_ERR_RANGE = 8
+
+CDIST_TENSOR_CORES = 0
+CDIST_CUDA_CORES = 1
 
 PREC_FP32 = 0
 PREC_BF16_K = 1
 MAX_VR = 256
 
 _STATUS = {0: "OK", 1: "INVALID_ARG", 2: "OUT_OF_MEMORY", 3: "CUDA", 4: "NOT_READY",
-           5: "TIMEOUT", 6: "SHUTDOWN", 7: "UNSUPPORTED"}
+           5: "TIMEOUT", 6: "SHUTDOWN", 7: "UNSUPPORTED", 8: "RANGE"}
 
 
 class WMDError(RuntimeError):
@@ -60,7 +64,14 @@ class ServerStats(C.Structure):
 
 class CorpusInfo(C.Structure):
     _fields_ = [("V", C.c_int64), ("d", C.c_int32), ("N", C.c_int64), ("nnz", C.c_int64),
-                ("U", C.c_int64), ("device", C.c_int32), ("device_bytes", C.c_size_t)]
+                ("U", C.c_int64), ("device", C.c_int32), ("device_bytes", C.c_size_t),
+                ("cdist_kernel", C.c_int32)]
+
+
+class Options(C.Structure):
+    _fields_ = [("device", C.c_int32), ("use_graphs", C.c_int32), ("cdist_kernel", C.c_int32),
+                ("autotune_cache", C.c_char_p), ("wait_limit_cycles", C.c_int64),
+                ("server", ServerOptions)]
 
 
 _lib = None
@@ -70,10 +81,12 @@ _SIGS = {
     "wmd_last_error": (C.c_char_p, []),
     "wmd_version": (C.c_char_p, []),
     "wmd_compact_query": (C.c_int, [_P, _P, C.c_int32, C.c_int64, _P, _P, _P]),
+    "wmd_options_default": (None, [_P]),
     "wmd_corpus_load": (C.c_int, [_P, C.c_int64, C.c_int32, _P, _P, _P, C.c_int64, C.c_int64,
-                                  C.c_int32, _P]),
+                                  _P, _P]),
     "wmd_corpus_free": (None, [_P]),
     "wmd_corpus_get_info": (C.c_int, [_P, _P]),
+    "wmd_corpus_set_wait_limit": (C.c_int, [_P, C.c_int64]),
     "wmd_query": (C.c_int, [_P, _P, _P, C.c_int32, C.c_float, C.c_int32, C.c_int, _P]),
     "wmd_workspace_bytes": (C.c_size_t, [_P, C.c_int32, C.c_int]),
     "wmd_build_kernel_matrix": (C.c_int, [_P, _P, _P, C.c_int32, C.c_float, C.c_int, _P,
@@ -95,6 +108,7 @@ _SIGS = {
     "wmd_query_batch": (C.c_int, [_P, C.c_int32, _P, _P, _P, _P, C.c_int32, C.c_int, _P]),
     "wmd_loop_variant_count": (C.c_int32, [C.c_int32]),
     "wmd_set_loop_variant": (C.c_int, [_P, C.c_int32, C.c_int, C.c_int32]),
+    "wmd_get_loop_variant": (C.c_int32, [_P, C.c_int32, C.c_int]),
     "wmd_autotune": (C.c_int, [_P, _P, _P, C.c_int32, C.c_float, C.c_int32, C.c_int, _P]),
     "wmd_server_create": (C.c_int, [_P, _P, _P]),
     "wmd_serve_submit": (C.c_int, [_P, _P, _P, C.c_int32, C.c_float, C.c_int32, C.c_int, _P]),
@@ -184,28 +198,49 @@ def _dptr(t):
     return C.c_void_p(t.data_ptr())
 
 
+def options(device: int = 0, use_graphs: bool = True, cdist_kernel: int = CDIST_TENSOR_CORES,
+            autotune_cache: str | None = None, wait_limit_cycles: int = 0, **server) -> Options:
+    """A ``wmd_options`` from ``wmd_options_default`` with the given fields
+    (``server`` keywords: max_batch, slots, mem_budget, max_pending)."""
+    o = Options()
+    lib().wmd_options_default(C.byref(o))
+    o.device = int(device)
+    o.use_graphs = 1 if use_graphs else 0
+    o.cdist_kernel = int(cdist_kernel)
+    o.autotune_cache = autotune_cache.encode() if autotune_cache else None
+    o.wait_limit_cycles = int(wait_limit_cycles)
+    for k, v in server.items():
+        if k not in {f for f, _ in ServerOptions._fields_}:
+            raise TypeError(f"unknown option {k}")
+        setattr(o.server, k, int(v))
+    return o
+
+
 class Corpus:
     """``wmd_corpus``: embeddings and the V x N CSR ``c`` resident on a GPU."""
 
-    def __init__(self, vecs, row_ptr, doc_idx, val, N: int, device: int = 0):
+    def __init__(self, vecs, row_ptr, doc_idx, val, N: int, device: int = 0, **opts):
         vecs = np.ascontiguousarray(vecs, dtype=np.float32)
         row_ptr = np.ascontiguousarray(row_ptr, dtype=np.int64)
         doc_idx = np.ascontiguousarray(doc_idx, dtype=np.int32)
         val = np.ascontiguousarray(val, dtype=np.float32)
         V, d = vecs.shape
+        o = options(device=device, **opts)
         h = C.c_void_p()
         _check(lib().wmd_corpus_load(_ptr(vecs), V, d, _ptr(row_ptr), _ptr(doc_idx), _ptr(val),
-                                     int(N), int(val.size), int(device), C.byref(h)))
+                                     int(N), int(val.size), C.byref(o), C.byref(h)))
         self._h = h
         info = CorpusInfo()
         _check(lib().wmd_corpus_get_info(self._h, C.byref(info)))
         self.V, self.d, self.N, self.nnz, self.U = info.V, info.d, info.N, info.nnz, info.U
         self.device = info.device
         self.device_bytes = info.device_bytes
+        self.cdist_kernel = "tensor cores (tcgen05)" if info.cdist_kernel == CDIST_TENSOR_CORES \
+            else "CUDA cores (float32 FMA)"
 
     @classmethod
-    def from_synth(cls, vecs, corpus, device: int = 0):
-        return cls(vecs, corpus.row_ptr, corpus.doc_idx, corpus.val, corpus.N, device)
+    def from_synth(cls, vecs, corpus, device: int = 0, **opts):
+        return cls(vecs, corpus.row_ptr, corpus.doc_idx, corpus.val, corpus.N, device, **opts)
 
     @property
     def handle(self):
@@ -236,9 +271,17 @@ class Corpus:
                                int(prec), _ptr(out)))
         return out
 
+    def set_wait_limit(self, cycles: int):
+        """``wmd_corpus_set_wait_limit`` (0 = the default, about 2 s)."""
+        _check(lib().wmd_corpus_set_wait_limit(self._h, int(cycles)))
+
     def set_loop_variant(self, v_r: int, variant: int, prec: int = PREC_FP32):
         """``wmd_set_loop_variant``."""
         _check(lib().wmd_set_loop_variant(self._h, int(v_r), int(prec), int(variant)))
+
+    def loop_variant(self, v_r: int, prec: int = PREC_FP32) -> int:
+        """``wmd_get_loop_variant``."""
+        return int(lib().wmd_get_loop_variant(self._h, int(v_r), int(prec)))
 
     def autotune(self, q_ids, q_w, lam: float, max_iter: int, prec: int = PREC_FP32) -> int:
         """``wmd_autotune``: returns the chosen fused-loop variant."""

@@ -121,3 +121,26 @@ def test_new_entry_points_validate_on_host(lib):
     assert lib.wmd_dense_load_c(None, fake, 1 << 20, None) == bad
     assert lib.wmd_dense_workspace_bytes(None, 5) == 0
     assert b"corpus" in lib.wmd_last_error()
+
+
+def test_options_defaults_and_host_validation(lib):
+    """wmd_options_default gives the documented defaults, and options out of
+    range are refused before anything touches a GPU."""
+    o = wmd.options()
+    assert (o.device, o.use_graphs, o.cdist_kernel, o.wait_limit_cycles) == (0, 1, 0, 0)
+    assert o.autotune_cache is None
+    assert (o.server.max_batch, o.server.slots, o.server.mem_budget, o.server.max_pending) == \
+        (64, 2, 8 << 30, 65536)
+    args = _corpus_args()
+    for kw, msg in [({"cdist_kernel": 5}, "cdist kernel"), ({"wait_limit_cycles": -1}, "wait"),
+                    ({"slots": 0}, "server options"), ({"slots": 17}, "server options"),
+                    ({"device": -1}, "device")]:
+        with pytest.raises(wmd.WMDError) as e:
+            wmd.Corpus(*args, **kw)
+        assert e.value.status == wmd.WMD_ERR_INVALID_ARG
+        assert msg in str(e.value)
+    with pytest.raises(TypeError):
+        wmd.options(no_such_option=1)
+    # a NULL corpus is refused by the setters and getters
+    assert lib.wmd_corpus_set_wait_limit(None, 5) == wmd.WMD_ERR_INVALID_ARG
+    assert lib.wmd_get_loop_variant(None, 30, 0) == -1
