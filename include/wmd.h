@@ -45,9 +45,11 @@
  *    query that leaves the range gets NaN for every document, and the host
  *    entry points (wmd_query, wmd_query_batch, the server) report
  *    WMD_ERR_RANGE.
- *  - Device-side errors are per query: every query (or batch) clears its
- *    own error words, kept in its workspace, before its first kernel, so a
- *    failed query never affects a later one or one running beside it.
+ *  - Device-side errors are per query: every CTA of a query's cdist kernel
+ *    writes its own error slot in the query's workspace at every launch
+ *    (nothing has to clear them), so a failed query never affects a later
+ *    one or one running beside it; a query of a batch that fails gets NaN
+ *    results and the batch call reports it.
  */
 #ifndef WMD_GB300_H
 #define WMD_GB300_H
@@ -192,6 +194,37 @@ wmd_status wmd_corpus_load(const float* vecs, int64_t V, int32_t d,
                            const int64_t* row_ptr, const int32_t* doc_idx,
                            const float* val, int64_t N, int64_t nnz,
                            const wmd_options* opt, wmd_corpus** out);
+
+/* ---------------------------------------------------------------------------
+ * Document sharding.  The paper parallelises the SDDMM_SpMM kernel by
+ * splitting the documents (the columns of c) into ranges of about equal
+ * nonzeros, one per thread and, across sockets, per socket (Sec. 3 and 4):
+ * every column of x, u and v depends only on its own column of c, so the
+ * ranges need no communication until the results are put together.  These
+ * calls make that split across corpora (one per GPU, or several on one GPU).
+ *
+ * wmd_shard_plan: host only.  c as in wmd_corpus_load (host); S >= 1 shards.
+ *   doc_begin[S + 1] (host) receives the boundaries: shard s holds documents
+ *   [doc_begin[s], doc_begin[s + 1]), contiguous, each with about nnz / S
+ *   nonzeros (a range may be empty when S is large).  WMD_ERR_INVALID_ARG
+ *   for a malformed input.
+ * wmd_corpus_load_shard: wmd_corpus_load of documents [doc_begin, doc_end)
+ *   only, renumbered from 0 (document doc_begin + j of c is document j of
+ *   the shard), with the whole vocabulary.  A shard's results equal the
+ *   corresponding slice of the unsharded corpus's bit for bit when both use
+ *   the same fused-loop tile variant (wmd_set_loop_variant).  Errors as
+ *   wmd_corpus_load, plus WMD_ERR_INVALID_ARG for a range outside [0, N].
+ * The k nearest documents of the whole corpus are the k nearest among the
+ * shards' own k nearest (ids shifted by doc_begin): wmd_topk over the
+ * shards' candidate values concatenated in shard order returns them, since
+ * that order is also ascending document order between equal values.
+ * ------------------------------------------------------------------------- */
+wmd_status wmd_shard_plan(const int64_t* row_ptr, const int32_t* doc_idx, int64_t V, int64_t N,
+                          int32_t S, int64_t* doc_begin);
+wmd_status wmd_corpus_load_shard(const float* vecs, int64_t V, int32_t d,
+                                 const int64_t* row_ptr, const int32_t* doc_idx,
+                                 const float* val, int64_t N, int64_t nnz, int64_t doc_begin,
+                                 int64_t doc_end, const wmd_options* opt, wmd_corpus** out);
 
 /* Frees a corpus (NULL is accepted).  The caller must not free a corpus that
  * a server or an in-flight device call still uses. */
@@ -460,9 +493,9 @@ void wmd_server_destroy(wmd_server* server);
  * with WMD_ERR_UNSUPPORTED.  wmd_corpus_load, which allocates anyway, looks
  * up the array's device address on the corpus's device, so the driver
  * reserves the array there at load time and this call itself never touches
- * the allocator; the call only reads that recorded address.  Every call
- * clears the array's error words before its first kernel.  All calls share
- * the one array and each call overwrites what it reads, so calls whose
+ * the allocator; the call only reads that recorded address.  All calls share
+ * the one array and each call overwrites what it reads (its error slots
+ * included: every cdist CTA rewrites its own), so calls whose
  * kernels overlap on the GPU (different streams, or different corpora on the
  * same device) race and must be serialised by the caller.  Allocates no
  * memory: no cudaMalloc, no cudaFree.

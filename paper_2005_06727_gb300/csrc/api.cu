@@ -157,9 +157,10 @@ wmd_status device_error(int err) {
 WsLayout ws_layout(const wmd_corpus* c, int VR, wmd_precision prec) {
   WsLayout L;
   size_t o = 0;
-  L.r_off = o;
-  L.err_off = o + (size_t)(VR + 4) * sizeof(float);
-  o = align_up(o + (size_t)(VR + 4 + kErrWords) * sizeof(float), 256);  // r, lambda, scale, errors
+  L.r_off = o;                                        // r, lambda, scale
+  L.err_off = o + (size_t)(VR + 4) * sizeof(float);   // error slots
+  L.n_err = cdist_err_slots(c, VR);
+  o = align_up(L.err_off + (size_t)L.n_err * sizeof(int), 256);
   const size_t kelem = prec == WMD_PREC_BF16_K ? 2 : 4;
   const size_t kbytes = align_up((size_t)std::max<int64_t>(c->U, 1) * VR * kelem, 256);
   L.k_off = o;
@@ -441,6 +442,68 @@ wmd_status wmd_corpus_load(const float* vecs, int64_t V, int32_t d, const int64_
   return WMD_OK;
 }
 
+wmd_status wmd_shard_plan(const int64_t* row_ptr, const int32_t* doc_idx, int64_t V, int64_t N,
+                          int32_t S, int64_t* doc_begin) {
+  if (!row_ptr || !doc_begin || V <= 0 || N < 0 || S <= 0)
+    return set_error(WMD_ERR_INVALID_ARG, "shard plan: bad arguments");
+  const int64_t nnz = row_ptr[V];
+  if (nnz < 0 || (nnz > 0 && !doc_idx)) return set_error(WMD_ERR_INVALID_ARG, "shard plan: bad CSR");
+  // nonzeros per document (the SDDMM/SpMM work of a document is its length
+  // times v_r, so equal nonzeros mean equal work, as in Sec. 3's split)
+  std::vector<int64_t> pre(N + 1, 0);
+  for (int64_t e = 0; e < nnz; ++e) {
+    const int64_t j = doc_idx[e];
+    if (j < 0 || j >= N) return set_error(WMD_ERR_INVALID_ARG, "shard plan: doc_idx outside [0, N)");
+    pre[j + 1]++;
+  }
+  for (int64_t j = 0; j < N; ++j) pre[j + 1] += pre[j];
+  // boundary s: the first document whose prefix reaches s nnz / S (rounded to
+  // the nearer side), never before the previous boundary
+  doc_begin[0] = 0;
+  for (int32_t sh = 1; sh < S; ++sh) {
+    const double target = (double)nnz * sh / S;
+    int64_t j = std::lower_bound(pre.begin(), pre.end(), (int64_t)std::ceil(target)) - pre.begin();
+    if (j > 0 && j <= N && target - pre[j - 1] < pre[j] - target) --j;
+    doc_begin[sh] = std::min<int64_t>(N, std::max<int64_t>(doc_begin[sh - 1], j));
+  }
+  doc_begin[S] = N;
+  return WMD_OK;
+}
+
+wmd_status wmd_corpus_load_shard(const float* vecs, int64_t V, int32_t d, const int64_t* row_ptr,
+                                 const int32_t* doc_idx, const float* val, int64_t N, int64_t nnz,
+                                 int64_t doc_begin, int64_t doc_end, const wmd_options* opt,
+                                 wmd_corpus** out) {
+  wmd::NvtxRange nvtx_range("wmd_corpus_load_shard");
+  if (!out) return set_error(WMD_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  if (V <= 0 || V > INT32_MAX || !row_ptr || nnz < 0 || (nnz > 0 && (!doc_idx || !val)))
+    return set_error(WMD_ERR_INVALID_ARG, "shard load: bad CSR arguments");
+  if (N < 0 || doc_begin < 0 || doc_end < doc_begin || doc_end > N)
+    return set_error(WMD_ERR_INVALID_ARG, "shard load: document range outside [0, N]");
+  if (row_ptr[0] != 0 || row_ptr[V] != nnz)
+    return set_error(WMD_ERR_INVALID_ARG, "row_ptr must start at 0 and end at nnz");
+  // the shard's V x (doc_end - doc_begin) CSR: every word row keeps its
+  // entries inside the range, documents renumbered from 0 (the full
+  // validation happens in wmd_corpus_load)
+  std::vector<int64_t> rp(V + 1, 0);
+  std::vector<int32_t> di;
+  std::vector<float> vv;
+  for (int64_t w = 0; w < V; ++w) {
+    if (row_ptr[w + 1] < row_ptr[w]) return set_error(WMD_ERR_INVALID_ARG, "row_ptr decreases");
+    for (int64_t e = row_ptr[w]; e < row_ptr[w + 1]; ++e) {
+      const int64_t j = doc_idx[e];
+      if (j >= doc_begin && j < doc_end) {
+        di.push_back((int32_t)(j - doc_begin));
+        vv.push_back(val[e]);
+      }
+    }
+    rp[w + 1] = (int64_t)di.size();
+  }
+  return wmd_corpus_load(vecs, V, d, rp.data(), di.data(), vv.data(), doc_end - doc_begin,
+                         (int64_t)di.size(), opt, out);
+}
+
 void wmd_corpus_free(wmd_corpus* c) {
   if (!c) return;
   release_batch_state(c);
@@ -501,7 +564,6 @@ wmd_status wmd_build_kernel_matrix(wmd_corpus* c, const int32_t* d_q_ids, const 
   float* r = reinterpret_cast<float*>(ws + L.r_off);
   int* err = reinterpret_cast<int*>(ws + L.err_off);
   const L2Prefetch pf = loop_inputs(c, vr_class(v_r), prec);
-  WMD_CUDA_TRY(clear_errors(err, s));
   WMD_CUDA_TRY(launch_cdist(c, d_q_ids, d_q_w, v_r, VR, lambda, prec, ws + L.k_off, VR, 0, r,
                             r + VR, err, &pf, s));
   return WMD_OK;
@@ -525,7 +587,7 @@ wmd_status sinkhorn_loop(wmd_corpus* c, int32_t v_r, int32_t max_iter, wmd_preci
   const float* r = reinterpret_cast<const float*>(ws + L.r_off);
   const int* err = reinterpret_cast<const int*>(ws + L.err_off);
   WMD_CUDA_TRY(launch_loop(c, cls, ws + L.k_off, VR, 0, r, r + VR, v_r, max_iter, prec, d_out,
-                           err, err_out, static_cast<cudaStream_t>(stream)));
+                           err, L.n_err, err_out, static_cast<cudaStream_t>(stream)));
   return WMD_OK;
 }
 
@@ -574,7 +636,7 @@ wmd_status wmd_query_device_tol(wmd_corpus* c, const int32_t* d_q_ids, const flo
   const float* r = reinterpret_cast<const float*>(ws + L.r_off);
   const int* err = reinterpret_cast<const int*>(ws + L.err_off);
   WMD_CUDA_TRY(launch_loop_conv(c, cls, ws + L.k_off, VR, r, r + VR, v_r, max_iter, tol, prec,
-                                d_out, d_iters, err, static_cast<cudaStream_t>(stream)));
+                                d_out, d_iters, err, L.n_err, static_cast<cudaStream_t>(stream)));
   return WMD_OK;
 }
 

@@ -211,7 +211,7 @@ __global__ void __launch_bounds__(256) cdist_kernel(
 #pragma unroll
     for (int q = 0; q < TC; ++q) K[o + q] = outk[q];
   }
-  if (out_of_range) atomicOr(err + 1, kRangeFlag);
+  if (out_of_range) atomicOr(err, kRangeFlag);
 }
 
 template <int VRB, typename KT>
@@ -247,31 +247,42 @@ cudaError_t launch_cdist(const wmd_corpus* c, const int32_t* q_ids, const float*
                          cudaStream_t s) {
   // tensor cores (cdist_tc.cu): the query's columns in slices as wide as the
   // resident query operand allows (128 at most); every slice streams the
-  // active vocabulary once
-  cudaError_t e = cudaErrorNotSupported;
+  // active vocabulary once and writes its own cdist_tc_grid error slots.
+  // The choice must match cdist_err_slots.
   const int width = cdist_tc_max_width(c);
-  if (width >= VR || (width > 0 && VR <= 16)) {
-    e = launch_cdist_tc(c, q_ids, q_w, v_r, VR, lambda, prec, K, ldk, kcol0, r_out, lam_out,
-                        err, pf, s);
-  } else if (width > 0) {
+  if (width >= VR || (width > 0 && VR <= 16))
+    return launch_cdist_tc(c, q_ids, q_w, v_r, VR, lambda, prec, K, ldk, kcol0, r_out, lam_out,
+                           err, pf, s);
+  if (width > 0) {
     const size_t esz = prec == WMD_PREC_BF16_K ? 2 : 4;
+    const int G = cdist_tc_grid(c);
     for (int j0 = 0; j0 < VR; j0 += width) {
       const int vr_slice = std::max(0, std::min(width, v_r - j0));
       // a slice past the last query word still writes its zero padding
-      e = launch_cdist_tc(c, q_ids + std::min(j0, v_r), q_w + std::min(j0, v_r), vr_slice, width,
-                          lambda, prec, static_cast<char*>(K) + (size_t)j0 * esz, ldk, kcol0,
-                          r_out ? r_out + j0 : nullptr, j0 == 0 ? lam_out : nullptr, err,
-                          j0 == 0 ? pf : nullptr, s);
-      if (e != cudaSuccess) break;
+      const cudaError_t e = launch_cdist_tc(
+          c, q_ids + std::min(j0, v_r), q_w + std::min(j0, v_r), vr_slice, width, lambda, prec,
+          static_cast<char*>(K) + (size_t)j0 * esz, ldk, kcol0, r_out ? r_out + j0 : nullptr,
+          j0 == 0 ? lam_out : nullptr, err + (j0 / width) * G, j0 == 0 ? pf : nullptr, s);
+      if (e != cudaSuccess) return e;
     }
+    return cudaSuccess;
   }
-  if (e != cudaErrorNotSupported) return e;
+  // CUDA cores: one slot, cleared here and ORed into by every CTA
+  cudaError_t e = cudaMemsetAsync(err, 0, sizeof(int), s);
+  if (e != cudaSuccess) return e;
   if (prec == WMD_PREC_BF16_K)
     return dispatch_cdist<__nv_bfloat16>(c, q_ids, q_w, v_r, VR, lambda,
                                          static_cast<__nv_bfloat16*>(K), ldk, kcol0, r_out,
                                          lam_out, err, s);
   return dispatch_cdist<float>(c, q_ids, q_w, v_r, VR, lambda, static_cast<float*>(K), ldk,
                                kcol0, r_out, lam_out, err, s);
+}
+
+int cdist_err_slots(const wmd_corpus* c, int VR) {
+  const int width = cdist_tc_max_width(c);
+  if (width >= VR || (width > 0 && VR <= 16)) return cdist_tc_grid(c);
+  if (width > 0) return (VR + width - 1) / width * cdist_tc_grid(c);
+  return 1;
 }
 
 }  // namespace wmd

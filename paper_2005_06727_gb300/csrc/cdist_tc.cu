@@ -77,7 +77,8 @@ struct Params {
   int num_tiles;
   int KB;
   int S;  // stages of the A ring
-  int* err;              // the query's error words: [0] timeout, [1] range
+  int* err;              // this launch's error slots, one per CTA, written by every CTA
+                         // at its end: 0, or a timeout code and/or kRangeFlag
   long long wait_cycles; // limit of every wait between roles (drains keep kWaitCycles)
   // read-only data the next kernel (the fused loop) starts from: prefetched
   // into L2 with the evict-last priority while the vocabulary streams
@@ -354,6 +355,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_base_s + 1);
   int* consumed_s = const_cast<int*>(abort_flag) + 1;
   volatile int* issued_s = consumed_s + 1;      // gathering warps whose loads are in flight
+  int* range_s = const_cast<int*>(issued_s) + 1; // kRangeFlag once an epilogue thread saw lambda m too large
 
   const int tid = threadIdx.x;
   const int warp = tid >> 5;
@@ -385,6 +387,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     *abort_flag = 0;
     *consumed_s = 0;
     *issued_s = 0;
+    *range_s = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     fence_async_smem();
   }
@@ -614,7 +617,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
       }
     }
-    if (out_of_range) atomicOr(p.err + 1, kRangeFlag);
+    if (out_of_range) atomicOr(range_s, kRangeFlag);
   }
 
   if (warp == 0 && lane == 0) TC_TRACE(4, 0);
@@ -625,13 +628,15 @@ __global__ void __launch_bounds__(kThreads, 1)
     tc_fence_after();
     tmem_dealloc(tmem_base, kCols);
   }
-  if (tid == 0 && *abort_flag) atomicCAS(p.err, 0, *abort_flag);
+  // this CTA's error slot, written whatever happened, so that nothing has to
+  // clear it before the launch
+  if (tid == 0) p.err[blockIdx.x] = *abort_flag | *range_s;
 }
 
 // Shared memory of one CTA for S stages.
 template <int N>
 size_t smem_bytes(int KB, int S) {
-  return 1024 + 2 * (size_t)KB * N * 128 + (size_t)S * kStageBytes + (2 * S + 5) * 8 + N * 12 + 16;
+  return 1024 + 2 * (size_t)KB * N * 128 + (size_t)S * kStageBytes + (2 * S + 5) * 8 + N * 12 + 32;
 }
 
 constexpr size_t kSmemLimit = 232448;
@@ -679,7 +684,7 @@ cudaError_t launch_t(const wmd_corpus* c, Params p, cudaStream_t s) {
       set_bytes[dev] = bytes;
     }
   }
-  const int grid = std::max(1, std::min(p.num_tiles, c->num_sms));
+  const int grid = cdist_tc_grid(c);
   const CUtensorMap* mh = reinterpret_cast<const CUtensorMap*>(c->tmap_hi);
   const CUtensorMap* ml = reinterpret_cast<const CUtensorMap*>(c->tmap_lo);
   cdist_tc_kernel<N, KT><<<grid, kThreads, bytes, s>>>(*mh, *ml, p);
@@ -708,6 +713,11 @@ bool make_vecs_tensor_map(wmd_corpus* c) {
     std::memcpy(part ? c->tmap_lo : c->tmap_hi, &map, sizeof(map));
   }
   return true;
+}
+
+int cdist_tc_grid(const wmd_corpus* c) {
+  const int tiles = (int)((c->U + tc::kM - 1) / tc::kM);
+  return std::max(1, std::min(tiles, c->num_sms));
 }
 
 int cdist_tc_max_width(const wmd_corpus* c) {

@@ -74,9 +74,9 @@ extern "C" wmd_status wmd_query_device_noalloc(wmd_corpus* corpus, const int32_t
     scratch = g_scratch_ptr[corpus->device];
   }
   if (!scratch) return wmd::set_error(WMD_ERR_CUDA, "scratch array not reserved on this device");
-  // The kernels overwrite every byte of the scratch they read (r, lambda, K);
-  // the error words, which must start at zero, are cleared by a memset node at
-  // the start of every call (stream-ordered, no allocation).
+  // The kernels overwrite every byte of the scratch they read (r, lambda, K,
+  // and the error slots, one per cdist CTA), so nothing has to be cleared
+  // between calls.
   return wmd_query_device(corpus, d_q_ids, d_q_w, v_r, lambda, max_iter, prec, scratch,
                           kWmdScratchBytes, d_out, stream);
 }

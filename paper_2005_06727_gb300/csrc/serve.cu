@@ -21,6 +21,7 @@
 #include <condition_variable>
 #include <cstring>
 #include <deque>
+#include <limits>
 #include <map>
 #include <memory>
 #include <mutex>
@@ -133,6 +134,7 @@ struct Layout {
   int ldk = 0;
   size_t words = 0;
   size_t r_off = 0, err_off = 0, k_off = 0, ws_bytes = 0;
+  std::vector<size_t> err_first;   // query -> its first error slot (prefix sums; [nq] = total)
   std::vector<int> desc_of;        // query -> index in the descriptor table
   int cls_begin[kNumClasses + 1];  // descriptor ranges per class
 };
@@ -148,8 +150,12 @@ Layout plan(const wmd_corpus* c, const std::vector<const Req*>& qs, wmd_precisio
   }
   L.ldk = std::max(col, 8);
   L.r_off = 0;
-  L.err_off = (size_t)L.ldk * 4;  // every query's error words, after every query's r
-  L.k_off = round_up(L.err_off + qs.size() * kErrWords * sizeof(int), 256);
+  // after every query's r: every query's error slots (one per cdist CTA)
+  L.err_off = (size_t)L.ldk * 4;
+  L.err_first.assign(qs.size() + 1, 0);
+  for (size_t q = 0; q < qs.size(); ++q)
+    L.err_first[q + 1] = L.err_first[q] + cdist_err_slots(c, qs[q]->VR);
+  L.k_off = round_up(L.err_off + L.err_first.back() * sizeof(int), 256);
   const size_t kb = round_up((size_t)std::max<int64_t>(c->U, 1) * L.ldk * k_elem(prec), 256);
   L.ws_bytes = L.k_off + kb;
   // descriptors grouped by width class
@@ -181,7 +187,7 @@ wmd_status enqueue_batch(wmd_corpus* c, Slot& s, const std::vector<const Req*>& 
   WMD_CUDA_TRY(grow_host(&s.h_w, &s.h_w_cap, L.words));
   WMD_CUDA_TRY(grow_host(&s.h_desc, &s.h_desc_cap, nq));
   WMD_CUDA_TRY(grow_host(&s.h_out, &s.h_out_cap, nq * N1));
-  WMD_CUDA_TRY(grow_host(&s.h_err, &s.h_err_cap, nq * kErrWords));
+  WMD_CUDA_TRY(grow_host(&s.h_err, &s.h_err_cap, L.err_first.back()));
 
   // staging: compacted words of every query, and the descriptor table
   size_t off = 0;
@@ -194,10 +200,9 @@ wmd_status enqueue_batch(wmd_corpus* c, Slot& s, const std::vector<const Req*>& 
   }
   char* ws = s.d_ws;
   float* r_all = reinterpret_cast<float*>(ws + L.r_off);
-  int* err = reinterpret_cast<int*>(ws + L.err_off);  // [nq][kErrWords]
+  int* err = reinterpret_cast<int*>(ws + L.err_off);  // every query's slots
   for (size_t q = 0; q < nq; ++q) {
     QueryDesc& d = s.h_desc[L.desc_of[q]];
-    d.err = err + q * kErrWords;
     d.r = r_all + L.col0[q];
     d.out = s.d_out + q * N1;
     d.kcol0 = L.col0[q];
@@ -209,14 +214,13 @@ wmd_status enqueue_batch(wmd_corpus* c, Slot& s, const std::vector<const Req*>& 
   WMD_CUDA_TRY(cudaMemcpyAsync(s.d_ids, s.h_ids, L.words * sizeof(int32_t), cudaMemcpyHostToDevice, st));
   WMD_CUDA_TRY(cudaMemcpyAsync(s.d_w, s.h_w, L.words * sizeof(float), cudaMemcpyHostToDevice, st));
   WMD_CUDA_TRY(cudaMemcpyAsync(s.d_desc, s.h_desc, nq * sizeof(QueryDesc), cudaMemcpyHostToDevice, st));
-  // every query's error words start clear: a failure fails that query only
-  WMD_CUDA_TRY(cudaMemsetAsync(err, 0, nq * kErrWords * sizeof(int), st));
-  // the first cdist launch prefetches the loop's document CSR into L2
+  // the first cdist launch prefetches the loop's document CSR into L2; every
+  // query's cdist writes its own error slots (a failure fails that query only)
   const L2Prefetch pf = loop_inputs(c, vr_class(qs[0]->v_r), prec);
   for (size_t q = 0; q < nq; ++q)
     WMD_CUDA_TRY(launch_cdist(c, s.d_ids + word_off[q], s.d_w + word_off[q], qs[q]->v_r, qs[q]->VR,
                               qs[q]->lambda, prec, ws + L.k_off, L.ldk, L.col0[q],
-                              r_all + L.col0[q], nullptr, err + q * kErrWords,
+                              r_all + L.col0[q], nullptr, err + L.err_first[q],
                               q == 0 ? &pf : nullptr, st));
   for (int cls = 0; cls < kNumClasses; ++cls) {
     const int n = L.cls_begin[cls + 1] - L.cls_begin[cls];
@@ -226,7 +230,8 @@ wmd_status enqueue_batch(wmd_corpus* c, Slot& s, const std::vector<const Req*>& 
   }
   if (c->N > 0)
     WMD_CUDA_TRY(cudaMemcpyAsync(s.h_out, s.d_out, nq * N1 * sizeof(double), cudaMemcpyDeviceToHost, st));
-  WMD_CUDA_TRY(cudaMemcpyAsync(s.h_err, err, nq * kErrWords * sizeof(int), cudaMemcpyDeviceToHost, st));
+  WMD_CUDA_TRY(cudaMemcpyAsync(s.h_err, err, L.err_first.back() * sizeof(int),
+                               cudaMemcpyDeviceToHost, st));
   return WMD_OK;
 }
 
@@ -311,6 +316,7 @@ struct wmd_server {
   struct InFlight {
     int slot = -1;
     std::vector<std::shared_ptr<Request>> reqs;
+    std::vector<size_t> err_first;  // each request's error slots in the slot's copy
   };
 
   wmd_corpus* corpus = nullptr;
@@ -355,9 +361,9 @@ void wmd_server::retire_finished(std::unique_lock<std::mutex>& lock, bool block)
     auto& reqs = inflight[i].reqs;
     for (size_t q = 0; q < reqs.size(); ++q) {
       Request& r = *reqs[q];
-      // the request's own error words (copied back with the results)
-      const int* ew = s.h_err + q * kErrWords;
-      const int err = e == cudaSuccess ? (ew[0] ? ew[0] : ew[1]) : 0;
+      // the request's own error slots (copied back with the results)
+      const auto& ef = inflight[i].err_first;
+      const int err = e == cudaSuccess ? error_summary(s.h_err + ef[q], ef[q + 1] - ef[q]) : 0;
       if (e != cudaSuccess) {
         r.status = WMD_ERR_CUDA;
         r.error = std::string("batch failed: ") + cudaGetErrorString(e);
@@ -428,6 +434,7 @@ bool wmd_server::launch_one(std::unique_lock<std::mutex>& lock) {
   slot_busy[free_slot] = true;
   InFlight f;
   f.slot = free_slot;
+  f.err_first = L.err_first;
   f.reqs = std::move(batch);
   stats.batches += 1;
   stats.max_batch_seen = std::max<int64_t>(stats.max_batch_seen, (int64_t)f.reqs.size());
@@ -547,17 +554,26 @@ wmd_status wmd_query_batch(wmd_corpus* c, int32_t nq, const int64_t* q_ptr, cons
   }
   if (ge) ge->last_use = ++B->tick;
   WMD_CUDA_TRY(cudaStreamSynchronize(s.stream));
+  // a query whose cdist reported an error gets NaN results (the loop kernel
+  // of a batch does not read the error slots) and the call reports the first
+  // such query
+  const size_t N1 = (size_t)std::max<int64_t>(c->N, 1);
+  wmd_status first = WMD_OK;
+  std::string msg;
   for (int q = 0; q < nq; ++q) {
-    const int* ew = s.h_err + (size_t)q * kErrWords;
-    if (ew[0] | ew[1]) {
-      device_error(ew[0] ? ew[0] : ew[1]);
-      return set_error(ew[0] ? WMD_ERR_TIMEOUT : WMD_ERR_RANGE,
-                       "query " + std::to_string(q) + " of the batch: " + wmd_last_error());
+    double* row = out + (size_t)q * c->N;
+    const int err = error_summary(s.h_err + L.err_first[q], L.err_first[q + 1] - L.err_first[q]);
+    if (err) {
+      if (c->N > 0) std::fill(row, row + c->N, std::numeric_limits<double>::quiet_NaN());
+      if (first == WMD_OK) {
+        first = device_error(err);
+        msg = "query " + std::to_string(q) + " of the batch: " + wmd_last_error();
+      }
+    } else if (c->N > 0) {
+      std::memcpy(row, s.h_out + q * N1, c->N * sizeof(double));
     }
   }
-  const size_t N1 = (size_t)std::max<int64_t>(c->N, 1);
-  for (int q = 0; q < nq; ++q)
-    if (c->N > 0) std::memcpy(out + (size_t)q * c->N, s.h_out + q * N1, c->N * sizeof(double));
+  if (first != WMD_OK) return set_error(first, msg);
   return WMD_OK;
 }
 

@@ -10,24 +10,43 @@ namespace {
 template <int CLS, int V>
 constexpr int rpw() { return (32 / Var<CLS, V>::PI) * Var<CLS, V>::RMAX; }
 
+// rows per warp and warps per CTA of variant `var` of class CLS
+template <int CLS>
+int cls_rows(int var) {
+  if constexpr (kClassVariants[CLS] > 2) {
+    if (var == 2) return rpw<CLS, 2>();
+  }
+  return var ? rpw<CLS, 1>() : rpw<CLS, 0>();
+}
+template <int CLS>
+int cls_warps(int var) {
+  if constexpr (kClassVariants[CLS] > 2) {
+    if (var == 2) return Var<CLS, 2>::NW;
+  }
+  return var ? Var<CLS, 1>::NW : Var<CLS, 0>::NW;
+}
+
 }  // namespace
 
 int rows_per_warp(int cls, int var) {
   switch (cls) {
-    case 0: return var ? rpw<0, 1>() : rpw<0, 0>();
-    case 1: return var ? rpw<1, 1>() : rpw<1, 0>();
-    case 2: return var ? rpw<2, 1>() : rpw<2, 0>();
-    case 3: return var ? rpw<3, 1>() : rpw<3, 0>();
-    case 4: return var ? rpw<4, 1>() : rpw<4, 0>();
-    default: return var ? rpw<5, 1>() : rpw<5, 0>();
+    case 0: return cls_rows<0>(var);
+    case 1: return cls_rows<1>(var);
+    case 2: return cls_rows<2>(var);
+    case 3: return cls_rows<3>(var);
+    case 4: return cls_rows<4>(var);
+    default: return cls_rows<5>(var);
   }
 }
 
 int warps_per_cta(int cls, int var) {
   switch (cls) {
-    case 4: return var ? Var<4, 1>::NW : Var<4, 0>::NW;
-    case 5: return var ? Var<5, 1>::NW : Var<5, 0>::NW;
-    default: return 4;
+    case 0: return cls_warps<0>(var);
+    case 1: return cls_warps<1>(var);
+    case 2: return cls_warps<2>(var);
+    case 3: return cls_warps<3>(var);
+    case 4: return cls_warps<4>(var);
+    default: return cls_warps<5>(var);
   }
 }
 
@@ -46,9 +65,9 @@ L2Prefetch loop_inputs(const wmd_corpus* c, int cls, wmd_precision prec) {
 
 cudaError_t launch_loop(const wmd_corpus* c, int cls, const void* K, int ldk, int kcol0,
                         const float* r, const float* lam, int v_r, int T, wmd_precision prec,
-                        double* out, const int* err, int* err_out, cudaStream_t s) {
+                        double* out, const int* err, int n_err, int* err_out, cudaStream_t s) {
   const int var = c->loop_variant[cls][prec == WMD_PREC_BF16_K];
-  LoopParams p = base_params(c, cls, var, K, ldk, T, err);
+  LoopParams p = base_params(c, cls, var, K, ldk, T, err, n_err);
   p.kcol0 = kcol0;
   p.r = r;
   p.lam = lam;
@@ -64,7 +83,8 @@ cudaError_t launch_loop_batch(const wmd_corpus* c, int cls, const void* K, int l
                               const QueryDesc* d_queries, int nq, int T, wmd_precision prec,
                               cudaStream_t s) {
   const int var = c->loop_variant[cls][prec == WMD_PREC_BF16_K];
-  LoopParams p = base_params(c, cls, var, K, ldk, T, nullptr);  // errors: per query descriptor
+  // errors: the host reads every batched query's slots
+  LoopParams p = base_params(c, cls, var, K, ldk, T, nullptr, 0);
   p.queries = d_queries;
   const int n_items = c->sched[cls][var].n_items;
   if (prec == WMD_PREC_BF16_K) return dispatch_loop<false, __nv_bfloat16>(cls, var, p, n_items, nq, s);

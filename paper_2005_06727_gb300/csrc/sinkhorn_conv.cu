@@ -16,9 +16,9 @@ namespace wmd {
 cudaError_t launch_loop_conv(const wmd_corpus* c, int cls, const void* K, int ldk,
                              const float* r, const float* lam, int v_r, int T, float tol,
                              wmd_precision prec, double* out, int32_t* iters, const int* err,
-                             cudaStream_t s) {
+                             int n_err, cudaStream_t s) {
   const int var = c->loop_variant[cls][prec == WMD_PREC_BF16_K];
-  LoopParams p = base_params(c, cls, var, K, ldk, T, err);
+  LoopParams p = base_params(c, cls, var, K, ldk, T, err, n_err);
   p.r = r;
   p.lam = lam;
   p.v_r = v_r;

@@ -46,7 +46,7 @@
 // The kernel is launched as a programmatic dependent of the cdist kernel: a
 // warp reads its task record and its rows' word ids and weights (corpus data,
 // which cdist prefetched into L2) and only then waits for cdist's K, r,
-// lambda and error words.
+// lambda and error slots.
 //
 // K .* M for the final step is recovered from the K block already in
 // registers: M = -ln(K) / lambda = -log2(K) ln 2 / lambda, exact for K = 1
@@ -76,10 +76,11 @@ struct LoopParams {
   int T;
   const WarpTask* tasks;  // [item][warp]
   double* out;
-  const int* err;  // the query's error words (a cdist wait ran out, or K left the
-                   // float32 range): when either is set, every result is NaN
-                   // (batched launches: each query's own, in its descriptor)
-  int* err_out;    // optional summary of err for the host (block 0 writes it)
+  const int* err;  // the query's error slots, one per cdist CTA (a wait ran out,
+  int n_err;       // or K left the float32 range): if any is set, every result is
+                   // NaN.  Batched launches do not read them: the host turns a
+                   // failed query of a batch into NaN results and an error.
+  int* err_out;    // optional summary of the slots for the host (warp 0 of block 0)
   const QueryDesc* queries;  // blockIdx.y selects the query; NULL: the fields above
   // convergence-tested instances (CONV) only, single query: a document stops
   // once x changes by at most tol relative to its previous value, and
@@ -113,9 +114,17 @@ __device__ __forceinline__ void load_krow(const KT* __restrict__ Kb, int64_t row
   }
 }
 
+// OR of a query's error slots (one per cdist CTA, written by every CTA at
+// its end, so nothing clears them before a query), read by a whole warp.
+__device__ __forceinline__ int read_errors(const int* err, int n, int lane) {
+  int v = 0;
+  for (int i = lane; i < n; i += 32) v |= err[i];
+  return __reduce_or_sync(0xffffffffu, v);
+}
+
 // Programmatic dependent launch: the kernel may start while the cdist
 // kernel before it in the stream still runs; from this wait on, everything
-// that kernel wrote (K, r, lambda, the error words) is visible.  A no-op when
+// that kernel wrote (K, r, lambda, the error slots) is visible.  A no-op when
 // the launch has no programmatic predecessor.
 __device__ __forceinline__ void wait_for_producer() {
   asm volatile("griddepcontrol.wait;" ::: "memory");
@@ -284,8 +293,9 @@ __device__ __forceinline__ void solve(const LoopParams& p, const TeamCtx& t) {
     }
   }
   wait_for_producer();
-  if (t.q.err[0] | t.q.err[1]) {  // cdist gave up waiting, or K left the float32 range:
-                              // no result (whole teams leave together)
+  if (!p.queries && read_errors(p.err, p.n_err, t.lane)) {
+    // the cdist kernel gave up waiting, or K left the float32 range: no
+    // result (whole teams leave together)
     if (t.kw == 0 && t.lane == 0) {
       t.q.out[t.doc] = __longlong_as_double(0x7ff8000000000000ll);
       if (CONV && p.iters) p.iters[t.doc] = p.T;
@@ -580,9 +590,15 @@ __global__ void __launch_bounds__(NW * 32, MINB) sinkhorn_fused_kernel(LoopParam
   t.lane = threadIdx.x & 31;
   t.pi = t.lane % PI;
   t.pw = t.lane / PI;
-  if (p.err_out && blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) {
+  if (p.err_out && blockIdx.x == 0 && blockIdx.y == 0 && t.warp == 0) {
+    // summary for the host: the first CTA code found, with the range flag
     wait_for_producer();
-    *p.err_out = p.err[0] ? p.err[0] : p.err[1];
+    int v = 0;
+    for (int i = t.lane; i < p.n_err; i += 32) v |= p.err[i];
+    const unsigned nz = __ballot_sync(0xffffffffu, v != 0);
+    const int first = __shfl_sync(0xffffffffu, v, nz ? __ffs(nz) - 1 : 0);
+    const int range = __reduce_or_sync(0xffffffffu, v) & kRangeFlag;
+    if (t.lane == 0) *p.err_out = first | range;
   }
   const WarpTask task = p.tasks[blockIdx.x * NW + t.warp];
   t.W = task.n_w >> kTaskWShift;
@@ -599,12 +615,12 @@ __global__ void __launch_bounds__(NW * 32, MINB) sinkhorn_fused_kernel(LoopParam
     t.q.out = p.out;
     t.q.kcol0 = p.kcol0;
     t.q.v_r = p.v_r;
-    t.q.err = p.err;
   }
   if (t.n == 0) {
-    wait_for_producer();  // the timeout word comes from the cdist kernel
+    wait_for_producer();  // the error slots come from the cdist kernel
+    const bool bad = !p.queries && read_errors(p.err, p.n_err, t.lane);
     if (t.kw == 0 && t.lane == 0) {
-      t.q.out[t.doc] = (t.q.err[0] | t.q.err[1]) || p.T >= 1 ? __longlong_as_double(0x7ff8000000000000ll) : 0.0;
+      t.q.out[t.doc] = bad || p.T >= 1 ? __longlong_as_double(0x7ff8000000000000ll) : 0.0;
       // x of an empty document goes 1/v_r -> 0 -> 0/0: it never settles
       if (CONV && p.iters) p.iters[t.doc] = p.T;
     }
@@ -686,22 +702,31 @@ cudaError_t launch_var(const LoopParams& p, int n_items, int nq, cudaStream_t s)
   return cudaLaunchKernelEx(&cfg, kern, p);
 }
 
+template <int CLS, bool CONV, typename KT>
+cudaError_t launch_cls(int var, const LoopParams& p, int n_items, int nq, cudaStream_t s) {
+  if constexpr (kClassVariants[CLS] > 2) {
+    if (var == 2) return launch_var<CLS, 2, CONV, KT>(p, n_items, nq, s);
+  }
+  return var ? launch_var<CLS, 1, CONV, KT>(p, n_items, nq, s)
+             : launch_var<CLS, 0, CONV, KT>(p, n_items, nq, s);
+}
+
 template <bool CONV, typename KT>
 cudaError_t dispatch_loop(int cls, int var, const LoopParams& p, int n_items, int nq,
                           cudaStream_t s) {
   switch (cls) {
-    case 0: return var ? launch_var<0, 1, CONV, KT>(p, n_items, nq, s) : launch_var<0, 0, CONV, KT>(p, n_items, nq, s);
-    case 1: return var ? launch_var<1, 1, CONV, KT>(p, n_items, nq, s) : launch_var<1, 0, CONV, KT>(p, n_items, nq, s);
-    case 2: return var ? launch_var<2, 1, CONV, KT>(p, n_items, nq, s) : launch_var<2, 0, CONV, KT>(p, n_items, nq, s);
-    case 3: return var ? launch_var<3, 1, CONV, KT>(p, n_items, nq, s) : launch_var<3, 0, CONV, KT>(p, n_items, nq, s);
-    case 4: return var ? launch_var<4, 1, CONV, KT>(p, n_items, nq, s) : launch_var<4, 0, CONV, KT>(p, n_items, nq, s);
-    default: return var ? launch_var<5, 1, CONV, KT>(p, n_items, nq, s) : launch_var<5, 0, CONV, KT>(p, n_items, nq, s);
+    case 0: return launch_cls<0, CONV, KT>(var, p, n_items, nq, s);
+    case 1: return launch_cls<1, CONV, KT>(var, p, n_items, nq, s);
+    case 2: return launch_cls<2, CONV, KT>(var, p, n_items, nq, s);
+    case 3: return launch_cls<3, CONV, KT>(var, p, n_items, nq, s);
+    case 4: return launch_cls<4, CONV, KT>(var, p, n_items, nq, s);
+    default: return launch_cls<5, CONV, KT>(var, p, n_items, nq, s);
   }
 }
 
 // Parameters shared by every launch of the loop for query class cls.
 inline LoopParams base_params(const wmd_corpus* c, int cls, int var, const void* K, int ldk,
-                              int T, const int* err) {
+                              int T, const int* err, int n_err) {
   LoopParams p;
   p.doc_ptr = c->doc_ptr;
   p.doc_words = c->doc_words;
@@ -716,6 +741,7 @@ inline LoopParams base_params(const wmd_corpus* c, int cls, int var, const void*
   p.tasks = c->sched[cls][var].d_tasks;
   p.out = nullptr;
   p.err = err;
+  p.n_err = n_err;
   p.err_out = nullptr;
   p.queries = nullptr;
   p.tol = 0.f;

@@ -128,22 +128,34 @@ struct wmd_corpus {
 namespace wmd {
 
 // Workspace carve-up for one query of class VR: the padded query weights r
-// (VR floats) followed by lambda (float VR), the final step's scale
-// -ln 2 / lambda (a double at float VR + 2), the query's two device-side error
-// words (ints at float VR + 4 and VR + 5, cleared before every query), and the
-// word-major K (U x VR).
+// (VR floats) followed by lambda (float VR) and the final step's scale
+// -ln 2 / lambda (a double at float VR + 2); the query's error slots
+// (cdist_err_slots ints); and the word-major K (U x VR).
 struct WsLayout {
   size_t r_off, err_off, k_off, total;
+  int n_err;
 };
-// The two error words of a query or batch: [0] the first cdist wait that ran
-// out (0x40000000 | role << 24 | iteration), [1] kRangeFlag once some
-// lambda * M reached the float32 range limit of K.
-constexpr int kErrWords = 2;
+// Error slot codes: a cdist wait that ran out (0x40000000 | role << 24 |
+// iteration) and/or kRangeFlag once some lambda * M reached the float32 range
+// limit of K.  The tensor-core cdist writes one slot per CTA at its end, so
+// nothing clears the slots before a query; the CUDA-core cdist ORs into one
+// slot that a memset clears first.
 constexpr int kRangeFlag = 0x20000000;
 constexpr float kRangeLimit = 87.33654f;  // -ln(FLT_MIN): K = exp(-lambda M) below is subnormal
-// Clears the error words on `s` (a memset node; no allocation).
-inline cudaError_t clear_errors(int* err, cudaStream_t s) {
-  return cudaMemsetAsync(err, 0, kErrWords * sizeof(int), s);
+// Error slots one query of width class VR uses (the cdist kernel's CTAs over
+// all its column slices, or 1 for the CUDA-core kernel).
+int cdist_err_slots(const wmd_corpus* c, int VR);
+// CTAs of one tensor-core cdist launch.
+int cdist_tc_grid(const wmd_corpus* c);
+// Host summary of a query's error slots: the first nonzero code, with the
+// range flag if any slot has it (0: no error).
+inline int error_summary(const int* slots, size_t n) {
+  int first = 0, any = 0;
+  for (size_t i = 0; i < n; ++i) {
+    if (!first) first = slots[i];
+    any |= slots[i];
+  }
+  return first | (any & kRangeFlag);
 }
 WsLayout ws_layout(const wmd_corpus* c, int VR, wmd_precision prec);
 
@@ -157,7 +169,8 @@ struct L2Prefetch {
 // document-major CSR.
 L2Prefetch loop_inputs(const wmd_corpus* c, int cls, wmd_precision prec);
 
-// Kernel launchers (cdist.cu / sinkhorn.cu).  err: the query's error words.
+// Kernel launchers (cdist.cu / sinkhorn.cu).  err: the query's error slots
+// (cdist_err_slots of them).
 cudaError_t launch_cdist(const wmd_corpus* c, const int32_t* q_ids, const float* q_w, int v_r,
                          int VR, float lambda, wmd_precision prec, void* K, int ldk, int kcol0,
                          float* r_out, float* lam_out, int* err, const L2Prefetch* pf,
@@ -171,8 +184,7 @@ bool make_vecs_tensor_map(wmd_corpus* c);
 int cdist_tc_max_width(const wmd_corpus* c);
 void release_batch_state(const wmd_corpus* c);  // serve.cu: cached batch buffers and graphs
 // One query of a batched loop launch: its padded weights r, output row, first
-// column of its block in the word-major K, its number of words and its error
-// words (so that one failed query of a batch fails no other).
+// column of its block in the word-major K, and its number of words.
 struct QueryDesc {
   const float* r;
   double* out;
@@ -180,16 +192,15 @@ struct QueryDesc {
   int v_r;
   float lambda;
   double scale;    // -ln 2 / lambda, the final step's factor
-  const int* err;  // the query's own error words
 };
 cudaError_t launch_loop_batch(const wmd_corpus* c, int cls, const void* K, int ldk,
                               const QueryDesc* d_queries, int nq, int T, wmd_precision prec,
                               cudaStream_t s);
-// err: the query's error words; err_out (optional, device-visible): receives
-// their summary (the timeout code if set, else the range flag, else 0)
+// err: the query's error slots; err_out (optional, device-visible): receives
+// their summary (the first CTA's code found, with the range flag, or 0)
 cudaError_t launch_loop(const wmd_corpus* c, int cls, const void* K, int ldk, int kcol0,
                         const float* r, const float* lam, int v_r, int T, wmd_precision prec,
-                        double* out, const int* err, int* err_out, cudaStream_t s);
+                        double* out, const int* err, int n_err, int* err_out, cudaStream_t s);
 // Top-k selection of WMD[N] (topk.cu): the k smallest values (ties: lower
 // document id first; NaN last) into out_idx / out_val, ascending.
 constexpr int kTopkMaxK = 1024;
@@ -201,7 +212,7 @@ cudaError_t launch_topk(const double* wmd, int64_t N, int k, int64_t* out_idx, d
 cudaError_t launch_loop_conv(const wmd_corpus* c, int cls, const void* K, int ldk,
                              const float* r, const float* lam, int v_r, int T, float tol,
                              wmd_precision prec, double* out, int32_t* iters, const int* err,
-                             cudaStream_t s);
+                             int n_err, cudaStream_t s);
 // Host-side message for a nonzero error word summary (timeout or range).
 wmd_status device_error(int code);
 // Looks up the no-allocation entry point's scratch array on `device` (once

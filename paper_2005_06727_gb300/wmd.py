@@ -85,6 +85,9 @@ _SIGS = {
     "wmd_corpus_load": (C.c_int, [_P, C.c_int64, C.c_int32, _P, _P, _P, C.c_int64, C.c_int64,
                                   _P, _P]),
     "wmd_corpus_free": (None, [_P]),
+    "wmd_shard_plan": (C.c_int, [_P, _P, C.c_int64, C.c_int64, C.c_int32, _P]),
+    "wmd_corpus_load_shard": (C.c_int, [_P, C.c_int64, C.c_int32, _P, _P, _P, C.c_int64, C.c_int64,
+                                        C.c_int64, C.c_int64, _P, _P]),
     "wmd_corpus_get_info": (C.c_int, [_P, _P]),
     "wmd_corpus_set_wait_limit": (C.c_int, [_P, C.c_int64]),
     "wmd_query": (C.c_int, [_P, _P, _P, C.c_int32, C.c_float, C.c_int32, C.c_int, _P]),
@@ -229,6 +232,16 @@ class Corpus:
         h = C.c_void_p()
         _check(lib().wmd_corpus_load(_ptr(vecs), V, d, _ptr(row_ptr), _ptr(doc_idx), _ptr(val),
                                      int(N), int(val.size), C.byref(o), C.byref(h)))
+        self._adopt(h)
+
+    @classmethod
+    def _from_handle(cls, h):
+        """A Corpus owning a handle returned by another loading call."""
+        self = cls.__new__(cls)
+        self._adopt(h)
+        return self
+
+    def _adopt(self, h):
         self._h = h
         info = CorpusInfo()
         _check(lib().wmd_corpus_get_info(self._h, C.byref(info)))
