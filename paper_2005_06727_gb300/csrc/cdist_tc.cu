@@ -294,6 +294,22 @@ __device__ __forceinline__ void tmem_load<32>(uint32_t taddr, float* v) {
   for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+// Hardware square root and base-2 exponential (PTX sqrt.approx / ex2.approx,
+// relative errors near 2^-23 and 2^-22): the epilogue's two transcendental
+// steps in one instruction each, since at 128-column queries the epilogue,
+// not the vocabulary stream, sets the kernel's pace.
+__device__ __forceinline__ float sqrt_fast(float x) {
+  float y;
+  asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+__device__ __forceinline__ float exp2_fast(float x) {
+  float y;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+constexpr float kLog2e = 1.4426950408889634f;
+
 // Stores the first n (a multiple of 4, n <= CH) values of a row chunk.
 template <int CH>
 __device__ __forceinline__ void store_chunk(float* dst, const float (&v)[CH], int n) {
@@ -361,9 +377,6 @@ __global__ void __launch_bounds__(kThreads, 1)
   const int warp = tid >> 5;
   const int lane = tid & 31;
   if (tid == 0) TC_TRACE(5, 0);
-  // the next kernel in the stream (the fused loop) may start its CTAs now;
-  // they wait for this grid's results before reading them
-  if (tid == 0) asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
 
   // the device rows of the query words (ids -> permutation) are looked up
   // first, so that these dependent loads overlap the prologue
@@ -372,6 +385,10 @@ __global__ void __launch_bounds__(kThreads, 1)
     const int64_t id = p.q_ids[tid];
     qrow = (id >= 0 && id < p.V) ? p.perm[id] : -2;
   }
+  // CTA 0 also copies the padded weights for the loop kernel: loaded here,
+  // beside the ids, so that their store below does not wait for a load
+  float qw = 0.f;
+  if (p.r_out && blockIdx.x == 0 && tid < p.VR && tid < p.v_r) qw = p.q_w[tid];
 
   // ---- prologue: barriers and TMEM only, so that the producer starts at once
   if (tid == 0) {
@@ -417,7 +434,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         qn = __int_as_float(0x7fc00000);
       }
     }
-    if (p.r_out && blockIdx.x == 0 && bt < p.VR) p.r_out[bt] = bt < p.v_r ? p.q_w[bt] : 0.f;
+    if (p.r_out && blockIdx.x == 0 && bt < p.VR) p.r_out[bt] = qw;
     if (p.lam_out && blockIdx.x == 0 && bt == 0) {
       // lambda, and the final step's scale -ln 2 / lambda as a double two
       // floats further on (8-byte aligned), for the loop kernel
@@ -499,6 +516,12 @@ __global__ void __launch_bounds__(kThreads, 1)
           TC_TRACE(0, it);
         }
       }
+      // the vocabulary stream of this CTA is issued: the next kernel in the
+      // stream (the fused loop) may start its CTAs once every CTA is here,
+      // so that they share the SMs with this grid's last tiles only (started
+      // earlier, they slowed this kernel more than they gained); they wait
+      // for this grid's results before reading them
+      asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
       if (*abort_flag) {
         // let the loads already issued land before the CTA leaves
         for (int j = *consumed_s; j < it; ++j) {
@@ -597,18 +620,31 @@ __global__ void __launch_bounds__(kThreads, 1)
           // NaN.  Where the GEMM form has cancelled more than two bits (m^2
           // below a quarter of |a|^2 + |b|^2: a near pair, Sec. 5), m^2 is
           // recomputed from the float32 rows by direct differences (Sec. 2).
+          // Three passes, so that the rare recomputation stays out of the two
+          // straight-line ones: m^2 by the GEMM form, the near pairs again,
+          // then K.
           float kv[CH];
+          uint32_t near = 0;  // bit j: column c + j is a near pair
 #pragma unroll
           for (int j = 0; j < CH; ++j) {
             const int col = c + j;
             const float dot = (fmaf(small[j], kLoScale, big[j]) * rsw) * qrs_s[col];
             const int qr = qrow_s[col];
             const float nsum = nw + qn_s[col];
-            float m2 = nsum - 2.f * dot;
-            if (m2 < kNearPair * nsum && qr >= 0 && qr != (int)w && col < p.v_r)
-              m2 = direct_m2(p.vecs, p.ldv, p.d, w, qr);
-            const float lm = p.lambda * sqrtf(fmaxf(m2, 0.f));
-            const float e = expf(-lm);
+            kv[j] = nsum - 2.f * dot;  // m^2 for now
+            near |= (kv[j] < kNearPair * nsum && qr >= 0 && qr != (int)w && col < p.v_r ? 1u : 0u) << j;
+          }
+          if (near) {
+#pragma unroll
+            for (int j = 0; j < CH; ++j)
+              if ((near >> j) & 1u) kv[j] = direct_m2(p.vecs, p.ldv, p.d, w, qrow_s[c + j]);
+          }
+#pragma unroll
+          for (int j = 0; j < CH; ++j) {
+            const int col = c + j;
+            const int qr = qrow_s[col];
+            const float lm = p.lambda * sqrt_fast(fmaxf(kv[j], 0.f));
+            const float e = exp2_fast(-lm * kLog2e);  // exp(-lambda m)
             const float k = qr == (int)w ? 1.f : (qr == -2 ? __int_as_float(0x7fc00000) : e);
             out_of_range |= col < p.v_r && qr >= 0 && qr != (int)w && lm > kRangeLimit;
             kv[j] = col < p.v_r ? k : 0.f;

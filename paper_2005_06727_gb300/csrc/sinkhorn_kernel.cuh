@@ -89,16 +89,34 @@ struct LoopParams {
   int32_t* iters;
 };
 
+// K is written by the cdist kernel, which may still be running when this
+// kernel starts (programmatic dependent launch), so K is not read-only for
+// this kernel's lifetime: no __ldg / ld.global.nc, which the compiler may
+// schedule above griddepcontrol.wait.  These loads are volatile asm, kept in
+// program order with the wait (itself volatile asm).
+__device__ __forceinline__ float4 ld_k4(const float4* a) {
+  float4 v;
+  asm volatile("ld.global.v4.f32 {%0, %1, %2, %3}, [%4];"
+               : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+               : "l"(a));
+  return v;
+}
+__device__ __forceinline__ uint2 ld_k2(const uint2* a) {
+  uint2 v;
+  asm volatile("ld.global.v2.u32 {%0, %1}, [%2];" : "=r"(v.x), "=r"(v.y) : "l"(a));
+  return v;
+}
+
 // Loads the C columns of K row `row` that lane pi owns, as C/2 float2 pairs.
 template <typename KT, int C, int PI>
-__device__ __forceinline__ void load_krow(const KT* __restrict__ Kb, int64_t row, int ldk,
+__device__ __forceinline__ void load_krow(const KT* Kb, int64_t row, int ldk,
                                           int kcol0, int pi, float2 (&dst)[C / 2]) {
   if constexpr (sizeof(KT) == 4) {
     const float4* src =
         reinterpret_cast<const float4*>(reinterpret_cast<const float*>(Kb) + row * ldk + kcol0);
 #pragma unroll
     for (int g = 0; g < C / 4; ++g) {
-      const float4 t = __ldg(src + g * PI + pi);
+      const float4 t = ld_k4(src + g * PI + pi);
       dst[2 * g + 0] = make_float2(t.x, t.y);
       dst[2 * g + 1] = make_float2(t.z, t.w);
     }
@@ -107,7 +125,7 @@ __device__ __forceinline__ void load_krow(const KT* __restrict__ Kb, int64_t row
         reinterpret_cast<const __nv_bfloat16*>(Kb) + row * ldk + kcol0);
 #pragma unroll
     for (int g = 0; g < C / 4; ++g) {
-      const uint2 t = __ldg(src + g * PI + pi);
+      const uint2 t = ld_k2(src + g * PI + pi);
       dst[2 * g + 0] = make_float2(__uint_as_float(t.x << 16), __uint_as_float(t.x & 0xffff0000u));
       dst[2 * g + 1] = make_float2(__uint_as_float(t.y << 16), __uint_as_float(t.y & 0xffff0000u));
     }
@@ -116,9 +134,17 @@ __device__ __forceinline__ void load_krow(const KT* __restrict__ Kb, int64_t row
 
 // OR of a query's error slots (one per cdist CTA, written by every CTA at
 // its end, so nothing clears them before a query), read by a whole warp.
+// Eight loads per lane are issued before any is used, so that up to 256
+// slots (every single-launch query) cost one trip to L2, not one per slot.
 __device__ __forceinline__ int read_errors(const int* err, int n, int lane) {
   int v = 0;
-  for (int i = lane; i < n; i += 32) v |= err[i];
+  for (int base = lane; base < n; base += 256) {
+    int w[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) w[k] = base + 32 * k < n ? err[base + 32 * k] : 0;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) v |= w[k];
+  }
   return __reduce_or_sync(0xffffffffu, v);
 }
 
@@ -293,15 +319,18 @@ __device__ __forceinline__ void solve(const LoopParams& p, const TeamCtx& t) {
     }
   }
   wait_for_producer();
-  if (!p.queries && read_errors(p.err, p.n_err, t.lane)) {
-    // the cdist kernel gave up waiting, or K left the float32 range: no
-    // result (whole teams leave together)
+  // the cdist kernel gave up waiting, or K left the float32 range: no result
+  // (whole teams leave together).  The resident path reads the error slots
+  // after it has issued its K gathers, so that both share one trip to L2.
+  auto failed = [&]() {
+    if (p.queries || !read_errors(p.err, p.n_err, t.lane)) return false;
     if (t.kw == 0 && t.lane == 0) {
       t.q.out[t.doc] = __longlong_as_double(0x7ff8000000000000ll);
       if (CONV && p.iters) p.iters[t.doc] = p.T;
     }
-    return;
-  }
+    return true;
+  };
+  if ((RELOAD || !t.nch) && failed()) return;
 
   // query weights and the initial u = 1 / x = v_r for my columns; one lane
   // per column seeds the SpMM sums of padding columns with 1 so that 1/x stays
@@ -353,6 +382,7 @@ __device__ __forceinline__ void solve(const LoopParams& p, const TeamCtx& t) {
         for (int q = 0; q < C2; ++q) kt[rI][q] = make_float2(1.f, 1.f);
       }
     }
+    if (failed()) return;
     permute_slots<R, PX, C2>(kt, px);
   }
 
@@ -594,7 +624,7 @@ __global__ void __launch_bounds__(NW * 32, MINB) sinkhorn_fused_kernel(LoopParam
     // summary for the host: the first CTA code found, with the range flag
     wait_for_producer();
     int v = 0;
-    for (int i = t.lane; i < p.n_err; i += 32) v |= p.err[i];
+    for (int i = t.lane; i < p.n_err; i += 32) v |= p.err[i];  // one CTA, once: plain loop
     const unsigned nz = __ballot_sync(0xffffffffu, v != 0);
     const int first = __shfl_sync(0xffffffffu, v, nz ? __ffs(nz) - 1 : 0);
     const int range = __reduce_or_sync(0xffffffffu, v) & kRangeFlag;
