@@ -62,6 +62,8 @@ def parse():
                          "independent replicas")
     ap.add_argument("--loop-variant", type=int, default=-1,
                     help="fused-loop tile variant (default: chosen by the autotuner)")
+    ap.add_argument("--loop-partition", type=int, default=100,
+                    help="team-size fill of the pinned --loop-variant (50, 75, 100, 200)")
     return ap.parse_args()
 
 
@@ -98,10 +100,10 @@ def measured_peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
 
 
-def recorded_traffic(kernel: str, workload: str, loop_variant=None):
+def recorded_traffic(kernel: str, workload: str, loop_variant=None, loop_partition=None):
     """DRAM bytes per launch from a committed ncu summary, if it was taken on
-    this workload (and loop variant) and the kernel's source is unchanged
-    since the counters were taken."""
+    this workload (and loop variant and partition) and the kernel's source is
+    unchanged since the counters were taken."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         rec = json.load(open(path)).get(kernel)
@@ -110,6 +112,8 @@ def recorded_traffic(kernel: str, workload: str, loop_variant=None):
     if not rec or rec.get("workload") != workload:
         return None
     if loop_variant is not None and rec.get("loop_variant") != loop_variant:
+        return None
+    if loop_partition is not None and rec.get("loop_partition", 100) != loop_partition:
         return None
     src = os.path.join(ROOT, "paper_2005_06727_gb300", "csrc", rec["source"])
     try:
@@ -532,12 +536,25 @@ def bench_serving(wmd, device, n_requests=1000, seed=11, workload="serving", n_c
                                        "max_batch_seen": stats["max_batch_seen"]}}
 
 
+_ALU_PEAK = {}
+
+
 def alu_peak_tflops(device, sm_max_mhz):
-    """FP32 FMA peak: the device's SM count x 128 FP32 lanes x 2 flop x the
-    maximum SM clock."""
+    """FP32 FMA peak of the fused loop's roofline, measured on the device by
+    ``wmd_measure_fp32_peak`` (the faster of packed FFMA2 and scalar FFMA).
+    Returns (TFLOP/s, details); the details also carry the figure derived
+    from the SM count x 128 FP32 lanes x 2 flop x the maximum SM clock."""
     import torch
-    sms = torch.cuda.get_device_properties(device).multi_processor_count
-    return sms * FP32_LANES_PER_SM * 2 * sm_max_mhz * 1e6 / 1e12, sms
+    from paper_2005_06727_gb300 import wmd
+    idx = torch.device(device).index or 0
+    if idx not in _ALU_PEAK:
+        sms = torch.cuda.get_device_properties(idx).multi_processor_count
+        measured = {"ffma2": wmd.measure_fp32_peak(idx, True),
+                    "ffma": wmd.measure_fp32_peak(idx, False)}
+        _ALU_PEAK[idx] = (max(measured.values()),
+                          {"measured_tflops": measured, "sms": sms,
+                           "derived_tflops": sms * FP32_LANES_PER_SM * 2 * sm_max_mhz * 1e6 / 1e12})
+    return _ALU_PEAK[idx]
 
 
 def bench_large(wmd, device, steps=5):
@@ -645,7 +662,7 @@ def bench_converge(wmd, corpus, dq, w, prec, stream, flush, reps=10):
             "rows": rows}
 
 
-def bench_topk(wmd, dq, N, stream, reps=20):
+def bench_topk(wmd, dq, N, stream, reps=20, corpus=None, w=None, prec=0, flush=None):
     """k nearest documents: wmd_topk on the bench query's WMD[N] (paper shape)
     and on a WMD-like vector of the serving corpus's size (N = 200000), CUDA
     events around each call (inputs in L2: one selection follows the loop
@@ -669,8 +686,41 @@ def bench_topk(wmd, dq, N, stream, reps=20):
                 b.synchronize()
                 ts.append(a.elapsed_time(b) * 1e3)
             rows.append({"input": name, "N": n, "k": k, "us": statistics.mean(ts)})
-    return {"what": "one-CTA radix select of the k smallest WMD values (ties to the lower id)",
-            "rows": rows}
+    out = {"what": "one-CTA radix select of the k smallest WMD values (ties to the lower id): "
+                   "keys in registers, 11-bit digits for N <= 16384 and k <= 256, else "
+                   "8-bit digits over shared-memory or streamed keys",
+           "rows": rows}
+    if corpus is not None:
+        # the retrieval call against the plain query, L2 flushed before each:
+        # what the selection adds to a query when it runs as the loop's
+        # programmatic dependent
+        def per_call(fn):
+            for _ in range(3):
+                fn()
+            ts = []
+            for _ in range(reps):
+                flush.zero_()
+                a = torch.cuda.Event(enable_timing=True)
+                b = torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                fn()
+                b.record(stream)
+                b.synchronize()
+                ts.append(a.elapsed_time(b) * 1e3)
+            return statistics.median(ts)
+        plain = per_call(lambda: corpus.query_device(dq.ids, dq.w, dq.v_r, w.lam, w.max_iter, prec,
+                                                     dq.ws, dq.ws_bytes, dq.out, stream))
+        added = []
+        for k in (10, 100):
+            idx = torch.empty(k, dtype=torch.int64, device=dq.out.device)
+            val = torch.empty(k, dtype=torch.float64, device=dq.out.device)
+            t = per_call(lambda: corpus.query_device_topk(dq.ids, dq.w, dq.v_r, w.lam, w.max_iter,
+                                                          prec, dq.ws, dq.ws_bytes, dq.out, k, idx,
+                                                          val, stream))
+            added.append({"k": k, "query_topk_us": t, "added_us": t - plain})
+        out["query_device_us"] = plain
+        out["query_device_topk"] = added
+    return out
 
 
 def bench_dense(wmd, corpus, dq, w, stream, flush, reps=5):
@@ -738,9 +788,11 @@ def run_ours(args, w):
     # profiler distorts its timings: pin the variant with --loop-variant there)
     if args.loop_variant >= 0:
         corpus.set_loop_variant(len(q_ids), args.loop_variant, prec)
+        corpus.set_loop_partition(len(q_ids), args.loop_variant, args.loop_partition)
         loop_variant = args.loop_variant
     else:
         loop_variant = corpus.autotune(q_ids, q_w, w.lam, w.max_iter, prec)
+    loop_partition = corpus.loop_partition(len(q_ids), loop_variant)
     dq = wmd.DeviceQuery(corpus, q_ids, q_w, prec)
     v_r = dq.v_r
     stream = torch.cuda.current_stream(dev)
@@ -755,8 +807,12 @@ def run_ours(args, w):
         step()
     torch.cuda.synchronize()
 
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True),
-           torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    # timed steps: the two kernels back to back, as a caller runs them (the
+    # loop kernel is a programmatic dependent of the cdist kernel and may
+    # start its CTAs while that kernel finishes; an event between the two
+    # would serialise them)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
     clocks = ClockSampler(local_rank)
     clocks.start()
     time.sleep(0.3)
@@ -765,21 +821,32 @@ def run_ours(args, w):
     torch.cuda.synchronize()
     for k in range(args.steps):
         flush.zero_()                       # L2 flush (untimed, between steps)
-        e0, e1, e2 = ev[k]
+        e0, e2 = ev[k]
+        e0.record(stream)
+        step()
+        e2.record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clk = clocks.stop()
+    step_ms = sum(a.elapsed_time(b) for a, b in ev) / args.steps
+    value, step_ms_max = replica_throughput(step_ms, c.N, world)
+
+    # per-kernel times (the roofline of each kernel) from separate steps with
+    # an event between the two kernels
+    kev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True),
+            torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    for k in range(args.steps):
+        flush.zero_()
+        e0, e1, e2 = kev[k]
         e0.record(stream)
         corpus.build_kernel_matrix(dq.ids, dq.w, v_r, w.lam, prec, dq.ws, dq.ws_bytes, stream)
         e1.record(stream)
         corpus.sinkhorn_loop(v_r, w.max_iter, prec, dq.ws, dq.ws_bytes, dq.out, stream)
         e2.record(stream)
     torch.cuda.synchronize()
-    if world > 1:
-        dist.barrier()
-    clk = clocks.stop()
-
-    cdist_ms = sum(a.elapsed_time(b) for a, b, _ in ev) / args.steps
-    loop_ms = sum(b.elapsed_time(cc) for _, b, cc in ev) / args.steps
-    step_ms = sum(a.elapsed_time(cc) for a, _, cc in ev) / args.steps
-    value, step_ms_max = replica_throughput(step_ms, c.N, world)
+    cdist_ms = sum(a.elapsed_time(b) for a, b, _ in kev) / args.steps
+    loop_ms = sum(b.elapsed_time(cc) for _, b, cc in kev) / args.steps
 
     # end to end through the public host API: pinned query in, WMD[N] out
     h_ids = torch.from_numpy(np.ascontiguousarray(q_ids)).pin_memory()
@@ -810,7 +877,7 @@ def run_ours(args, w):
     # fp16 hi + lo rows of the active vocabulary, K, norms and row scales, the query rows
     cdist_bytes = U * ldv * 4 + U * VR * kelem + U * 8 + v_r * ldv * 4
     loop_flops = 4.0 * v_r * c.nnz * (w.max_iter + 1)
-    alu_tf, num_sms = alu_peak_tflops(dev, peaks.get("sm_max_mhz", 2070.0))
+    alu_tf, alu_info = alu_peak_tflops(dev, peaks.get("sm_max_mhz", 2070.0))
     alu_peak = alu_tf * 1e12
     kernels = {
         "cdist_k": {"ms": cdist_ms, "bound": "hbm", "bytes": cdist_bytes,
@@ -829,8 +896,9 @@ def run_ours(args, w):
         ach = loop_flops / (loop_ms * 1e-3) / 1e12
         pk = alu_peak / 1e12
         roof = {"kernel": "sinkhorn_fused", "bound": "alu", "achieved": ach, "peak": pk,
-                "unit": "TFLOP/s", "frac": ach / pk, "traffic": recorded_traffic("sinkhorn_fused", w.name, loop_variant),
-                "peak_source": f"{num_sms} SMs (from the device) x 128 FP32 lanes x 2 flop x max SM clock"}
+                "unit": "TFLOP/s", "frac": ach / pk, "traffic": recorded_traffic("sinkhorn_fused", w.name, loop_variant, loop_partition),
+                "peak_source": "measured FP32 FMA rate of this GPU (wmd_measure_fp32_peak, faster of "
+                               "FFMA2 and FFMA)", "peak_detail": alu_info}
 
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -839,7 +907,8 @@ def run_ours(args, w):
         "data": "synthetic (seeded Zipf(1.1) corpus, N(0,1/d) embeddings)",
         "config": {"workload": workload_name(w), "V": w.V, "d": w.d, "N": w.N, "v_r": v_r,
                    "lambda": w.lam, "max_iter": w.max_iter, "nnz": c.nnz, "active_words": U,
-                   "loop_variant": loop_variant, "cdist_kernel": corpus.cdist_kernel,
+                   "loop_variant": loop_variant, "loop_partition": loop_partition,
+                   "cdist_kernel": corpus.cdist_kernel,
                    "l2": "flushed between steps (512 MiB write)",
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(v_r * 8),
@@ -861,7 +930,8 @@ def run_ours(args, w):
         if "converge" in legs:
             out["converge"] = bench_converge(wmd, corpus, dq, w, prec, stream, flush)
         if "topk" in legs:
-            out["topk"] = bench_topk(wmd, dq, c.N, stream)
+            out["topk"] = bench_topk(wmd, dq, c.N, stream, corpus=corpus, w=w, prec=prec,
+                                     flush=flush)
         if "dense" in legs and prec == wmd.PREC_FP32:
             out["dense"] = bench_dense(wmd, corpus, dq, w, stream, flush)
         if "large" in legs:

@@ -119,6 +119,7 @@ typedef struct wmd_corpus_info {
  *                   the tensor-core kernel cannot hold).  The environment
  *                   variable WMD_CDIST_KERNEL=simt also selects it.
  * autotune_cache    path of a text file of tuned fused-loop tile variants
+ *                   and partitions
  *                   (NULL: the environment variable WMD_AUTOTUNE_CACHE, else
  *                   no file).  wmd_corpus_load applies the entries recorded
  *                   for a corpus of the same shape (V, d, N, nnz, active
@@ -158,6 +159,17 @@ const char* wmd_last_error(void);
 
 /* Library version string. */
 const char* wmd_version(void);
+
+/* Measured FP32 fused multiply-add rate of GPU `device` in TFLOP/s (2 flops
+ * per FMA), the roof of the fused Sinkhorn loop, which is bound by FP32
+ * issue (Sec. 3's SDDMM and SpMM are one FMA per K element each).  packed = 0
+ * times scalar FFMA, packed != 0 packed float2 FFMA2.  Runs a few launches of
+ * a register-only kernel on a private stream of that device (about 10 ms in
+ * all; the calling thread's current device is restored) and reports the
+ * fastest.  *tflops is written on success only.  Errors: WMD_ERR_INVALID_ARG
+ * (null tflops, device out of range), WMD_ERR_CUDA, WMD_ERR_OUT_OF_MEMORY is
+ * reported as WMD_ERR_CUDA (4 bytes per CTA of scratch). */
+wmd_status wmd_measure_fp32_peak(int32_t device, int32_t packed, double* tflops);
 
 /* ---------------------------------------------------------------------------
  * Query compaction (Algorithm 1, the selection I = (r > 0)).  Host only, no GPU.
@@ -400,17 +412,41 @@ wmd_status wmd_query_dense(wmd_corpus* corpus, const int32_t* d_q_ids, const flo
  * this corpus (all later calls; not thread-safe against running queries).
  * wmd_get_loop_variant: the variant in use for v_r's class and `prec` (-1
  * for a NULL corpus, v_r out of range or an unknown precision).
+ *
+ * Partition (the paper's split of the documents over threads, Sec. 3, here
+ * over warps): documents are taken in decreasing length and a document of n
+ * words gets a team of W warps, the smallest power of two (up to the tile
+ * variant's warps per CTA) with n <= W x rows_per_warp x fill / 100.
+ * fill = 100 (the default) is the fewest warps that keep the document's K
+ * block in registers; 75 and 50 spread documents over more warps; 200 gives
+ * long documents half the warps, which then re-read chunks of K from L2
+ * each pass.  The partition belongs to a class and tile variant (both
+ * precisions).  wmd_set_loop_partition: rebuild the work items of v_r's
+ * class and `variant` with `fill` (50, 75, 100 or 200; else
+ * WMD_ERR_INVALID_ARG); waits for all work on the device first and drops
+ * the corpus's captured CUDA graphs.  wmd_get_loop_partition: the fill in
+ * use (-1 for a NULL corpus or an invalid class or variant).  Results of
+ * different partitions agree within rounding (the sums across warps run in
+ * another order).
+ *
  * wmd_autotune: synchronous; builds K for the given query (host buffers, as
- * wmd_query), times every variant of its class on this corpus with CUDA
- * events, keeps the fastest for that class and precision and writes its
- * index to *chosen (may be NULL).  Allocates a temporary workspace.  With an
- * autotune cache (wmd_options) the choice is appended to the cache file, and
- * corpora of the same shape loaded later start from it.
+ * wmd_query), times every variant of its class with every partition on
+ * this corpus with CUDA events, keeps the fastest partition for each
+ * variant and the fastest variant for that class and precision, and writes
+ * the variant's index to *chosen (may be NULL).  Allocates a temporary
+ * workspace; waits for all work on the device first and drops the corpus's
+ * captured CUDA graphs, and must not overlap other calls on the corpus.
+ * With an autotune cache (wmd_options) the choice (variant and partition)
+ * is appended to the cache file, and corpora of the same shape loaded later
+ * start from it.
  * ------------------------------------------------------------------------- */
 int32_t wmd_loop_variant_count(int32_t v_r);
 wmd_status wmd_set_loop_variant(wmd_corpus* corpus, int32_t v_r, wmd_precision prec,
                                 int32_t variant);
 int32_t wmd_get_loop_variant(const wmd_corpus* corpus, int32_t v_r, wmd_precision prec);
+wmd_status wmd_set_loop_partition(wmd_corpus* corpus, int32_t v_r, int32_t variant,
+                                  int32_t fill);
+int32_t wmd_get_loop_partition(const wmd_corpus* corpus, int32_t v_r, int32_t variant);
 wmd_status wmd_autotune(wmd_corpus* corpus, const int32_t* q_ids, const float* q_w,
                         int32_t n_q, float lambda, int32_t max_iter, wmd_precision prec,
                         int32_t* chosen);

@@ -20,7 +20,7 @@ LIB = os.path.join(HERE, "libwmd_gb300.so")
 ROOT = os.path.dirname(HERE)
 
 SOURCES = ["api.cu", "cdist.cu", "cdist_tc.cu", "sinkhorn.cu", "sinkhorn_conv.cu", "serve.cu",
-           "topk.cu", "dense.cu", "noalloc.cu"]
+           "topk.cu", "dense.cu", "noalloc.cu", "peak.cu"]
 # cuBLAS serves the dense comparator's two plain GEMMs (dense.cu)
 LIBS = ["-lcublas", "-Xlinker", "-rpath,/usr/local/cuda/lib64"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

@@ -66,9 +66,69 @@ void free_corpus_device(wmd_corpus* c) {
   if (c->stream) cudaStreamDestroy(c->stream);
 }
 
+// ---------------------------------------------------------------- schedules
+// The CTA work items of class `cls`, tile variant `var`, partition `fill`:
+// documents in decreasing length, each with the smallest team allowed by
+// the partition (see kFills); a CTA's NW / W teams take consecutive
+// documents of one team size.  Replaces the class's previous schedule; the
+// caller makes sure that no launch still reads it.
+cudaError_t build_schedule(wmd_corpus* c, int cls, int var, int fill) {
+  const std::vector<int64_t>& dptr = c->h_dptr;
+  const std::vector<int32_t>& order = c->h_order;
+  const int64_t N = c->N;
+  const int64_t rpw = rows_per_warp(cls, var);
+  const int nw = warps_per_cta(cls, var);
+  auto team = [&](int64_t n) {
+    int W = 1;
+    while (W < nw && n * 100 > W * rpw * fill) W *= 2;
+    return W;
+  };
+  std::vector<WarpTask> tasks;
+  int32_t n_items = 0;
+  int64_t i = 0;
+  while (i < N) {
+    const int W = team(dptr[order[i] + 1] - dptr[order[i]]);
+    const int per = nw / W;
+    int64_t j = i;
+    while (j < N && team(dptr[order[j] + 1] - dptr[order[j]]) == W) ++j;
+    for (int64_t b = i; b < j; b += per, ++n_items) {
+      for (int warp = 0; warp < nw; ++warp) {
+        const int64_t slot = b + warp / W;
+        if (slot < std::min<int64_t>(b + per, j)) {
+          const int32_t d = order[slot];
+          const int32_t len = (int32_t)(dptr[d + 1] - dptr[d]);
+          tasks.push_back(WarpTask{dptr[d], len | (W << kTaskWShift), d});
+        } else {
+          tasks.push_back(WarpTask{0, 0, 0});
+        }
+      }
+    }
+    i = j;
+  }
+  Schedule& sc = c->sched[cls][var];
+  if (sc.d_tasks) {
+    c->device_bytes -= std::max<size_t>(size_t(sc.n_items) * nw, 1) * sizeof(WarpTask);
+    cudaFree(sc.d_tasks);
+    sc.d_tasks = nullptr;
+  }
+  sc.n_items = n_items;
+  sc.fill = fill;
+  return upload(&sc.d_tasks, tasks.data(), tasks.size(), &c->device_bytes);
+}
+
+// Drops everything that captured a schedule's address: the host path's CUDA
+// graphs and the batch path's cached graphs.
+void drop_captured(wmd_corpus* c) {
+  for (auto& g : c->qgraphs)
+    if (g.exec) cudaGraphExecDestroy(g.exec);
+  c->qgraphs.clear();
+  release_batch_state(c);
+}
+
 // ---------------------------------------------------------------- autotune cache
-// One line per tuned choice: "wmd-loop V d N nnz U class precision variant".
-// A corpus applies the lines recorded for its own shape; the last one wins.
+// One line per tuned choice: "wmd-loop V d N nnz U class precision variant
+// fill" (fill: the partition; lines without it mean 100).  A corpus applies
+// the lines recorded for its own shape; the last one wins.
 void load_autotune_cache(wmd_corpus* c) {
   if (c->autotune_cache.empty()) return;
   FILE* f = std::fopen(c->autotune_cache.c_str(), "r");
@@ -76,15 +136,16 @@ void load_autotune_cache(wmd_corpus* c) {
   char line[256];
   while (std::fgets(line, sizeof line, f)) {
     long long V, N, nnz, U;
-    int d, cls, prec, var;
-    if (std::sscanf(line, "wmd-loop %lld %d %lld %lld %lld %d %d %d", &V, &d, &N, &nnz, &U, &cls,
-                    &prec, &var) != 8)
-      continue;
+    int d, cls, prec, var, fill = 100;
+    const int got = std::sscanf(line, "wmd-loop %lld %d %lld %lld %lld %d %d %d %d", &V, &d, &N,
+                                &nnz, &U, &cls, &prec, &var, &fill);
+    if (got != 8 && got != 9) continue;  // lines without a partition keep fill = 100
     if (V != c->V || d != c->d || N != c->N || nnz != c->nnz || U != c->U) continue;
     if (cls < 0 || cls >= kNumClasses || prec < 0 || prec > 1 || var < 0 ||
-        var >= kClassVariants[cls])
+        var >= kClassVariants[cls] || !valid_fill(fill))
       continue;
     c->loop_variant[cls][prec] = var;
+    if (c->sched[cls][var].fill != fill && build_schedule(c, cls, var, fill) != cudaSuccess) break;
   }
   std::fclose(f);
 }
@@ -95,8 +156,9 @@ void save_autotune_choice(const wmd_corpus* c, int cls, int prec, int var) {
   std::lock_guard<std::mutex> lock(mu);
   FILE* f = std::fopen(c->autotune_cache.c_str(), "a");
   if (!f) return;
-  std::fprintf(f, "wmd-loop %lld %d %lld %lld %lld %d %d %d\n", (long long)c->V, (int)c->d,
-               (long long)c->N, (long long)c->nnz, (long long)c->U, cls, prec, var);
+  std::fprintf(f, "wmd-loop %lld %d %lld %lld %lld %d %d %d %d\n", (long long)c->V, (int)c->d,
+               (long long)c->N, (long long)c->nnz, (long long)c->U, cls, prec, var,
+               (int)c->sched[cls][var].fill);
   std::fclose(f);
 }
 
@@ -391,46 +453,14 @@ wmd_status wmd_corpus_load(const float* vecs, int64_t V, int32_t d, const int64_
   // allocating is allowed anyway (its first query then allocates nothing)
   if (e == cudaSuccess) e = noalloc_reserve(device);
 
-  // per query-width class and tile variant: team size per document and CTA
-  // work items (a CTA's 4/W teams take consecutive documents of one team size)
-  for (int cls = 0; cls < kNumClasses && e == cudaSuccess; ++cls) {
-    for (int var = 0; var < kClassVariants[cls] && e == cudaSuccess; ++var) {
-      const int64_t rpw = rows_per_warp(cls, var);
-      const int nw = warps_per_cta(cls, var);
-      // the smallest team that keeps the document resident, else the widest
-      auto team = [&](int64_t n) {
-        int W = 1;
-        while (W < nw && n > W * rpw) W *= 2;
-        return W;
-      };
-      std::vector<WarpTask> tasks;
-      int32_t n_items = 0;
-      int64_t i = 0;
-      while (i < N) {
-        const int64_t n = dptr[order[i] + 1] - dptr[order[i]];
-        const int W = team(n);
-        const int per = nw / W;
-        int64_t j = i;
-        while (j < N && team(dptr[order[j] + 1] - dptr[order[j]]) == W) ++j;
-        for (int64_t b = i; b < j; b += per, ++n_items) {
-          for (int warp = 0; warp < nw; ++warp) {
-            const int64_t slot = b + warp / W;
-            if (slot < std::min<int64_t>(b + per, j)) {
-              const int32_t d = order[slot];
-              const int32_t len = (int32_t)(dptr[d + 1] - dptr[d]);
-              tasks.push_back(WarpTask{dptr[d], len | (W << kTaskWShift), d});
-            } else {
-              tasks.push_back(WarpTask{0, 0, 0});
-            }
-          }
-        }
-        i = j;
-      }
-      c->sched[cls][var].n_items = n_items;
-      e = upload(&c->sched[cls][var].d_tasks, tasks.data(), tasks.size(), &bytes);
-    }
-  }
+  // per query-width class and tile variant: the CTA work items of the
+  // default partition (fill = 100)
   c->device_bytes = bytes;
+  c->h_dptr = std::move(dptr);
+  c->h_order = std::move(order);
+  for (int cls = 0; cls < kNumClasses && e == cudaSuccess; ++cls)
+    for (int var = 0; var < kClassVariants[cls] && e == cudaSuccess; ++var)
+      e = build_schedule(c, cls, var, 100);
   if (e != cudaSuccess) {
     wmd_status st = cuda_error(e, "corpus upload");
     free_corpus_device(c);
@@ -685,6 +715,29 @@ wmd_status wmd_set_loop_variant(wmd_corpus* c, int32_t v_r, wmd_precision prec, 
   return WMD_OK;
 }
 
+wmd_status wmd_set_loop_partition(wmd_corpus* c, int32_t v_r, int32_t variant, int32_t fill) {
+  if (!c) return set_error(WMD_ERR_INVALID_ARG, "corpus is NULL");
+  const int cls = v_r > 0 ? vr_class(v_r) : -1;
+  if (cls < 0) return set_error(WMD_ERR_INVALID_ARG, "v_r out of range");
+  if (variant < 0 || variant >= kClassVariants[cls])
+    return set_error(WMD_ERR_INVALID_ARG, "no such variant for this query width");
+  if (!valid_fill(fill)) return set_error(WMD_ERR_INVALID_ARG, "fill must be 50, 75, 100 or 200");
+  if (c->sched[cls][variant].fill == fill) return WMD_OK;
+  DeviceGuard g(c->device);
+  std::lock_guard<std::mutex> lock(c->mu);
+  // the old work items may still be read by launches in flight on any stream
+  WMD_CUDA_TRY(cudaDeviceSynchronize());
+  drop_captured(c);
+  WMD_CUDA_TRY(build_schedule(c, cls, variant, fill));
+  return WMD_OK;
+}
+
+int32_t wmd_get_loop_partition(const wmd_corpus* c, int32_t v_r, int32_t variant) {
+  const int cls = v_r > 0 ? vr_class(v_r) : -1;
+  if (!c || cls < 0 || variant < 0 || variant >= kClassVariants[cls]) return -1;
+  return c->sched[cls][variant].fill;
+}
+
 int32_t wmd_get_loop_variant(const wmd_corpus* c, int32_t v_r, wmd_precision prec) {
   const int cls = v_r > 0 ? vr_class(v_r) : -1;
   if (!c || cls < 0 || (prec != WMD_PREC_FP32 && prec != WMD_PREC_BF16_K)) return -1;
@@ -705,6 +758,12 @@ wmd_status wmd_autotune(wmd_corpus* c, const int32_t* q_ids, const float* q_w, i
     return set_error(WMD_ERR_INVALID_ARG, "unknown precision");
   const int cls = vr_class(v_r);
   DeviceGuard g(c->device);
+  // the timed partitions replace the class's work items: nothing else may
+  // use the corpus meanwhile (the host path waits on the lock), and launches
+  // in flight on other streams finish first
+  std::lock_guard<std::mutex> lock(c->mu);
+  WMD_CUDA_TRY(cudaDeviceSynchronize());
+  drop_captured(c);
   const size_t ws_bytes = wmd_workspace_bytes(c, v_r, prec);
   void* ws = nullptr;
   int32_t* d_ids = nullptr;
@@ -724,27 +783,47 @@ wmd_status wmd_autotune(wmd_corpus* c, const int32_t* q_ids, const float* q_w, i
   if (e == cudaSuccess) e = cudaMemcpyAsync(d_ids, ids.data(), v_r * sizeof(int32_t), cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess) e = cudaMemcpyAsync(d_w, w.data(), v_r * sizeof(float), cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess) {
+    // every tile variant of the class with every partition: the fastest
+    // partition stays with each variant, the fastest pair is chosen
     st = wmd_build_kernel_matrix(c, d_ids, d_w, v_r, lambda, prec, ws, ws_bytes, s);
-    const int keep = c->loop_variant[cls][prec == WMD_PREC_BF16_K];
+    const int pi = prec == WMD_PREC_BF16_K;
+    const int keep = c->loop_variant[cls][pi];
+    float best_var_ms[kMaxVariants] = {};
     for (int var = 0; var < kClassVariants[cls] && st == WMD_OK && e == cudaSuccess; ++var) {
-      c->loop_variant[cls][prec == WMD_PREC_BF16_K] = var;
-      for (int k = 0; k < 2 && st == WMD_OK; ++k)
-        st = wmd_sinkhorn_loop(c, v_r, max_iter, prec, ws, ws_bytes, d_out, s);
-      if (st != WMD_OK) break;
-      e = cudaEventRecord(e0, s);
-      for (int k = 0; k < 5 && st == WMD_OK; ++k)
-        st = wmd_sinkhorn_loop(c, v_r, max_iter, prec, ws, ws_bytes, d_out, s);
-      if (e == cudaSuccess) e = cudaEventRecord(e1, s);
-      if (e == cudaSuccess) e = cudaEventSynchronize(e1);
-      float ms = 0.f;
-      if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
-      if (e == cudaSuccess && (var == 0 || ms < best_ms)) {
-        best_ms = ms;
+      c->loop_variant[cls][pi] = var;
+      int best_fill = c->sched[cls][var].fill;
+      for (int fi = 0; fi < kNumFills && st == WMD_OK && e == cudaSuccess; ++fi) {
+        if (c->sched[cls][var].fill != kFills[fi]) {
+          e = cudaStreamSynchronize(s);
+          if (e == cudaSuccess) e = build_schedule(c, cls, var, kFills[fi]);
+          if (e != cudaSuccess) break;
+        }
+        for (int k = 0; k < 2 && st == WMD_OK; ++k)
+          st = wmd_sinkhorn_loop(c, v_r, max_iter, prec, ws, ws_bytes, d_out, s);
+        if (st != WMD_OK) break;
+        e = cudaEventRecord(e0, s);
+        for (int k = 0; k < 5 && st == WMD_OK; ++k)
+          st = wmd_sinkhorn_loop(c, v_r, max_iter, prec, ws, ws_bytes, d_out, s);
+        if (e == cudaSuccess) e = cudaEventRecord(e1, s);
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        float ms = 0.f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+        if (e == cudaSuccess && (fi == 0 || ms < best_var_ms[var])) {
+          best_var_ms[var] = ms;
+          best_fill = kFills[fi];
+        }
+      }
+      if (st == WMD_OK && e == cudaSuccess && c->sched[cls][var].fill != best_fill) {
+        e = cudaStreamSynchronize(s);
+        if (e == cudaSuccess) e = build_schedule(c, cls, var, best_fill);
+      }
+      if (st == WMD_OK && e == cudaSuccess && (var == 0 || best_var_ms[var] < best_ms)) {
+        best_ms = best_var_ms[var];
         best = var;
       }
     }
-    c->loop_variant[cls][prec == WMD_PREC_BF16_K] = (st == WMD_OK && e == cudaSuccess) ? best : keep;
-    if (st == WMD_OK && e == cudaSuccess) save_autotune_choice(c, cls, prec == WMD_PREC_BF16_K, best);
+    c->loop_variant[cls][pi] = (st == WMD_OK && e == cudaSuccess) ? best : keep;
+    if (st == WMD_OK && e == cudaSuccess) save_autotune_choice(c, cls, pi, best);
   }
   if (s) cudaStreamSynchronize(s);
   if (e0) cudaEventDestroy(e0);

@@ -615,6 +615,10 @@ __global__ void __launch_bounds__(NW * 32, MINB) sinkhorn_fused_kernel(LoopParam
   __shared__ __align__(16) float wpart[VR <= 32 ? NW * (PW + 1) * wpart_stride(VR, PI) : 4];
   __shared__ double wred[NW];
 
+  // a programmatic dependent of this launch (the top-k selection, or the
+  // next width class of a batch) may start once every CTA of this grid has
+  // started; it waits for this grid's results itself
+  asm volatile("griddepcontrol.launch_dependents;");
   TeamCtx t;
   t.warp = threadIdx.x >> 5;
   t.lane = threadIdx.x & 31;

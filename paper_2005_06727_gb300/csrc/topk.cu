@@ -53,6 +53,18 @@ __device__ __forceinline__ unsigned long long order_key(unsigned long long b) {
   return (b >> 63) ? ~b : (b | 0x8000000000000000ull);
 }
 
+// WMD[] is written by the kernel before this one in the stream, which may
+// still run when this kernel starts (programmatic dependent launch): wait for
+// it, then read the values with ordinary coherent loads kept in order with
+// the wait (volatile asm; no __ldg, whose data must be read-only for the
+// kernel's lifetime).
+__device__ __forceinline__ void wait_for_values() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ unsigned long long ld_bits(const unsigned long long* a) {
+  unsigned long long v;
+  asm volatile("ld.global.u64 %0, [%1];" : "=l"(v) : "l"(a));
+  return v;
+}
+
 // Block-wide exclusive prefix count of `flag` (every thread calls it);
 // returns this thread's rank and writes the block total to *total.
 template <int NT>
@@ -84,7 +96,7 @@ __device__ __forceinline__ unsigned block_rank(bool flag, unsigned* warp_sums, u
 // collectives inside `f` are safe).  The set is either the whole array
 // filtered by (key & mask) == prefix (full) or an explicit index list.
 template <bool CACHED, int NT, typename F>
-__device__ __forceinline__ void sweep(const unsigned long long* __restrict__ bits,
+__device__ __forceinline__ void sweep(const unsigned long long* bits,
                                       const unsigned long long* cache,
                                       int64_t N, bool full, const int* list, unsigned nlist,
                                       unsigned long long mask, unsigned long long prefix, F&& f) {
@@ -96,7 +108,7 @@ __device__ __forceinline__ void sweep(const unsigned long long* __restrict__ bit
     for (int u = 0; u < kUnroll; ++u) {
       const int64_t t = base + u * NT + threadIdx.x;
       idx[u] = t < n ? (full ? t : (int64_t)list[t]) : -1;
-      key[u] = idx[u] >= 0 ? (CACHED ? cache[idx[u]] : order_key(__ldg(bits + idx[u]))) : ~0ull;
+      key[u] = idx[u] >= 0 ? (CACHED ? cache[idx[u]] : order_key(ld_bits(bits + idx[u]))) : ~0ull;
     }
 #pragma unroll
     for (int u = 0; u < kUnroll; ++u) {
@@ -108,7 +120,7 @@ __device__ __forceinline__ void sweep(const unsigned long long* __restrict__ bit
 
 template <bool CACHED, int NT>
 __global__ void __launch_bounds__(NT, 1)
-    topk_kernel(const double* __restrict__ wmd, int64_t N, int k, int64_t* __restrict__ out_idx,
+    topk_kernel(const double* wmd, int64_t N, int k, int64_t* __restrict__ out_idx,
                 double* __restrict__ out_val) {
   // dynamic: [N keys if CACHED][two candidate lists of kCandMax indices]
   extern __shared__ __align__(16) unsigned char dyn[];
@@ -124,8 +136,9 @@ __global__ void __launch_bounds__(NT, 1)
   __shared__ unsigned long long s_key[kTopkMaxK];
   __shared__ long long s_idx[kTopkMaxK];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  wait_for_values();
   const unsigned long long* bits = reinterpret_cast<const unsigned long long*>(wmd);
-  auto key_at = [&](int64_t i) { return CACHED ? cache[i] : order_key(__ldg(bits + i)); };
+  auto key_at = [&](int64_t i) { return CACHED ? cache[i] : order_key(ld_bits(bits + i)); };
 
   // 1. smallest and largest key (and the shared-memory copy of the keys)
   unsigned long long kmin = ~0ull, kmax = 0;
@@ -134,7 +147,7 @@ __global__ void __launch_bounds__(NT, 1)
 #pragma unroll
     for (int u = 0; u < kUnroll; ++u) {
       const int64_t i = base + u * NT + tid;
-      key[u] = i < N ? order_key(__ldg(bits + i)) : ~0ull;
+      key[u] = i < N ? order_key(ld_bits(bits + i)) : ~0ull;
     }
 #pragma unroll
     for (int u = 0; u < kUnroll; ++u) {
@@ -379,6 +392,253 @@ __global__ void __launch_bounds__(NT, 1)
   }
 }
 
+// ---------------------------------------------------------------- small N, k <= 256
+// N <= kSmallThreads * kSmallE keys, kept in registers: thread t holds keys
+// t E ... t E + E - 1 (E = ceil(N / 1024), a compile-time count so that no
+// loop over a thread's keys runs empty slots), and thread order is
+// document order.
+// A radix select on 11-bit digits of key - (smallest key), most significant
+// first from the top bit of the range (largest - smallest): the first pass
+// spreads the keys over all 2048 bins whatever their exponents, and usually
+// leaves the k-th key's bin with a few keys, which are then ranked by
+// (key, id) directly; repeated exact ties fall through to document order.
+// About ten barriers in all, against two sweeps per 8-bit pass above.
+constexpr int kSmallThreads = 512;
+constexpr int kSmallE = 32;        // keys per thread at most (one instance per count)
+constexpr int kSmallBits = 10;
+constexpr int kSmallBins = 1 << kSmallBits;
+constexpr int kSmallCand = 64;     // candidates ranked directly (16 threads each)
+constexpr int64_t kSmallMaxN = (int64_t)kSmallThreads * kSmallE;
+static_assert(kSmallBins == 2 * kSmallThreads, "two bins per thread in the scan");
+static_assert(kSmallCand * 8 == kSmallThreads && kRankSortMax * 2 == kSmallThreads, "rank split");
+
+__device__ __forceinline__ bool before(unsigned long long ka, int ia, unsigned long long kb, int ib) {
+  return ka < kb || (ka == kb && ia < ib);
+}
+
+template <int E>
+__global__ void __launch_bounds__(kSmallThreads, 1)
+    topk_small_kernel(const double* wmd, int N, int k, int64_t* out_idx, double* out_val) {
+  __shared__ unsigned hist[kSmallBins];
+  constexpr int kW = kSmallThreads / 32;
+  __shared__ unsigned warp_sums[kW];
+  __shared__ unsigned long long s_min[kW], s_max[kW];
+  __shared__ unsigned s_sel[3];   // bin, keys below it, keys in it
+  __shared__ unsigned s_taken, s_ncand;
+  __shared__ unsigned long long s_key[kRankSortMax];
+  __shared__ int s_idx[kRankSortMax];
+  __shared__ unsigned long long c_key[kSmallCand];
+  __shared__ int c_idx[kSmallCand];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int i0 = tid * E;
+
+  hist[2 * tid] = 0;
+  hist[2 * tid + 1] = 0;
+  if (tid == 0) {
+    s_taken = 0;
+    s_ncand = 0;
+  }
+  wait_for_values();
+  const unsigned long long* bits = reinterpret_cast<const unsigned long long*>(wmd);
+  unsigned long long key[E];
+  unsigned valid = 0;  // bit e: key e exists
+  unsigned long long kmin = ~0ull, kmax = 0;
+#pragma unroll
+  for (int e = 0; e < E; ++e) {
+    const bool v = i0 + e < N;
+    key[e] = v ? order_key(ld_bits(bits + i0 + e)) : ~0ull;
+    valid |= (v ? 1u : 0u) << e;
+    if (v) {
+      kmin = key[e] < kmin ? key[e] : kmin;
+      kmax = key[e] > kmax ? key[e] : kmax;
+    }
+  }
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    const unsigned long long a = __shfl_xor_sync(0xffffffffu, kmin, off);
+    const unsigned long long b = __shfl_xor_sync(0xffffffffu, kmax, off);
+    kmin = a < kmin ? a : kmin;
+    kmax = b > kmax ? b : kmax;
+  }
+  if (lane == 0) {
+    s_min[warp] = kmin;
+    s_max[warp] = kmax;
+  }
+  __syncthreads();
+  kmin = lane < kW ? s_min[lane] : ~0ull;  // a full butterfly: every lane gets the total
+  kmax = lane < kW ? s_max[lane] : 0ull;
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    const unsigned long long a = __shfl_xor_sync(0xffffffffu, kmin, off);
+    const unsigned long long b = __shfl_xor_sync(0xffffffffu, kmax, off);
+    kmin = a < kmin ? a : kmin;
+    kmax = b > kmax ? b : kmax;
+  }
+  // from here on the keys are offsets from the smallest (same order)
+#pragma unroll
+  for (int e = 0; e < E; ++e) key[e] -= kmin;
+  const unsigned long long range = kmax - kmin;
+
+  unsigned cm = valid;  // bit e: key e is a candidate (matches the decided prefix)
+  int hi = range == 0 ? 0 : 64 - __clzll((long long)range);  // undecided low bits
+  unsigned long long mask = hi == 64 ? 0ull : ~((1ull << hi) - 1ull);
+  unsigned long long prefix = 0;
+  unsigned need = (unsigned)k;  // rank of the k-th key among the candidates
+  unsigned ncand = (unsigned)N;
+  while (hi > 0 && ncand > (unsigned)kSmallCand) {
+    const int width = hi < kSmallBits ? hi : kSmallBits;
+    const int shift = hi - width;
+    const unsigned dmask = (1u << width) - 1u;
+#pragma unroll
+    for (int e = 0; e < E; ++e)
+      if ((cm >> e) & 1u) atomicAdd(&hist[(unsigned)(key[e] >> shift) & dmask], 1u);
+    __syncthreads();
+    // block-wide scan of the bins (thread t: bins 2t and 2t + 1); the thread
+    // whose bins hold the need-th candidate publishes its bin
+    const unsigned h0 = hist[2 * tid], h1 = hist[2 * tid + 1];
+    hist[2 * tid] = 0;  // only this thread reads them in this pass
+    hist[2 * tid + 1] = 0;
+    const unsigned sum = h0 + h1;
+    unsigned incl = sum;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+      const unsigned o = __shfl_up_sync(0xffffffffu, incl, off);
+      if (lane >= off) incl += o;
+    }
+    if (lane == 31) warp_sums[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+      const unsigned v = lane < kW ? warp_sums[lane] : 0u;
+      unsigned w = v;
+#pragma unroll
+      for (int off = 1; off < kW; off <<= 1) {
+        const unsigned o = __shfl_up_sync(0xffffffffu, w, off);
+        if (lane >= off) w += o;
+      }
+      if (lane < kW) warp_sums[lane] = w - v;  // exclusive
+    }
+    __syncthreads();
+    const unsigned excl = warp_sums[warp] + incl - sum;
+    if (excl < need && need <= excl + h0) {
+      s_sel[0] = 2 * tid;
+      s_sel[1] = excl;
+      s_sel[2] = h0;
+    } else if (excl + h0 < need && need <= excl + sum) {
+      s_sel[0] = 2 * tid + 1;
+      s_sel[1] = excl + h0;
+      s_sel[2] = h1;
+    }
+    __syncthreads();
+    const unsigned bin = s_sel[0];
+    need -= s_sel[1];
+    ncand = s_sel[2];
+    prefix |= (unsigned long long)bin << shift;
+    mask |= (unsigned long long)dmask << shift;
+    hi = shift;
+#pragma unroll
+    for (int e = 0; e < E; ++e)
+      if (((unsigned)(key[e] >> shift) & dmask) != bin) cm &= ~(1u << e);
+    // warp_sums and s_sel are rewritten only after the next pass's first
+    // barrier, which every thread reaches after reading them
+  }
+
+  // the keys below the decided prefix are among the k; the candidates (keys
+  // equal to it in the decided bits) supply the last `need` by (key, id)
+  const unsigned base = (unsigned)k - need;
+#pragma unroll
+  for (int e = 0; e < E; ++e) {
+    if (((valid >> e) & 1u) && (key[e] & mask) < prefix) {
+      const unsigned slot = atomicAdd(&s_taken, 1u);
+      if (slot < (unsigned)kRankSortMax) {  // always: fewer than k lie below
+        s_key[slot] = key[e];
+        s_idx[slot] = i0 + e;
+      }
+    }
+  }
+  if (ncand <= (unsigned)kSmallCand) {
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+      if ((cm >> e) & 1u) {
+        const unsigned p = atomicAdd(&s_ncand, 1u);
+        if (p < (unsigned)kSmallCand) {
+          c_key[p] = key[e];
+          c_idx[p] = i0 + e;
+        }
+      }
+    }
+    __syncthreads();
+    // candidate tid / 8, its rank summed over 8 threads
+    const unsigned m = s_ncand < (unsigned)kSmallCand ? s_ncand : (unsigned)kSmallCand;
+    const unsigned c = (unsigned)tid >> 3, part = (unsigned)tid & 7u;
+    unsigned long long kt = 0;
+    int it = 0;
+    unsigned r = 0;
+    if (c < m) {
+      kt = c_key[c];
+      it = c_idx[c];
+      for (unsigned j = part; j < m; j += 8) r += before(c_key[j], c_idx[j], kt, it) ? 1u : 0u;
+    }
+#pragma unroll
+    for (int off = 1; off < 8; off <<= 1) r += __shfl_xor_sync(0xffffffffu, r, off);
+    if (c < m && part == 0 && r < need && base + r < (unsigned)kRankSortMax) {
+      s_key[base + r] = kt;
+      s_idx[base + r] = it;
+    }
+  } else {
+    // every bit decided and more than kSmallCand keys equal to the k-th:
+    // the lowest document ids win; thread order is document order, so a
+    // block-wide prefix count of each thread's candidates ranks them
+    const unsigned mine = __popc(cm);
+    unsigned incl = mine;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+      const unsigned o = __shfl_up_sync(0xffffffffu, incl, off);
+      if (lane >= off) incl += o;
+    }
+    if (lane == 31) warp_sums[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+      const unsigned v = lane < kW ? warp_sums[lane] : 0u;
+      unsigned w = v;
+#pragma unroll
+      for (int off = 1; off < kW; off <<= 1) {
+        const unsigned o = __shfl_up_sync(0xffffffffu, w, off);
+        if (lane >= off) w += o;
+      }
+      if (lane < kW) warp_sums[lane] = w - v;
+    }
+    __syncthreads();
+    unsigned r = warp_sums[warp] + incl - mine;
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+      if ((cm >> e) & 1u) {
+        if (r < need && base + r < (unsigned)kRankSortMax) {
+          s_key[base + r] = key[e];
+          s_idx[base + r] = i0 + e;
+        }
+        ++r;
+      }
+    }
+  }
+  __syncthreads();
+
+  // the k taken, ordered by (key, document id): entry tid / 2, its rank
+  // summed over 2 threads
+  const int en = tid >> 1, part = tid & 1;
+  unsigned long long kt = 0;
+  int it = 0, rank = 0;
+  if (en < k) {
+    kt = s_key[en];
+    it = s_idx[en];
+    for (int j = part; j < k; j += 2) rank += before(s_key[j], s_idx[j], kt, it) ? 1 : 0;
+  }
+  rank += __shfl_xor_sync(0xffffffffu, rank, 1);
+  if (en < k && part == 0) {
+    out_idx[rank] = it;
+    out_val[rank] = (it >= 0 && it < N) ? wmd[it] : __longlong_as_double(0x7ff8000000000000ll);
+  }
+}
+
 }  // namespace
 
 cudaError_t launch_topk(const double* wmd, int64_t N, int k, int64_t* out_idx, double* out_val,
@@ -396,15 +656,43 @@ cudaError_t launch_topk(const double* wmd, int64_t N, int k, int64_t* out_idx, d
                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lists);
   });
   if (attr_err != cudaSuccess) return attr_err;
-  if (N <= kCacheMax) {
-    topk_kernel<true, kThreadsCached>
-        <<<1, kThreadsCached, (size_t)N * sizeof(unsigned long long) + lists, s>>>(wmd, N, k,
-                                                                                 out_idx, out_val);
-  } else {
-    topk_kernel<false, kThreadsStream><<<1, kThreadsStream, lists, s>>>(wmd, N, k, out_idx,
-                                                                       out_val);
+  // programmatic dependent launch: the CTA may become resident while the
+  // kernel that writes WMD[] (the fused loop) drains; it waits for it first
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(1);
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  if (N <= kSmallMaxN && k <= kRankSortMax) {
+    cfg.blockDim = dim3(kSmallThreads);
+    cfg.dynamicSmemBytes = 0;
+    const int n = (int)N;
+    const int e = (n + kSmallThreads - 1) / kSmallThreads;
+    auto go = [&](auto kern) { return cudaLaunchKernelEx(&cfg, kern, wmd, n, k, out_idx, out_val); };
+    if (e <= 1) return go(topk_small_kernel<1>);
+    if (e <= 2) return go(topk_small_kernel<2>);
+    if (e <= 3) return go(topk_small_kernel<3>);
+    if (e <= 4) return go(topk_small_kernel<4>);
+    if (e <= 6) return go(topk_small_kernel<6>);
+    if (e <= 8) return go(topk_small_kernel<8>);
+    if (e <= 10) return go(topk_small_kernel<10>);
+    if (e <= 12) return go(topk_small_kernel<12>);
+    if (e <= 16) return go(topk_small_kernel<16>);
+    if (e <= 20) return go(topk_small_kernel<20>);
+    if (e <= 24) return go(topk_small_kernel<24>);
+    return go(topk_small_kernel<32>);
   }
-  return cudaGetLastError();
+  if (N <= kCacheMax) {
+    cfg.blockDim = dim3(kThreadsCached);
+    cfg.dynamicSmemBytes = (size_t)N * sizeof(unsigned long long) + lists;
+    return cudaLaunchKernelEx(&cfg, topk_kernel<true, kThreadsCached>, wmd, N, k, out_idx, out_val);
+  }
+  cfg.blockDim = dim3(kThreadsStream);
+  cfg.dynamicSmemBytes = lists;
+  return cudaLaunchKernelEx(&cfg, topk_kernel<false, kThreadsStream>, wmd, N, k, out_idx, out_val);
 }
 
 }  // namespace wmd

@@ -65,9 +65,25 @@ struct WarpTask {
 };
 constexpr int kTaskWShift = 24;
 
+// The partition of the documents into teams: a document of n words gets the
+// smallest team of W warps (W = 1, 2, 4, ... up to the CTA's warps) with
+// n <= W x rows_per_warp x fill / 100.  fill = 100 keeps every document that
+// fits in registers resident with as few warps as possible; below 100 spreads
+// documents over more warps (fewer rows per warp, more cross-warp sums);
+// above 100 gives long documents fewer warps, which then re-read chunks of K
+// from L2 each pass.  The autotuner picks one per class and tile variant.
+constexpr int kNumFills = 4;
+constexpr int kFills[kNumFills] = {100, 75, 50, 200};
+inline bool valid_fill(int f) {
+  for (int i = 0; i < kNumFills; ++i)
+    if (kFills[i] == f) return true;
+  return false;
+}
+
 struct Schedule {
   WarpTask* d_tasks = nullptr;  // n_items x (warps per CTA)
   int32_t n_items = 0;
+  int32_t fill = 100;           // the partition this schedule was built with
 };
 
 }  // namespace wmd
@@ -91,6 +107,9 @@ struct wmd_corpus {
   int32_t* doc_words = nullptr;// nnz, device rows (< U) sorted within a doc
   float* doc_vals = nullptr;   // nnz
   wmd::Schedule sched[wmd::kNumClasses][wmd::kMaxVariants];
+  // host copies kept for rebuilding schedules with another partition
+  std::vector<int64_t> h_dptr;   // N+1, document-major CSR offsets
+  std::vector<int32_t> h_order;  // documents by decreasing length (stable)
   int loop_variant[wmd::kNumClasses][2] = {};  // chosen variant per class and precision
   size_t device_bytes = 0;
   int num_sms = 0;

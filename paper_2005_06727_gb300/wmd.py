@@ -80,6 +80,7 @@ _P = C.c_void_p
 _SIGS = {
     "wmd_last_error": (C.c_char_p, []),
     "wmd_version": (C.c_char_p, []),
+    "wmd_measure_fp32_peak": (C.c_int, [C.c_int32, C.c_int32, _P]),
     "wmd_compact_query": (C.c_int, [_P, _P, C.c_int32, C.c_int64, _P, _P, _P]),
     "wmd_options_default": (None, [_P]),
     "wmd_corpus_load": (C.c_int, [_P, C.c_int64, C.c_int32, _P, _P, _P, C.c_int64, C.c_int64,
@@ -112,6 +113,8 @@ _SIGS = {
     "wmd_loop_variant_count": (C.c_int32, [C.c_int32]),
     "wmd_set_loop_variant": (C.c_int, [_P, C.c_int32, C.c_int, C.c_int32]),
     "wmd_get_loop_variant": (C.c_int32, [_P, C.c_int32, C.c_int]),
+    "wmd_set_loop_partition": (C.c_int, [_P, C.c_int32, C.c_int32, C.c_int32]),
+    "wmd_get_loop_partition": (C.c_int32, [_P, C.c_int32, C.c_int32]),
     "wmd_autotune": (C.c_int, [_P, _P, _P, C.c_int32, C.c_float, C.c_int32, C.c_int, _P]),
     "wmd_server_create": (C.c_int, [_P, _P, _P]),
     "wmd_serve_submit": (C.c_int, [_P, _P, _P, C.c_int32, C.c_float, C.c_int32, C.c_int, _P]),
@@ -162,6 +165,14 @@ def _ptr(a: np.ndarray):
         return C.addressof(C.c_char.from_buffer(a))
     except (TypeError, ValueError, BufferError):  # read-only or strided
         return a.ctypes.data
+
+
+def measure_fp32_peak(device: int = 0, packed: bool = True) -> float:
+    """``wmd_measure_fp32_peak``: the device's measured FP32 FMA rate in
+    TFLOP/s (packed FFMA2 or scalar FFMA)."""
+    out = C.c_double(0.0)
+    _check(lib().wmd_measure_fp32_peak(int(device), 1 if packed else 0, C.byref(out)))
+    return float(out.value)
 
 
 def loop_variant_count(v_r: int) -> int:
@@ -295,6 +306,15 @@ class Corpus:
     def loop_variant(self, v_r: int, prec: int = PREC_FP32) -> int:
         """``wmd_get_loop_variant``."""
         return int(lib().wmd_get_loop_variant(self._h, int(v_r), int(prec)))
+
+    def set_loop_partition(self, v_r: int, variant: int, fill: int):
+        """``wmd_set_loop_partition``: team-size fill (50, 75, 100 or 200) of
+        v_r's class and tile variant."""
+        _check(lib().wmd_set_loop_partition(self._h, int(v_r), int(variant), int(fill)))
+
+    def loop_partition(self, v_r: int, variant: int) -> int:
+        """``wmd_get_loop_partition``."""
+        return int(lib().wmd_get_loop_partition(self._h, int(v_r), int(variant)))
 
     def autotune(self, q_ids, q_w, lam: float, max_iter: int, prec: int = PREC_FP32) -> int:
         """``wmd_autotune``: returns the chosen fused-loop variant."""

@@ -185,15 +185,25 @@ def test_autotune_cache_round_trip(wmd, small, tmp_path):
     corpus.close()
     lines = path.read_text().splitlines()
     assert lines and lines[-1].startswith("wmd-loop ")
-    # a corpus of the same shape starts from the recorded choice; a forced
-    # entry for the other variant wins (last line), a malformed line is skipped
-    other = 1 - chosen
     fields = lines[-1].split()
-    fields[-1] = str(other)
-    path.write_text("\n".join(lines + ["garbage line", " ".join(fields)]) + "\n")
+    assert len(fields) == 10 and int(fields[-2]) == chosen and int(fields[-1]) in (50, 75, 100, 200)
+    # a corpus of the same shape starts from the recorded choice; a forced
+    # entry for the other variant and partition wins (last line); malformed
+    # lines and invalid partitions are skipped
+    other = 1 - chosen
+    fields[-2], fields[-1] = str(other), "200"
+    bad_fill = fields[:-1] + ["60"]
+    path.write_text("\n".join(lines + ["garbage line", " ".join(fields), " ".join(bad_fill)]) + "\n")
     corpus = wmd.Corpus.from_synth(vecs, c, autotune_cache=str(path))
     assert corpus.loop_variant(v_r) == other
+    assert corpus.loop_partition(v_r, other) == 200
     _close(corpus.query(qs[2][0], qs[2][1], 10.0, 15), _oracle(vecs, c, qs[2], 10.0))
+    corpus.close()
+    # a line without a partition (variant only) keeps fill = 100
+    path.write_text(" ".join(fields[:-1]) + "\n")
+    corpus = wmd.Corpus.from_synth(vecs, c, autotune_cache=str(path))
+    assert corpus.loop_variant(v_r) == other
+    assert corpus.loop_partition(v_r, other) == 100
     corpus.close()
     # another corpus shape ignores the file
     c2 = synth.make_corpus(vecs.shape[0], 50, 5, 60, 77)

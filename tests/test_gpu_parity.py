@@ -397,3 +397,48 @@ def test_every_loop_variant_matches_oracle(wmd, v_r):
     assert_parity(corpus.query(q_ids, q_w, 10.0, 15), want, FP32_RTOL, "after autotune")
     with pytest.raises(wmd.WMDError):
         corpus.set_loop_variant(v_r, n_var)
+
+
+# ---------------------------------------------------------------- partitions (team sizes)
+@pytest.mark.parametrize("v_r", [6, 30, 64, 100, 200])
+def test_every_partition_matches_oracle(wmd, v_r):
+    """Every partition of the documents into teams (fill 50, 75, 100, 200:
+    spread over more warps, the default, or long documents re-read from L2
+    by fewer warps) with every tile variant gives the oracle's values, and
+    the autotuner's choice of variant and partition too."""
+    V = 4000
+    vecs = synth.make_vecs(V, 300, 700 + v_r)
+    rng = np.random.default_rng(800 + v_r)
+    lengths = [1, 2, 7, 20, 33, 48, 49, 64, 65, 96, 97, 130, 192, 193, 260, 400, 800]
+    docs = []
+    for n in lengths:
+        ids = np.sort(rng.choice(V, n, replace=False)).astype(np.int32)
+        wts = rng.random(n) + 0.05
+        docs.append((ids, (wts / wts.sum()).astype(np.float32)))
+    c = synth.corpus_from_docs(V, docs)
+    q_ids, q_w = synth.make_query(V, v_r, 900 + v_r)
+    corpus = wmd.Corpus.from_synth(vecs, c)
+    for T in (0, 15):
+        want = oracle(vecs, c, q_ids, q_w, 10.0, T)
+        for var in range(wmd.loop_variant_count(v_r)):
+            corpus.set_loop_variant(v_r, var)
+            corpus.set_loop_variant(v_r, var, wmd.PREC_BF16_K)
+            for fill in (50, 75, 100, 200):
+                corpus.set_loop_partition(v_r, var, fill)
+                assert corpus.loop_partition(v_r, var) == fill
+                assert_parity(corpus.query(q_ids, q_w, 10.0, T), want, FP32_RTOL,
+                              f"v_r={v_r} T={T} variant {var} fill {fill}")
+                assert_parity(corpus.query(q_ids, q_w, 10.0, T, wmd.PREC_BF16_K), want, BF16_RTOL,
+                              f"bf16 v_r={v_r} T={T} variant {var} fill {fill}")
+    want = oracle(vecs, c, q_ids, q_w, 10.0, 15)
+    chosen = corpus.autotune(q_ids, q_w, 10.0, 15)
+    assert corpus.loop_variant(v_r) == chosen
+    assert corpus.loop_partition(v_r, chosen) in (50, 75, 100, 200)
+    assert_parity(corpus.query(q_ids, q_w, 10.0, 15), want, FP32_RTOL, "after autotune")
+    for bad in (0, 60, 101, 400):
+        with pytest.raises(wmd.WMDError):
+            corpus.set_loop_partition(v_r, 0, bad)
+    with pytest.raises(wmd.WMDError):
+        corpus.set_loop_partition(v_r, wmd.loop_variant_count(v_r), 100)
+    assert corpus.loop_partition(v_r, 99) == -1
+    corpus.close()

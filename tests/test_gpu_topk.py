@@ -42,6 +42,8 @@ def _values(n, kind, seed):
     if kind == "ties":                     # few distinct values, signed zeros, NaN, inf
         v = rng.choice([1.5, 1.25, 0.0, -0.0, 2.0, np.nan, np.inf, 1.25], n)
         return v.astype(np.float64)
+    if kind == "dense":                    # a few ulps apart: several digit passes, many ties
+        return 1.0 + rng.integers(0, 3000, n) * 2.0 ** -50
     if kind == "nan":
         return np.full(n, np.nan)
     if kind == "equal":
@@ -49,11 +51,14 @@ def _values(n, kind, seed):
     raise ValueError(kind)
 
 
-@pytest.mark.parametrize("n", [1, 2, 100, 1023, 1024, 1025, 5000, 12288, 12289, 200_000])
-@pytest.mark.parametrize("kind", ["wmd", "ties"])
+@pytest.mark.parametrize("n", [1, 2, 100, 511, 512, 513, 1023, 1024, 1025, 5000, 12288, 12289,
+                               16384, 16385, 200_000])
+@pytest.mark.parametrize("kind", ["wmd", "ties", "dense"])
 def test_selection_is_bit_exact(wmd, n, kind):
+    """Both selection kernels (keys in registers for N <= 16384 and k <= 256,
+    the shared-memory / streamed radix select otherwise) at their edges."""
     v = _values(n, kind, n)
-    for k in sorted({1, min(7, n), min(100, n), min(1024, n)}):
+    for k in sorted({1, min(7, n), min(100, n), min(256, n), min(257, n), min(1024, n)}):
         ids, vals = _select(wmd, v, k)
         want_ids, want_vals = orc.nearest_documents(v, k)
         assert ids.tolist() == want_ids.tolist(), f"n={n} k={k} {kind}"
@@ -62,7 +67,7 @@ def test_selection_is_bit_exact(wmd, n, kind):
 
 @pytest.mark.parametrize("kind", ["nan", "equal"])
 def test_all_equal_values_give_the_lowest_ids(wmd, kind):
-    for n in (50, 3000, 20000):
+    for n in (50, 600, 3000, 16384, 20000):
         v = _values(n, kind, 0)
         k = min(64, n - 1)
         ids, vals = _select(wmd, v, k)
