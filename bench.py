@@ -655,6 +655,7 @@ def bench_converge(wmd, corpus, dq, w, prec, stream, flush, reps=10):
                      "fixed_ms": times["fixed"], "until_converged_ms": times["until_converged"],
                      "fixed_wmds_per_s": N / (times["fixed"] * 1e-3),
                      "until_converged_wmds_per_s": N / (times["until_converged"] * 1e-3),
+                     "speedup": times["fixed"] / times["until_converged"],
                      "mean_bodies": float(it.mean()), "max_bodies": int(it.max()),
                      "stopped_before_cap": float(np.mean(it < T))})
     return {"what": "per query: cdist + fused loop, stopping each document once "
