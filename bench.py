@@ -688,7 +688,7 @@ def bench_topk(wmd, dq, N, stream, reps=20, corpus=None, w=None, prec=0, flush=N
                 ts.append(a.elapsed_time(b) * 1e3)
             rows.append({"input": name, "N": n, "k": k, "us": statistics.mean(ts)})
     out = {"what": "one-CTA radix select of the k smallest WMD values (ties to the lower id): "
-                   "keys in registers, 11-bit digits for N <= 16384 and k <= 256, else "
+                   "keys in registers, 10-bit digits of key - min for N <= 16384 and k <= 256, else "
                    "8-bit digits over shared-memory or streamed keys",
            "rows": rows}
     if corpus is not None:
