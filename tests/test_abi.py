@@ -144,3 +144,13 @@ def test_options_defaults_and_host_validation(lib):
     # a NULL corpus is refused by the setters and getters
     assert lib.wmd_corpus_set_wait_limit(None, 5) == wmd.WMD_ERR_INVALID_ARG
     assert lib.wmd_get_loop_variant(None, 30, 0) == -1
+
+
+def test_measure_fp32_peak_rejects_null_output(lib):
+    """wmd_measure_fp32_peak checks its output pointer before touching CUDA."""
+    assert lib.wmd_measure_fp32_peak(0, 1, None) == wmd.WMD_ERR_INVALID_ARG
+
+
+def test_partition_entry_points_on_null_corpus(lib):
+    assert lib.wmd_get_loop_partition(None, 30, 0) == -1
+    assert lib.wmd_set_loop_partition(None, 30, 0, 100) == wmd.WMD_ERR_INVALID_ARG

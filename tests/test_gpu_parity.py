@@ -442,3 +442,17 @@ def test_every_partition_matches_oracle(wmd, v_r):
         corpus.set_loop_partition(v_r, wmd.loop_variant_count(v_r), 100)
     assert corpus.loop_partition(v_r, 99) == -1
     corpus.close()
+
+
+def test_measured_fp32_peak_is_plausible(wmd):
+    """wmd_measure_fp32_peak (the fused loop's roofline denominator) lies
+    below the unit-count bound (SMs x 128 FP32 lanes x 2 flop x 2.2 GHz, above
+    any GB300 clock) and not far under it; an invalid device is refused."""
+    import torch
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    bound = sms * 128 * 2 * 2.2e9 / 1e12
+    for packed in (True, False):
+        t = wmd.measure_fp32_peak(0, packed)
+        assert 0.3 * bound < t < bound, (packed, t, bound)
+    with pytest.raises(wmd.WMDError):
+        wmd.measure_fp32_peak(torch.cuda.device_count(), True)
