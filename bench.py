@@ -47,7 +47,7 @@ def parse():
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="paper")
     ap.add_argument("--prec", choices=["fp32", "bf16"], default="fp32")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--legs", default="converge,topk,dense,large,batched,serving",
+    ap.add_argument("--legs", default="converge,topk,dense,large,paper_exact,batched,serving",
                     help="comma-separated extra legs to run after the timed step")
     ap.add_argument("--no-systems", action="store_true",
                     help="skip the batched and served measurements")
@@ -616,6 +616,76 @@ def bench_large(wmd, device, steps=5):
     return rec
 
 
+def bench_paper_exact(wmd, device, steps=20):
+    """The paper's own corpus shape (5000 documents, about 173k nonzeros, 34.5
+    words per document; queries of 19 and 43 words): per query cdist + fused
+    loop (CUDA events on the launching stream, L2 flushed between steps), the
+    loop against the measured FP32 FMA rate, and every document against the
+    FP64 oracle."""
+    import torch
+    w = synth.PAPER_EXACT
+    vecs = synth.make_vecs(w.V, w.d, synth.embed_seed(w.cfg))
+    c = synth.make_corpus(w.V, w.N, w.doc_lo, w.doc_hi, synth.corpus_seed(w.cfg))
+    qs = synth.paper_exact_queries()
+    dev = torch.device("cuda", device)
+    stream = torch.cuda.current_stream(dev)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    corpus = wmd.Corpus.from_synth(vecs, c, device=device)
+    peaks, _ = measured_peaks()
+    alu, _ = alu_peak_tflops(dev, peaks.get("sm_max_mhz", 2070.0))
+    rows, outs = [], []
+    for q_ids, q_w in qs:
+        variant = corpus.autotune(q_ids, q_w, w.lam, w.max_iter)
+        dq = wmd.DeviceQuery(corpus, q_ids, q_w)
+        ev = []
+        for k in range(steps + 3):
+            flush.zero_()
+            e = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+            e[0].record(stream)
+            corpus.query_device(dq.ids, dq.w, dq.v_r, w.lam, w.max_iter, wmd.PREC_FP32, dq.ws,
+                                dq.ws_bytes, dq.out, stream)
+            e[1].record(stream)
+            if k >= 3:
+                ev.append(e)
+        lps = []
+        for k in range(steps + 3):
+            flush.zero_()
+            corpus.build_kernel_matrix(dq.ids, dq.w, dq.v_r, w.lam, wmd.PREC_FP32, dq.ws,
+                                       dq.ws_bytes, stream)
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            corpus.sinkhorn_loop(dq.v_r, w.max_iter, wmd.PREC_FP32, dq.ws, dq.ws_bytes, dq.out,
+                                 stream)
+            b.record(stream)
+            if k >= 3:
+                lps.append((a, b))
+        torch.cuda.synchronize()
+        st = statistics.mean(a.elapsed_time(b) for a, b in ev)
+        lp = statistics.mean(a.elapsed_time(b) for a, b in lps)
+        flops = 4.0 * len(q_ids) * c.nnz * (w.max_iter + 1)
+        outs.append(dq.out[: c.N].cpu().numpy())
+        rows.append({"v_r": len(q_ids), "ms_per_step": st, "value": c.N / (st * 1e-3), "unit": UNIT,
+                     "loop_ms": lp, "loop_tflops": flops / (lp * 1e-3) / 1e12,
+                     "loop_alu_frac": flops / (lp * 1e-3) / 1e12 / alu, "loop_variant": variant,
+                     "loop_partition": corpus.loop_partition(len(q_ids), variant)})
+    corpus.close()
+    docs = np.arange(c.N)
+    from oracle.pool import OraclePool
+    t0 = time.perf_counter()
+    with OraclePool(w.cfg) as pool:
+        chunks = [ch for ch in np.array_split(docs, pool.workers) if ch.size]
+        for row, (q_ids, q_w), got in zip(rows, qs, outs):
+            futs = [pool.submit(q_ids, q_w, w.lam, w.max_iter, ch) for ch in chunks]
+            ref = np.concatenate([f.result(timeout=3600)[0] for f in futs])
+            row["error_vs_oracle"] = error_vs_oracle(got, ref, wmd.PREC_FP32)
+    return {"workload": (f"{w.name}: V={w.V} d={w.d} N={w.N} docs of {w.doc_lo}-{w.doc_hi} "
+                         f"Zipf(1.1) words ({c.nnz} nonzeros, the paper's 173,087), queries of "
+                         f"19 and 43 words, lambda={w.lam:g}, max_iter={w.max_iter}"),
+            "rows": rows, "oracle": f"all {c.N} documents, {time.perf_counter() - t0:.1f} s on "
+                                    f"spawned workers", "l2": "flushed between steps (512 MiB write)"}
+
+
 # ------------------------------------------------------------------ ours
 def bench_converge(wmd, corpus, dq, w, prec, stream, flush, reps=10):
     """Algorithm 1's "while x changes" (wmd_query_device_tol) against the
@@ -937,6 +1007,8 @@ def run_ours(args, w):
             out["dense"] = bench_dense(wmd, corpus, dq, w, stream, flush)
         if "large" in legs:
             out["large"] = bench_large(wmd, local_rank)
+        if "paper_exact" in legs:
+            out["paper_exact"] = bench_paper_exact(wmd, local_rank)
         if "batched" in legs:
             out["batched"] = bench_batched(wmd, local_rank, with_oracle=not args.no_cpu_baseline)
         if "serving" in legs:

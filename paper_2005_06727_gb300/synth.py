@@ -50,7 +50,20 @@ LARGE = Workload("large V=100000 N=100000 v_r=64", 100_000, 300, 100_000, 20, 20
 BATCHED = Workload("batched V=100000 N=20000 256 queries v_r U[5,128]", 100_000, 300, 20_000, 20, 150, 5, 128, 256, 4)
 SERVING = Workload("serving V=200000 N=200000 v_r U[5,200]", 200_000, 300, 200_000, 20, 200, 5, 200, 2000, 5)
 
-WORKLOADS = {w.cfg: w for w in (TINY, PAPER, LARGE, BATCHED, SERVING)}
+# The paper's own corpus shape (Sec. 3: the first 5000 dbpedia documents,
+# 173,087 nonzeros, 34.6 distinct words per document on average; its queries
+# have 19 and 43 words): documents of U{10..59} words, queries of 19 and 43.
+PAPER_EXACT = Workload("paper-exact V=100000 N=5000 v_r 19 and 43", 100_000, 300, 5000, 10, 59, 19, 43,
+                       2, 6)
+PAPER_EXACT_VR = (19, 43)
+
+WORKLOADS = {w.cfg: w for w in (TINY, PAPER, LARGE, BATCHED, SERVING, PAPER_EXACT)}
+
+
+def paper_exact_queries() -> list[tuple[np.ndarray, np.ndarray]]:
+    """The two queries of the paper-exact workload, 19 and 43 words."""
+    return [make_query(PAPER_EXACT.V, vr, query_seed(PAPER_EXACT.cfg, q))
+            for q, vr in enumerate(PAPER_EXACT_VR)]
 
 
 def corpus_seed(cfg: int) -> int:

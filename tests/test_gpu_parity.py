@@ -81,6 +81,22 @@ def test_paper_shaped_workload_all_documents(wmd):
     assert np.array_equal(dev[: c.N], got)
 
 
+def test_paper_exact_shape_all_documents(wmd):
+    """The paper's own corpus shape (5000 documents of 10-59 words, about 173k
+    nonzeros; queries of 19 and 43 words), every document, FP32 and BF16 K."""
+    w = synth.PAPER_EXACT
+    vecs = synth.make_vecs(w.V, w.d, synth.embed_seed(w.cfg))
+    c = synth.make_corpus(w.V, w.N, w.doc_lo, w.doc_hi, synth.corpus_seed(w.cfg))
+    corpus = wmd.Corpus.from_synth(vecs, c)
+    for q_ids, q_w in synth.paper_exact_queries():
+        want = oracle(vecs, c, q_ids, q_w, w.lam, w.max_iter)
+        assert_parity(corpus.query(q_ids, q_w, w.lam, w.max_iter), want, FP32_RTOL,
+                      f"paper-exact v_r={len(q_ids)}")
+        assert_parity(corpus.query(q_ids, q_w, w.lam, w.max_iter, wmd.PREC_BF16_K), want,
+                      BF16_RTOL, f"paper-exact bf16 v_r={len(q_ids)}")
+    corpus.close()
+
+
 def test_large_workload_sampled_documents(wmd):
     """V=100000, N=100000, 20-200 words, v_r=64: sampled documents, FP32 and
     the bfloat16-stored K variant."""
