@@ -25,6 +25,8 @@
 // Ties are broken by the lower document id, so the result is unique.  When
 // N keys fit in shared memory (N <= kCacheMax) they are read from global
 // memory once and kept there for all passes.
+#include <cooperative_groups.h>
+
 #include "wmd_internal.h"
 
 namespace wmd {
@@ -639,6 +641,350 @@ __global__ void __launch_bounds__(kSmallThreads, 1)
   }
 }
 
+// ---------------------------------------------------------------- large N, k <= 256
+// The same selection spread over a thread-block cluster of CS CTAs (16 where
+// the GPU allows clusters that large, else 8), one SM each: CTA r keeps keys
+// [r S, (r + 1) S) in registers (S = ceil(N / CS), E keys per thread, 512
+// threads), and the CTAs meet through distributed shared memory:
+//   * every CTA publishes its smallest and largest key; each reads all CS of
+//     them and forms the global range itself;
+//   * per digit pass every CTA histograms its own keys in its shared memory;
+//     after a cluster barrier CTA 0 sums the CS histograms bin by bin (remote
+//     loads), scans them and publishes the bin of the k-th key, which every
+//     CTA reads after a second barrier;
+//   * the keys below that bin and the candidates in it are written into CTA
+//     0's shared memory with remote atomics on its counters; after a last
+//     barrier the other CTAs leave (nothing reads their shared memory any
+//     more) and CTA 0 ranks the candidates and orders the k.
+// Every wait is a hardware cluster barrier (barrier.cluster); the kernel has
+// no spin loop.
+constexpr int kClusterThreads = 512;
+constexpr int kClusterMaxE = 32;
+
+template <int E>
+__global__ void __launch_bounds__(kClusterThreads, 1)
+    topk_cluster_kernel(const double* wmd, int N, int k, int64_t* out_idx, double* out_val) {
+  namespace cg = cooperative_groups;
+  cg::cluster_group cluster = cg::this_cluster();
+  const int CS = (int)cluster.num_blocks();
+  const int rank = (int)cluster.block_rank();
+  constexpr int kW = kClusterThreads / 32;
+  __shared__ unsigned hist[kSmallBins];
+  __shared__ unsigned warp_sums[kW];
+  __shared__ unsigned long long s_min[kW], s_max[kW];
+  __shared__ unsigned long long blk_min, blk_max;
+  __shared__ unsigned blk_cnt;
+  __shared__ unsigned s_sel[3];   // CTA 0: bin, keys below it, keys in it
+  __shared__ unsigned s_taken, s_ncand;
+  __shared__ unsigned long long s_key[kRankSortMax];
+  __shared__ int s_idx[kRankSortMax];
+  __shared__ unsigned long long c_key[kSmallCand];
+  __shared__ int c_idx[kSmallCand];
+  static_assert(kSmallBins == 2 * kClusterThreads, "two bins per thread in the scan");
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int span = (N + CS - 1) / CS;
+  const int lo = rank * span;
+  const int end = min(N, lo + span);
+  const int i0 = lo + tid * E;
+
+  hist[2 * tid] = 0;
+  hist[2 * tid + 1] = 0;
+  if (tid == 0) {
+    s_taken = 0;
+    s_ncand = 0;
+  }
+  wait_for_values();
+  const unsigned long long* bits = reinterpret_cast<const unsigned long long*>(wmd);
+  unsigned long long key[E];
+  unsigned valid = 0;
+  unsigned long long kmin = ~0ull, kmax = 0;
+#pragma unroll
+  for (int e = 0; e < E; ++e) {
+    const bool v = i0 + e < end;
+    key[e] = v ? order_key(ld_bits(bits + i0 + e)) : ~0ull;
+    valid |= (v ? 1u : 0u) << e;
+    if (v) {
+      kmin = key[e] < kmin ? key[e] : kmin;
+      kmax = key[e] > kmax ? key[e] : kmax;
+    }
+  }
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    const unsigned long long a = __shfl_xor_sync(0xffffffffu, kmin, off);
+    const unsigned long long b = __shfl_xor_sync(0xffffffffu, kmax, off);
+    kmin = a < kmin ? a : kmin;
+    kmax = b > kmax ? b : kmax;
+  }
+  if (lane == 0) {
+    s_min[warp] = kmin;
+    s_max[warp] = kmax;
+  }
+  __syncthreads();
+  if (warp == 0) {
+    kmin = lane < kW ? s_min[lane] : ~0ull;
+    kmax = lane < kW ? s_max[lane] : 0ull;
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+      const unsigned long long a = __shfl_xor_sync(0xffffffffu, kmin, off);
+      const unsigned long long b = __shfl_xor_sync(0xffffffffu, kmax, off);
+      kmin = a < kmin ? a : kmin;
+      kmax = b > kmax ? b : kmax;
+    }
+    if (lane == 0) {
+      blk_min = kmin;
+      blk_max = kmax;
+    }
+  }
+  cluster.sync();  // every CTA's range and zeroed counters are visible
+  // the global range: lane l reads CTA l's (CS <= 32), then a butterfly
+  kmin = lane < CS ? *cluster.map_shared_rank(&blk_min, lane) : ~0ull;
+  kmax = lane < CS ? *cluster.map_shared_rank(&blk_max, lane) : 0ull;
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    const unsigned long long a = __shfl_xor_sync(0xffffffffu, kmin, off);
+    const unsigned long long b = __shfl_xor_sync(0xffffffffu, kmax, off);
+    kmin = a < kmin ? a : kmin;
+    kmax = b > kmax ? b : kmax;
+  }
+#pragma unroll
+  for (int e = 0; e < E; ++e) key[e] -= kmin;
+  const unsigned long long range = kmax - kmin;
+
+  unsigned cm = valid;
+  int hi = range == 0 ? 0 : 64 - __clzll((long long)range);
+  unsigned long long mask = hi == 64 ? 0ull : ~((1ull << hi) - 1ull);
+  unsigned long long prefix = 0;
+  unsigned need = (unsigned)k;
+  unsigned ncand = (unsigned)N;
+  while (hi > 0 && ncand > (unsigned)kSmallCand) {
+    const int width = hi < kSmallBits ? hi : kSmallBits;
+    const int shift = hi - width;
+    const unsigned dmask = (1u << width) - 1u;
+#pragma unroll
+    for (int e = 0; e < E; ++e)
+      if ((cm >> e) & 1u) atomicAdd(&hist[(unsigned)(key[e] >> shift) & dmask], 1u);
+    cluster.sync();  // every CTA's histogram is complete
+    if (rank == 0) {
+      unsigned h0 = 0, h1 = 0;
+      for (int r = 0; r < CS; ++r) {
+        const unsigned* rh = cluster.map_shared_rank(hist, r);
+        h0 += rh[2 * tid];
+        h1 += rh[2 * tid + 1];
+      }
+      const unsigned sum = h0 + h1;
+      unsigned incl = sum;
+#pragma unroll
+      for (int off = 1; off < 32; off <<= 1) {
+        const unsigned o = __shfl_up_sync(0xffffffffu, incl, off);
+        if (lane >= off) incl += o;
+      }
+      if (lane == 31) warp_sums[warp] = incl;
+      __syncthreads();
+      if (warp == 0) {
+        const unsigned v = lane < kW ? warp_sums[lane] : 0u;
+        unsigned w = v;
+#pragma unroll
+        for (int off = 1; off < kW; off <<= 1) {
+          const unsigned o = __shfl_up_sync(0xffffffffu, w, off);
+          if (lane >= off) w += o;
+        }
+        if (lane < kW) warp_sums[lane] = w - v;
+      }
+      __syncthreads();
+      const unsigned excl = warp_sums[warp] + incl - sum;
+      if (excl < need && need <= excl + h0) {
+        s_sel[0] = 2 * tid;
+        s_sel[1] = excl;
+        s_sel[2] = h0;
+      } else if (excl + h0 < need && need <= excl + sum) {
+        s_sel[0] = 2 * tid + 1;
+        s_sel[1] = excl + h0;
+        s_sel[2] = h1;
+      }
+    }
+    cluster.sync();  // the bin is published; no CTA reads another's histogram any more
+    const unsigned* sel = cluster.map_shared_rank(s_sel, 0);
+    const unsigned bin = sel[0];
+    need -= sel[1];
+    ncand = sel[2];
+    hist[2 * tid] = 0;
+    hist[2 * tid + 1] = 0;
+    __syncthreads();  // every bin is zero before any thread counts the next pass
+    prefix |= (unsigned long long)bin << shift;
+    mask |= (unsigned long long)dmask << shift;
+    hi = shift;
+#pragma unroll
+    for (int e = 0; e < E; ++e)
+      if (((unsigned)(key[e] >> shift) & dmask) != bin) cm &= ~(1u << e);
+    // CTA 0 rewrites s_sel only after the next pass's first barrier, which
+    // every CTA reaches after reading it
+  }
+
+  // the keys below the decided prefix and the candidates, into CTA 0
+  const unsigned base = (unsigned)k - need;
+  unsigned* r_taken = cluster.map_shared_rank(&s_taken, 0);
+  unsigned long long* r_key = cluster.map_shared_rank(s_key, 0);
+  int* r_idx = cluster.map_shared_rank(s_idx, 0);
+#pragma unroll
+  for (int e = 0; e < E; ++e) {
+    if (((valid >> e) & 1u) && (key[e] & mask) < prefix) {
+      const unsigned slot = atomicAdd(r_taken, 1u);
+      if (slot < (unsigned)kRankSortMax) {  // always: fewer than k lie below
+        r_key[slot] = key[e];
+        r_idx[slot] = i0 + e;
+      }
+    }
+  }
+  if (ncand <= (unsigned)kSmallCand) {
+    unsigned* r_ncand = cluster.map_shared_rank(&s_ncand, 0);
+    unsigned long long* r_ckey = cluster.map_shared_rank(c_key, 0);
+    int* r_cidx = cluster.map_shared_rank(c_idx, 0);
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+      if ((cm >> e) & 1u) {
+        const unsigned p = atomicAdd(r_ncand, 1u);
+        if (p < (unsigned)kSmallCand) {
+          r_ckey[p] = key[e];
+          r_cidx[p] = i0 + e;
+        }
+      }
+    }
+    cluster.sync();  // everything for CTA 0 has arrived
+    if (rank != 0) return;
+    // candidate tid / 8, its rank summed over 8 threads
+    const unsigned m = s_ncand < (unsigned)kSmallCand ? s_ncand : (unsigned)kSmallCand;
+    const unsigned c = (unsigned)tid >> 3, part = (unsigned)tid & 7u;
+    unsigned long long kt = 0;
+    int it = 0;
+    unsigned r = 0;
+    if (c < m) {
+      kt = c_key[c];
+      it = c_idx[c];
+      for (unsigned j = part; j < m; j += 8) r += before(c_key[j], c_idx[j], kt, it) ? 1u : 0u;
+    }
+#pragma unroll
+    for (int off = 1; off < 8; off <<= 1) r += __shfl_xor_sync(0xffffffffu, r, off);
+    if (c < m && part == 0 && r < need && base + r < (unsigned)kRankSortMax) {
+      s_key[base + r] = kt;
+      s_idx[base + r] = it;
+    }
+  } else {
+    // every bit decided and more than kSmallCand keys equal to the k-th: the
+    // lowest document ids win.  CTA r holds a contiguous id range, so a
+    // candidate's rank is the candidates of the CTAs before it plus its rank
+    // in its own CTA (thread order is document order).
+    const unsigned mine = __popc(cm);
+    unsigned incl = mine;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+      const unsigned o = __shfl_up_sync(0xffffffffu, incl, off);
+      if (lane >= off) incl += o;
+    }
+    if (lane == 31) warp_sums[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+      const unsigned v = lane < kW ? warp_sums[lane] : 0u;
+      unsigned w = v;
+#pragma unroll
+      for (int off = 1; off < kW; off <<= 1) {
+        const unsigned o = __shfl_up_sync(0xffffffffu, w, off);
+        if (lane >= off) w += o;
+      }
+      if (lane < kW) warp_sums[lane] = w - v;
+      if (lane == kW - 1) blk_cnt = w;
+    }
+    cluster.sync();  // every CTA's count is visible
+    unsigned before_me = 0;
+    for (int r = 0; r < rank; ++r) before_me += *cluster.map_shared_rank(&blk_cnt, r);
+    unsigned rr = before_me + warp_sums[warp] + incl - mine;
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+      if ((cm >> e) & 1u) {
+        if (rr < need && base + rr < (unsigned)kRankSortMax) {
+          r_key[base + rr] = key[e];
+          r_idx[base + rr] = i0 + e;
+        }
+        ++rr;
+      }
+    }
+    cluster.sync();  // everything for CTA 0 has arrived; nobody reads blk_cnt any more
+    if (rank != 0) return;
+  }
+  __syncthreads();
+
+  // CTA 0: the k taken, ordered by (key, document id)
+  const int en = tid >> 1, part = tid & 1;
+  unsigned long long kt = 0;
+  int it = 0, rk = 0;
+  if (en < k) {
+    kt = s_key[en];
+    it = s_idx[en];
+    for (int j = part; j < k; j += 2) rk += before(s_key[j], s_idx[j], kt, it) ? 1 : 0;
+  }
+  rk += __shfl_xor_sync(0xffffffffu, rk, 1);
+  if (en < k && part == 0) {
+    out_idx[rk] = it;
+    out_val[rk] = (it >= 0 && it < N) ? wmd[it] : __longlong_as_double(0x7ff8000000000000ll);
+  }
+}
+
+template <int E>
+cudaError_t launch_cluster(const double* wmd, int n, int k, int64_t* out_idx, double* out_val,
+                           int cs, cudaStream_t s) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)cs);
+  cfg.blockDim = dim3(kClusterThreads);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[2];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = (unsigned)cs;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  attr[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[1].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 2;
+  return cudaLaunchKernelEx(&cfg, topk_cluster_kernel<E>, wmd, n, k, out_idx, out_val);
+}
+
+// The cluster size the selection uses: 16 CTAs where the GPU can run such a
+// cluster (a non-portable size), else 8; 0 if neither fits.
+int cluster_size_for_topk() {
+  static std::once_flag once;
+  static int cs = 0;
+  std::call_once(once, [] {
+    const void* kerns[] = {(const void*)topk_cluster_kernel<4>, (const void*)topk_cluster_kernel<8>,
+                           (const void*)topk_cluster_kernel<12>, (const void*)topk_cluster_kernel<16>,
+                           (const void*)topk_cluster_kernel<20>, (const void*)topk_cluster_kernel<24>,
+                           (const void*)topk_cluster_kernel<28>, (const void*)topk_cluster_kernel<32>};
+    bool ok16 = true;
+    for (const void* f : kerns)
+      ok16 = ok16 && cudaFuncSetAttribute(f, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) ==
+                         cudaSuccess;
+    for (int want : {16, 8}) {
+      if (want == 16 && !ok16) continue;
+      cudaLaunchConfig_t cfg = {};
+      cfg.gridDim = dim3((unsigned)want);
+      cfg.blockDim = dim3(kClusterThreads);
+      cudaLaunchAttribute attr[1];
+      attr[0].id = cudaLaunchAttributeClusterDimension;
+      attr[0].val.clusterDim.x = (unsigned)want;
+      attr[0].val.clusterDim.y = 1;
+      attr[0].val.clusterDim.z = 1;
+      cfg.attrs = attr;
+      cfg.numAttrs = 1;
+      int n = 0;
+      if (cudaOccupancyMaxActiveClusters(&n, topk_cluster_kernel<32>, &cfg) == cudaSuccess && n > 0) {
+        cs = want;
+        break;
+      }
+    }
+    cudaGetLastError();  // a refused size leaves no error behind
+  });
+  return cs;
+}
+
 }  // namespace
 
 cudaError_t launch_topk(const double* wmd, int64_t N, int k, int64_t* out_idx, double* out_val,
@@ -684,6 +1030,19 @@ cudaError_t launch_topk(const double* wmd, int64_t N, int k, int64_t* out_idx, d
     if (e <= 20) return go(topk_small_kernel<20>);
     if (e <= 24) return go(topk_small_kernel<24>);
     return go(topk_small_kernel<32>);
+  }
+  const int cs = N > kSmallMaxN && k <= kRankSortMax ? cluster_size_for_topk() : 0;
+  if (cs > 0 && N <= (int64_t)cs * kClusterThreads * kClusterMaxE) {
+    const int n = (int)N;
+    const int e = ((n + cs - 1) / cs + kClusterThreads - 1) / kClusterThreads;
+    if (e <= 4) return launch_cluster<4>(wmd, n, k, out_idx, out_val, cs, s);
+    if (e <= 8) return launch_cluster<8>(wmd, n, k, out_idx, out_val, cs, s);
+    if (e <= 12) return launch_cluster<12>(wmd, n, k, out_idx, out_val, cs, s);
+    if (e <= 16) return launch_cluster<16>(wmd, n, k, out_idx, out_val, cs, s);
+    if (e <= 20) return launch_cluster<20>(wmd, n, k, out_idx, out_val, cs, s);
+    if (e <= 24) return launch_cluster<24>(wmd, n, k, out_idx, out_val, cs, s);
+    if (e <= 28) return launch_cluster<28>(wmd, n, k, out_idx, out_val, cs, s);
+    return launch_cluster<32>(wmd, n, k, out_idx, out_val, cs, s);
   }
   if (N <= kCacheMax) {
     cfg.blockDim = dim3(kThreadsCached);

@@ -52,11 +52,12 @@ def _values(n, kind, seed):
 
 
 @pytest.mark.parametrize("n", [1, 2, 100, 511, 512, 513, 1023, 1024, 1025, 5000, 12288, 12289,
-                               16384, 16385, 200_000])
+                               16384, 16385, 50_000, 131_072, 131_073, 200_000, 262_144, 262_145])
 @pytest.mark.parametrize("kind", ["wmd", "ties", "dense"])
 def test_selection_is_bit_exact(wmd, n, kind):
-    """Both selection kernels (keys in registers for N <= 16384 and k <= 256,
-    the shared-memory / streamed radix select otherwise) at their edges."""
+    """Every selection kernel at its edges: keys in registers of one CTA (N <=
+    16384, k <= 256), of a thread-block cluster (N up to 8 or 16 CTAs x 16384,
+    k <= 256), and the shared-memory / streamed radix select otherwise."""
     v = _values(n, kind, n)
     for k in sorted({1, min(7, n), min(100, n), min(256, n), min(257, n), min(1024, n)}):
         ids, vals = _select(wmd, v, k)
@@ -67,7 +68,7 @@ def test_selection_is_bit_exact(wmd, n, kind):
 
 @pytest.mark.parametrize("kind", ["nan", "equal"])
 def test_all_equal_values_give_the_lowest_ids(wmd, kind):
-    for n in (50, 600, 3000, 16384, 20000):
+    for n in (50, 600, 3000, 16384, 20000, 150_000):
         v = _values(n, kind, 0)
         k = min(64, n - 1)
         ids, vals = _select(wmd, v, k)
