@@ -394,7 +394,7 @@ __global__ void __launch_bounds__(NT, 1)
   }
 }
 
-// ---------------------------------------------------------------- small N, k <= 256
+// ---------------------------------------------------------------- small N
 // N <= kSmallThreads * kSmallE keys, kept in registers: thread t holds keys
 // t E ... t E + E - 1 (E = ceil(N / 1024), a compile-time count so that no
 // loop over a thread's keys runs empty slots), and thread order is
@@ -412,11 +412,71 @@ constexpr int kSmallBins = 1 << kSmallBits;
 constexpr int kSmallCand = 64;     // candidates ranked directly (16 threads each)
 constexpr int64_t kSmallMaxN = (int64_t)kSmallThreads * kSmallE;
 static_assert(kSmallBins == 2 * kSmallThreads, "two bins per thread in the scan");
-static_assert(kSmallCand * 8 == kSmallThreads && kRankSortMax * 2 == kSmallThreads, "rank split");
+static_assert(kSmallCand * 8 == kSmallThreads && kSmallThreads % kRankSortMax == 0, "rank split");
 
 __device__ __forceinline__ bool before(unsigned long long ka, int ia, unsigned long long kb, int ib) {
   return ka < kb || (ka == kb && ia < ib);
 }
+
+// The k taken (keys and ids in s_key / s_idx, any order, all distinct by
+// (key, id)), written out ordered by (key, document id), by a whole block of
+// NT threads: rank counting, NT / 256 threads per entry, for k <= 256; a
+// bitonic sort of the next power of two for larger k.
+template <int NT>
+__device__ __forceinline__ void order_taken(unsigned long long* s_key, int* s_idx, int k,
+                                            const double* wmd, int N, int64_t* out_idx,
+                                            double* out_val) {
+  const int tid = threadIdx.x;
+  if (k <= kRankSortMax) {
+    constexpr int kPer = NT / kRankSortMax;  // threads per entry (a power of two)
+    const int en = tid / kPer, part = tid % kPer;
+    unsigned long long kt = 0;
+    int it = 0, rank = 0;
+    if (en < k) {
+      kt = s_key[en];
+      it = s_idx[en];
+      for (int j = part; j < k; j += kPer) rank += before(s_key[j], s_idx[j], kt, it) ? 1 : 0;
+    }
+#pragma unroll
+    for (int off = 1; off < kPer; off <<= 1) rank += __shfl_xor_sync(0xffffffffu, rank, off);
+    if (en < k && part == 0) {
+      out_idx[rank] = it;
+      out_val[rank] = (it >= 0 && it < N) ? wmd[it] : __longlong_as_double(0x7ff8000000000000ll);
+    }
+    return;
+  }
+  int P = 1;
+  while (P < k) P <<= 1;
+  for (int t = k + tid; t < P; t += NT) {
+    s_key[t] = ~0ull;
+    s_idx[t] = 0x7fffffff;
+  }
+  __syncthreads();
+  for (int size = 2; size <= P; size <<= 1) {
+    for (int stride = size >> 1; stride > 0; stride >>= 1) {
+      for (int a = tid; a < P; a += NT) {
+        const int b = a ^ stride;
+        if (b > a) {
+          const unsigned long long ka = s_key[a], kb = s_key[b];
+          const int ia = s_idx[a], ib = s_idx[b];
+          if (before(kb, ib, ka, ia) == ((a & size) == 0)) {
+            s_key[a] = kb;
+            s_key[b] = ka;
+            s_idx[a] = ib;
+            s_idx[b] = ia;
+          }
+        }
+      }
+      __syncthreads();
+    }
+  }
+  for (int t = tid; t < k; t += NT) {
+    const int j = s_idx[t];
+    out_idx[t] = j;
+    out_val[t] = (j >= 0 && j < N) ? wmd[j] : __longlong_as_double(0x7ff8000000000000ll);
+  }
+}
+
 
 template <int E>
 __global__ void __launch_bounds__(kSmallThreads, 1)
@@ -427,8 +487,8 @@ __global__ void __launch_bounds__(kSmallThreads, 1)
   __shared__ unsigned long long s_min[kW], s_max[kW];
   __shared__ unsigned s_sel[3];   // bin, keys below it, keys in it
   __shared__ unsigned s_taken, s_ncand;
-  __shared__ unsigned long long s_key[kRankSortMax];
-  __shared__ int s_idx[kRankSortMax];
+  __shared__ unsigned long long s_key[kTopkMaxK];
+  __shared__ int s_idx[kTopkMaxK];
   __shared__ unsigned long long c_key[kSmallCand];
   __shared__ int c_idx[kSmallCand];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -551,7 +611,7 @@ __global__ void __launch_bounds__(kSmallThreads, 1)
   for (int e = 0; e < E; ++e) {
     if (((valid >> e) & 1u) && (key[e] & mask) < prefix) {
       const unsigned slot = atomicAdd(&s_taken, 1u);
-      if (slot < (unsigned)kRankSortMax) {  // always: fewer than k lie below
+      if (slot < (unsigned)kTopkMaxK) {  // always: fewer than k lie below
         s_key[slot] = key[e];
         s_idx[slot] = i0 + e;
       }
@@ -582,7 +642,7 @@ __global__ void __launch_bounds__(kSmallThreads, 1)
     }
 #pragma unroll
     for (int off = 1; off < 8; off <<= 1) r += __shfl_xor_sync(0xffffffffu, r, off);
-    if (c < m && part == 0 && r < need && base + r < (unsigned)kRankSortMax) {
+    if (c < m && part == 0 && r < need && base + r < (unsigned)kTopkMaxK) {
       s_key[base + r] = kt;
       s_idx[base + r] = it;
     }
@@ -614,7 +674,7 @@ __global__ void __launch_bounds__(kSmallThreads, 1)
 #pragma unroll
     for (int e = 0; e < E; ++e) {
       if ((cm >> e) & 1u) {
-        if (r < need && base + r < (unsigned)kRankSortMax) {
+        if (r < need && base + r < (unsigned)kTopkMaxK) {
           s_key[base + r] = key[e];
           s_idx[base + r] = i0 + e;
         }
@@ -624,24 +684,10 @@ __global__ void __launch_bounds__(kSmallThreads, 1)
   }
   __syncthreads();
 
-  // the k taken, ordered by (key, document id): entry tid / 2, its rank
-  // summed over 2 threads
-  const int en = tid >> 1, part = tid & 1;
-  unsigned long long kt = 0;
-  int it = 0, rank = 0;
-  if (en < k) {
-    kt = s_key[en];
-    it = s_idx[en];
-    for (int j = part; j < k; j += 2) rank += before(s_key[j], s_idx[j], kt, it) ? 1 : 0;
-  }
-  rank += __shfl_xor_sync(0xffffffffu, rank, 1);
-  if (en < k && part == 0) {
-    out_idx[rank] = it;
-    out_val[rank] = (it >= 0 && it < N) ? wmd[it] : __longlong_as_double(0x7ff8000000000000ll);
-  }
+  order_taken<kSmallThreads>(s_key, s_idx, k, wmd, N, out_idx, out_val);
 }
 
-// ---------------------------------------------------------------- large N, k <= 256
+// ---------------------------------------------------------------- large N
 // The same selection spread over a thread-block cluster of CS CTAs (16 where
 // the GPU allows clusters that large, else 8), one SM each: CTA r keeps keys
 // [r S, (r + 1) S) in registers (S = ceil(N / CS), E keys per thread, 512
@@ -676,8 +722,8 @@ __global__ void __launch_bounds__(kClusterThreads, 1)
   __shared__ unsigned blk_cnt;
   __shared__ unsigned s_sel[3];   // CTA 0: bin, keys below it, keys in it
   __shared__ unsigned s_taken, s_ncand;
-  __shared__ unsigned long long s_key[kRankSortMax];
-  __shared__ int s_idx[kRankSortMax];
+  __shared__ unsigned long long s_key[kTopkMaxK];
+  __shared__ int s_idx[kTopkMaxK];
   __shared__ unsigned long long c_key[kSmallCand];
   __shared__ int c_idx[kSmallCand];
   static_assert(kSmallBins == 2 * kClusterThreads, "two bins per thread in the scan");
@@ -829,7 +875,7 @@ __global__ void __launch_bounds__(kClusterThreads, 1)
   for (int e = 0; e < E; ++e) {
     if (((valid >> e) & 1u) && (key[e] & mask) < prefix) {
       const unsigned slot = atomicAdd(r_taken, 1u);
-      if (slot < (unsigned)kRankSortMax) {  // always: fewer than k lie below
+      if (slot < (unsigned)kTopkMaxK) {  // always: fewer than k lie below
         r_key[slot] = key[e];
         r_idx[slot] = i0 + e;
       }
@@ -864,7 +910,7 @@ __global__ void __launch_bounds__(kClusterThreads, 1)
     }
 #pragma unroll
     for (int off = 1; off < 8; off <<= 1) r += __shfl_xor_sync(0xffffffffu, r, off);
-    if (c < m && part == 0 && r < need && base + r < (unsigned)kRankSortMax) {
+    if (c < m && part == 0 && r < need && base + r < (unsigned)kTopkMaxK) {
       s_key[base + r] = kt;
       s_idx[base + r] = it;
     }
@@ -900,7 +946,7 @@ __global__ void __launch_bounds__(kClusterThreads, 1)
 #pragma unroll
     for (int e = 0; e < E; ++e) {
       if ((cm >> e) & 1u) {
-        if (rr < need && base + rr < (unsigned)kRankSortMax) {
+        if (rr < need && base + rr < (unsigned)kTopkMaxK) {
           r_key[base + rr] = key[e];
           r_idx[base + rr] = i0 + e;
         }
@@ -913,19 +959,7 @@ __global__ void __launch_bounds__(kClusterThreads, 1)
   __syncthreads();
 
   // CTA 0: the k taken, ordered by (key, document id)
-  const int en = tid >> 1, part = tid & 1;
-  unsigned long long kt = 0;
-  int it = 0, rk = 0;
-  if (en < k) {
-    kt = s_key[en];
-    it = s_idx[en];
-    for (int j = part; j < k; j += 2) rk += before(s_key[j], s_idx[j], kt, it) ? 1 : 0;
-  }
-  rk += __shfl_xor_sync(0xffffffffu, rk, 1);
-  if (en < k && part == 0) {
-    out_idx[rk] = it;
-    out_val[rk] = (it >= 0 && it < N) ? wmd[it] : __longlong_as_double(0x7ff8000000000000ll);
-  }
+  order_taken<kClusterThreads>(s_key, s_idx, k, wmd, N, out_idx, out_val);
 }
 
 template <int E>
@@ -1012,7 +1046,7 @@ cudaError_t launch_topk(const double* wmd, int64_t N, int k, int64_t* out_idx, d
   attr[0].val.programmaticStreamSerializationAllowed = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  if (N <= kSmallMaxN && k <= kRankSortMax) {
+  if (N <= kSmallMaxN) {
     cfg.blockDim = dim3(kSmallThreads);
     cfg.dynamicSmemBytes = 0;
     const int n = (int)N;
@@ -1031,7 +1065,7 @@ cudaError_t launch_topk(const double* wmd, int64_t N, int k, int64_t* out_idx, d
     if (e <= 24) return go(topk_small_kernel<24>);
     return go(topk_small_kernel<32>);
   }
-  const int cs = N > kSmallMaxN && k <= kRankSortMax ? cluster_size_for_topk() : 0;
+  const int cs = N > kSmallMaxN ? cluster_size_for_topk() : 0;
   if (cs > 0 && N <= (int64_t)cs * kClusterThreads * kClusterMaxE) {
     const int n = (int)N;
     const int e = ((n + cs - 1) / cs + kClusterThreads - 1) / kClusterThreads;
