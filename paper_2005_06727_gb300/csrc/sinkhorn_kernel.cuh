@@ -712,15 +712,22 @@ cudaError_t launch_var(const LoopParams& p, int n_items, int nq, cudaStream_t s)
   auto kern = sinkhorn_fused_kernel<Cf::VR, Cf::PI, Cf::RMAX, Cf::MINB, Cf::NW, CONV, KT>;
   if (n_items == 0 || nq == 0) return cudaSuccess;
   // the same shared-memory carveout as the cdist kernel, so that the first
-  // CTAs can share SMs with it (once per process, never inside a capture:
-  // the first launch of a shape always runs eagerly)
-  static std::once_flag once;
-  static cudaError_t attr_err = cudaSuccess;
-  std::call_once(once, [&] {
-    attr_err = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
-                                    (int)cudaSharedmemCarveoutMaxShared);
-  });
-  if (attr_err != cudaSuccess) return attr_err;
+  // CTAs can share SMs with it (once per device, never inside a capture: the
+  // first launch of a shape always runs eagerly)
+  static std::mutex mu;
+  static bool set_on[64] = {};
+  {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) dev = 0;
+    dev = dev < 64 ? dev : 63;
+    std::lock_guard<std::mutex> lock(mu);
+    if (!set_on[dev]) {
+      const cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                                 (int)cudaSharedmemCarveoutMaxShared);
+      if (e != cudaSuccess) return e;
+      set_on[dev] = true;
+    }
+  }
   // programmatic dependent launch: CTAs may start while the kernel before
   // them (the cdist kernel) finishes; they wait for its results in solve()
   cudaLaunchConfig_t cfg = {};

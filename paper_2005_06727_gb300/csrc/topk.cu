@@ -982,41 +982,62 @@ cudaError_t launch_cluster(const double* wmd, int n, int k, int64_t* out_idx, do
   return cudaLaunchKernelEx(&cfg, topk_cluster_kernel<E>, wmd, n, k, out_idx, out_val);
 }
 
-// The cluster size the selection uses: 16 CTAs where the GPU can run such a
-// cluster (a non-portable size), else 8; 0 if neither fits.
-int cluster_size_for_topk() {
-  static std::once_flag once;
-  static int cs = 0;
-  std::call_once(once, [] {
-    const void* kerns[] = {(const void*)topk_cluster_kernel<4>, (const void*)topk_cluster_kernel<8>,
-                           (const void*)topk_cluster_kernel<12>, (const void*)topk_cluster_kernel<16>,
-                           (const void*)topk_cluster_kernel<20>, (const void*)topk_cluster_kernel<24>,
-                           (const void*)topk_cluster_kernel<28>, (const void*)topk_cluster_kernel<32>};
-    bool ok16 = true;
-    for (const void* f : kerns)
-      ok16 = ok16 && cudaFuncSetAttribute(f, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) ==
-                         cudaSuccess;
-    for (int want : {16, 8}) {
-      if (want == 16 && !ok16) continue;
-      cudaLaunchConfig_t cfg = {};
-      cfg.gridDim = dim3((unsigned)want);
-      cfg.blockDim = dim3(kClusterThreads);
-      cudaLaunchAttribute attr[1];
-      attr[0].id = cudaLaunchAttributeClusterDimension;
-      attr[0].val.clusterDim.x = (unsigned)want;
-      attr[0].val.clusterDim.y = 1;
-      attr[0].val.clusterDim.z = 1;
-      cfg.attrs = attr;
-      cfg.numAttrs = 1;
-      int n = 0;
-      if (cudaOccupancyMaxActiveClusters(&n, topk_cluster_kernel<32>, &cfg) == cudaSuccess && n > 0) {
-        cs = want;
-        break;
-      }
+// Per device, once: the dynamic shared memory the 8-bit kernels need, and the
+// cluster size the selection uses (16 CTAs where the GPU can run such a
+// cluster, a non-portable size; else 8; 0 if neither fits).  Function
+// attributes are set per device, so a process that selects on several GPUs
+// sets them on each.
+struct TopkSetup {
+  bool done = false;
+  cudaError_t err = cudaSuccess;
+  int cs = 0;
+};
+
+TopkSetup topk_setup() {
+  static std::mutex mu;
+  static TopkSetup per_dev[64];
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) dev = 0;
+  dev = dev < 64 ? dev : 63;
+  std::lock_guard<std::mutex> lock(mu);
+  TopkSetup& st = per_dev[dev];
+  if (st.done) return st;
+  const size_t lists = 2 * (size_t)kCandMax * sizeof(int);
+  st.err = cudaFuncSetAttribute(topk_kernel<true, kThreadsCached>,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)(kCacheMax * sizeof(unsigned long long) + lists));
+  if (st.err == cudaSuccess)
+    st.err = cudaFuncSetAttribute(topk_kernel<false, kThreadsStream>,
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lists);
+  const void* kerns[] = {(const void*)topk_cluster_kernel<4>, (const void*)topk_cluster_kernel<8>,
+                         (const void*)topk_cluster_kernel<12>, (const void*)topk_cluster_kernel<16>,
+                         (const void*)topk_cluster_kernel<20>, (const void*)topk_cluster_kernel<24>,
+                         (const void*)topk_cluster_kernel<28>, (const void*)topk_cluster_kernel<32>};
+  bool ok16 = true;
+  for (const void* f : kerns)
+    ok16 = ok16 && cudaFuncSetAttribute(f, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) ==
+                       cudaSuccess;
+  for (int want : {16, 8}) {
+    if (want == 16 && !ok16) continue;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)want);
+    cfg.blockDim = dim3(kClusterThreads);
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = (unsigned)want;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    int n = 0;
+    if (cudaOccupancyMaxActiveClusters(&n, topk_cluster_kernel<32>, &cfg) == cudaSuccess && n > 0) {
+      st.cs = want;
+      break;
     }
-    cudaGetLastError();  // a refused size leaves no error behind
-  });
-  return cs;
+  }
+  cudaGetLastError();  // a refused cluster size leaves no error behind
+  st.done = true;
+  return st;
 }
 
 }  // namespace
@@ -1025,17 +1046,8 @@ cudaError_t launch_topk(const double* wmd, int64_t N, int k, int64_t* out_idx, d
                         cudaStream_t s) {
   if (k <= 0) return cudaSuccess;
   const size_t lists = 2 * (size_t)kCandMax * sizeof(int);
-  static std::once_flag once;
-  static cudaError_t attr_err = cudaSuccess;
-  std::call_once(once, [lists] {
-    attr_err = cudaFuncSetAttribute(topk_kernel<true, kThreadsCached>,
-                                    cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    (int)(kCacheMax * sizeof(unsigned long long) + lists));
-    if (attr_err == cudaSuccess)
-      attr_err = cudaFuncSetAttribute(topk_kernel<false, kThreadsStream>,
-                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lists);
-  });
-  if (attr_err != cudaSuccess) return attr_err;
+  const TopkSetup st = topk_setup();
+  if (st.err != cudaSuccess) return st.err;
   // programmatic dependent launch: the CTA may become resident while the
   // kernel that writes WMD[] (the fused loop) drains; it waits for it first
   cudaLaunchConfig_t cfg = {};
@@ -1065,7 +1077,7 @@ cudaError_t launch_topk(const double* wmd, int64_t N, int k, int64_t* out_idx, d
     if (e <= 24) return go(topk_small_kernel<24>);
     return go(topk_small_kernel<32>);
   }
-  const int cs = N > kSmallMaxN ? cluster_size_for_topk() : 0;
+  const int cs = N > kSmallMaxN ? st.cs : 0;
   if (cs > 0 && N <= (int64_t)cs * kClusterThreads * kClusterMaxE) {
     const int n = (int)N;
     const int e = ((n + cs - 1) / cs + kClusterThreads - 1) / kClusterThreads;
