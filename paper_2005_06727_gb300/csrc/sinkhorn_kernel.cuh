@@ -336,8 +336,9 @@ __device__ __forceinline__ void solve(const LoopParams& p, const TeamCtx& t) {
   // per column seeds the SpMM sums of padding columns with 1 so that 1/x stays
   // finite there (their r is 0, so u = r / x = 0, and K = 0 keeps them out of
   // every sum); bit 2q+h of `seed` marks those columns
-  // one-warp teams of narrow queries finish x through shared memory (below);
-  // wider ones keep the query weights of their columns in registers
+  // narrow queries finish x through shared memory (below: one-warp teams
+  // entirely, teams of several warps within each warp); wider ones keep the
+  // query weights of their columns in registers
   constexpr bool kSmemFinish = VR <= 32;
   float2 rr[C2], u[C2];
   uint32_t seed = 0;
@@ -508,13 +509,31 @@ __device__ __forceinline__ void solve(const LoopParams& p, const TeamCtx& t) {
       }
     } else if (!last) {
       // x: sum over the PW row groups of the warp ...
+      if constexpr (kSmemFinish) {
+        // (teams of several warps, narrow queries) through shared memory, as
+        // for one-warp teams: every lane stores its partials, lane L sums
+        // column L over the row groups in order and leaves the warp's sum in
+        // the team's exchange buffer
 #pragma unroll
-      for (int off = PI; off < 32; off <<= 1) {
+        for (int h = 0; h < C2 / 2; ++h)
+          *reinterpret_cast<float4*>(&wpart[t.pw * kWS + lane_col(2 * h)]) =
+              make_float4(xp[2 * h].x, xp[2 * h].y, xp[2 * h + 1].x, xp[2 * h + 1].y);
+        __syncwarp();
+        if (t.lane < VR) {
+          float xs = 0.f;
 #pragma unroll
-        for (int q = 0; q < C2; ++q) {
-          const float2 o = make_float2(__shfl_xor_sync(0xffffffffu, xp[q].x, off),
-                                       __shfl_xor_sync(0xffffffffu, xp[q].y, off));
-          xp[q] = __fadd2_rn(xp[q], o);
+          for (int k2 = 0; k2 < PW; ++k2) xs += wpart[k2 * kWS + t.lane];
+          red[t.warp * VR + t.lane] = xs;
+        }
+      } else {
+#pragma unroll
+        for (int off = PI; off < 32; off <<= 1) {
+#pragma unroll
+          for (int q = 0; q < C2; ++q) {
+            const float2 o = make_float2(__shfl_xor_sync(0xffffffffu, xp[q].x, off),
+                                         __shfl_xor_sync(0xffffffffu, xp[q].y, off));
+            xp[q] = __fadd2_rn(xp[q], o);
+          }
         }
       }
       // u = 1 / x with x = diag(1/r) (K v):  u_i = r_i / (K v)_i
@@ -532,7 +551,7 @@ __device__ __forceinline__ void solve(const LoopParams& p, const TeamCtx& t) {
         // ... and over the warps of the team: each lane of the team finishes
         // whole columns (the team's partial sums in fixed warp order, so
         // deterministic, then u), and every lane reads back its columns' u
-        if (t.pw == 0) {
+        if (!kSmemFinish && t.pw == 0) {
 #pragma unroll
           for (int q = 0; q < C2; ++q)
             *reinterpret_cast<float2*>(&red[t.warp * VR + lane_col(q)]) = xp[q];
