@@ -224,7 +224,8 @@ wmd_status wmd_corpus_load(const float* vecs, int64_t V, int32_t d,
  *   only, renumbered from 0 (document doc_begin + j of c is document j of
  *   the shard), with the whole vocabulary.  A shard's results equal the
  *   corresponding slice of the unsharded corpus's bit for bit when both use
- *   the same fused-loop tile variant (wmd_set_loop_variant).  Errors as
+ *   the same fused-loop tile variant and partition (wmd_set_loop_variant,
+ *   wmd_set_loop_partition).  Errors as
  *   wmd_corpus_load, plus WMD_ERR_INVALID_ARG for a range outside [0, N].
  * The k nearest documents of the whole corpus are the k nearest among the
  * shards' own k nearest (ids shifted by doc_begin): wmd_topk over the
@@ -357,7 +358,11 @@ wmd_status wmd_query_device_tol(wmd_corpus* corpus, const int32_t* d_q_ids,
  *   thread's current device, stream-ordered on `stream` (NULL = legacy
  *   default stream), asynchronous.  1 <= k <= min(N, 1024), else
  *   WMD_ERR_INVALID_ARG; k = 0 does nothing; N above 2^31 - 1 gives
- *   WMD_ERR_UNSUPPORTED.  Allocates nothing.
+ *   WMD_ERR_UNSUPPORTED.  Allocates nothing.  The selection runs in one CTA
+ *   for N <= 16384, on a thread-block cluster of 16 (else 8) CTAs for N up
+ *   to 262144 where the GPU can run such clusters, and in one CTA otherwise;
+ *   it is launched as a programmatic dependent of the work before it on the
+ *   stream and reads d_wmd only after that work has completed.
  * wmd_query_device_topk: wmd_query_device (same arguments; d_out receives
  *   all N values) followed by wmd_topk on its output, on the corpus's device.
  * ------------------------------------------------------------------------- */
