@@ -51,7 +51,7 @@ def parse():
                     help="comma-separated extra legs to run after the timed step")
     ap.add_argument("--no-systems", action="store_true",
                     help="skip the batched and served measurements")
-    ap.add_argument("--serve-requests", type=int, default=1000,
+    ap.add_argument("--serve-requests", type=int, default=2000,
                     help="Poisson requests per offered rate (a fifth of them at 0.1x capacity)")
     ap.add_argument("--serving-workload", choices=["paper", "serving"], default="serving",
                     help="corpus of the serving leg: the full serving configuration (default, "
@@ -411,7 +411,7 @@ def batch_errors_vs_oracle(w, c, qs, res, n_docs=200):
             "sample": f"every query on {docs.size} seeded documents (20 longest and 20 shortest included)"}
 
 
-def bench_serving(wmd, device, n_requests=1000, seed=11, workload="serving", n_checked=16):
+def bench_serving(wmd, device, n_requests=2000, seed=11, workload="serving", n_checked=16):
     """Poisson arrivals (v_r ~ U[5,200]) against the full serving corpus (or
     the paper-shaped one): latency p50/p99 and throughput of the
     continuous-batching server at 0.1x to 1.2x of its measured capacity, the
@@ -448,7 +448,7 @@ def bench_serving(wmd, device, n_requests=1000, seed=11, workload="serving", n_c
         rates = []
         for frac in (0.1, 0.5, 0.9, 1.2):
             rate = frac * capacity
-            n_rate = max(n_requests // 5, 16) if frac < 0.5 else n_requests
+            n_rate = max(n_requests // 10, 16) if frac < 0.5 else n_requests
             arrivals = np.cumsum(rng.exponential(1.0 / rate, n_rate))
             sub_t, done_t, tickets, qidx = {}, {}, [], {}
             lock = th.Lock()
@@ -528,7 +528,7 @@ def bench_serving(wmd, device, n_requests=1000, seed=11, workload="serving", n_c
     return {"workload": (f"serving against {w.name} corpus: V={w.V} N={w.N} docs of "
                          f"{w.doc_lo}-{w.doc_hi} words, queries v_r U[5,200], lambda={w.lam:g}, "
                          f"max_iter={w.max_iter}, Poisson arrivals, {n_requests} requests per rate "
-                         f"({max(n_requests // 5, 16)} at 0.1x)"),
+                         f"({max(n_requests // 10, 16)} at 0.1x)"),
             "error_vs_oracle": err,
             "one_at_a_time_qps": single_qps, "capacity_qps": capacity,
             "capacity_wmds_per_s": capacity * c.N, "one_at_a_time_wmds_per_s": single_qps * c.N,
