@@ -1,7 +1,16 @@
 // Top-k nearest documents: the k smallest WMD values of one query and their
 // document ids (the k-nearest-neighbour use of the distance, Sec. 1 and 2).
 //
-// One CTA of 1024 threads selects from WMD[N] (written by the fused loop):
+// Three kernels, by the size of WMD[N] (written by the fused loop), all
+// launched as programmatic dependents of the work before them:
+//   * N <= 16384: one CTA keeps the keys in registers (topk_small_kernel);
+//   * N <= 262144: the same over a thread-block cluster of 16 (or 8) CTAs,
+//     histograms merged through distributed shared memory
+//     (topk_cluster_kernel);
+//   * larger N: the kernel described next (topk_kernel).
+// Each kernel's own comment gives its steps.
+//
+// topk_kernel: one CTA of 1024 threads:
 //   1. every value is mapped to a 64-bit key whose unsigned order is the
 //      numeric order (-0 counts as +0, every NaN after every number); one
 //      sweep finds the smallest and largest key, whose common leading bits
