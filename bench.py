@@ -349,16 +349,28 @@ def run_reference(args, w):
 
 
 # ------------------------------------------------------------------ batched and served
+# the fused loop's query-width classes (the width of its register tile)
+LOOP_CLASS_WIDTHS = (8, 16, 32, 64, 96, 128, 192, 256)
+
+
+def autotune_classes(corpus, qs, w):
+    """Autotune every width class that one of the queries qs falls in (with
+    the first such query), untimed."""
+    lo = 0
+    for vr in LOOP_CLASS_WIDTHS:
+        q = next((q for q in qs if lo < len(q[0]) <= vr), None)
+        if q is not None:
+            corpus.autotune(q[0], q[1], w.lam, w.max_iter)
+        lo = vr
+
+
 def bench_batched(wmd, device, reps=2, with_oracle=True):
     """256 queries of v_r ~ U[5,128] against N=20000 documents: one at a time
     through wmd_query versus one wmd_query_batch call (graph replayed)."""
     wb = synth.BATCHED
     vecs, c, qs = synth.make_workload(wb)
     corpus = wmd.Corpus.from_synth(vecs, c, device=device)
-    for vr in (8, 16, 32, 64, 128):  # autotune every width class the batch uses
-        q = next((q for q in qs if (len(q[0]) <= vr and len(q[0]) > vr // 2)), None)
-        if q is not None:
-            corpus.autotune(q[0], q[1], wb.lam, wb.max_iter)
+    autotune_classes(corpus, qs, wb)  # every width class the batch uses
     out = np.empty(c.N, np.float64)
     for q in qs[:4]:
         corpus.query(q[0], q[1], wb.lam, wb.max_iter, out=out)
@@ -425,10 +437,7 @@ def bench_serving(wmd, device, n_requests=2000, seed=11, workload="serving", n_c
     qs = [synth.make_query(w.V, 200 if i == 0 else int(rng.integers(5, 201)), 50_000 + i)
           for i in range(64)]
     served = {}   # query index -> its first served result (n_checked distinct queries)
-    for vr in (8, 16, 32, 64, 128, 256):
-        q = next((q for q in qs if (len(q[0]) <= vr and len(q[0]) > vr // 2)), None)
-        if q is not None:
-            corpus.autotune(q[0], q[1], w.lam, w.max_iter)
+    autotune_classes(corpus, qs, w)
     out = np.empty(c.N, np.float64)
     for q in qs[:4]:
         corpus.query(q[0], q[1], w.lam, w.max_iter, out=out)

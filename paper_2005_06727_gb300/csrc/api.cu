@@ -126,9 +126,10 @@ void drop_captured(wmd_corpus* c) {
 }
 
 // ---------------------------------------------------------------- autotune cache
-// One line per tuned choice: "wmd-loop V d N nnz U class precision variant
-// fill" (fill: the partition; lines without it mean 100).  A corpus applies
-// the lines recorded for its own shape; the last one wins.
+// One line per tuned choice: "wmd-loop V d N nnz U width precision variant
+// fill" (width: the class's loop tile width, kClassVR; fill: the partition;
+// lines without it mean 100).  A corpus applies the lines recorded for its
+// own shape; the last one wins.
 void load_autotune_cache(wmd_corpus* c) {
   if (c->autotune_cache.empty()) return;
   FILE* f = std::fopen(c->autotune_cache.c_str(), "r");
@@ -136,12 +137,13 @@ void load_autotune_cache(wmd_corpus* c) {
   char line[256];
   while (std::fgets(line, sizeof line, f)) {
     long long V, N, nnz, U;
-    int d, cls, prec, var, fill = 100;
+    int d, width, prec, var, fill = 100;
     const int got = std::sscanf(line, "wmd-loop %lld %d %lld %lld %lld %d %d %d %d", &V, &d, &N,
-                                &nnz, &U, &cls, &prec, &var, &fill);
+                                &nnz, &U, &width, &prec, &var, &fill);
     if (got != 8 && got != 9) continue;  // lines without a partition keep fill = 100
     if (V != c->V || d != c->d || N != c->N || nnz != c->nnz || U != c->U) continue;
-    if (cls < 0 || cls >= kNumClasses || prec < 0 || prec > 1 || var < 0 ||
+    const int cls = class_of_width(width);
+    if (cls < 0 || prec < 0 || prec > 1 || var < 0 ||
         var >= kClassVariants[cls] || !valid_fill(fill))
       continue;
     c->loop_variant[cls][prec] = var;
@@ -157,7 +159,7 @@ void save_autotune_choice(const wmd_corpus* c, int cls, int prec, int var) {
   FILE* f = std::fopen(c->autotune_cache.c_str(), "a");
   if (!f) return;
   std::fprintf(f, "wmd-loop %lld %d %lld %lld %lld %d %d %d %d\n", (long long)c->V, (int)c->d,
-               (long long)c->N, (long long)c->nnz, (long long)c->U, cls, prec, var,
+               (long long)c->N, (long long)c->nnz, (long long)c->U, kClassVR[cls], prec, var,
                (int)c->sched[cls][var].fill);
   std::fclose(f);
 }
@@ -179,7 +181,7 @@ wmd_status check_ws(const wmd_corpus* c, int v_r, wmd_precision prec, const void
   if (!ws) return set_error(WMD_ERR_INVALID_ARG, "workspace is NULL");
   if (reinterpret_cast<uintptr_t>(ws) % 256)
     return set_error(WMD_ERR_INVALID_ARG, "workspace must be 256-byte aligned");
-  const WsLayout L = ws_layout(c, kClassVR[vr_class(v_r)], prec);
+  const WsLayout L = ws_layout(c, kClassKVR[vr_class(v_r)], prec);
   if (ws_bytes < L.total) return set_error(WMD_ERR_INVALID_ARG, "workspace too small");
   return WMD_OK;
 }
@@ -575,7 +577,7 @@ wmd_status wmd_corpus_get_info(const wmd_corpus* c, wmd_corpus_info* out) {
 
 size_t wmd_workspace_bytes(const wmd_corpus* c, int32_t v_r, wmd_precision prec) {
   if (!c || v_r <= 0 || v_r > WMD_MAX_VR) return 0;
-  return ws_layout(c, kClassVR[vr_class(v_r)], prec).total;
+  return ws_layout(c, kClassKVR[vr_class(v_r)], prec).total;
 }
 
 wmd_status wmd_build_kernel_matrix(wmd_corpus* c, const int32_t* d_q_ids, const float* d_q_w,
@@ -587,7 +589,7 @@ wmd_status wmd_build_kernel_matrix(wmd_corpus* c, const int32_t* d_q_ids, const 
   if (!d_q_ids || !d_q_w) return set_error(WMD_ERR_INVALID_ARG, "NULL query pointer");
   if ((st = check_ws(c, v_r, prec, d_ws, ws_bytes)) != WMD_OK) return st;
   DeviceGuard g(c->device);
-  const int VR = kClassVR[vr_class(v_r)];
+  const int VR = kClassKVR[vr_class(v_r)];
   const WsLayout L = ws_layout(c, VR, prec);
   char* ws = static_cast<char*>(d_ws);
   cudaStream_t s = static_cast<cudaStream_t>(stream);
@@ -611,7 +613,7 @@ wmd_status sinkhorn_loop(wmd_corpus* c, int32_t v_r, int32_t max_iter, wmd_preci
   if ((st = check_ws(c, v_r, prec, d_ws, ws_bytes)) != WMD_OK) return st;
   DeviceGuard g(c->device);
   const int cls = vr_class(v_r);
-  const int VR = kClassVR[cls];
+  const int VR = kClassKVR[cls];
   const WsLayout L = ws_layout(c, VR, prec);
   char* ws = static_cast<char*>(d_ws);
   const float* r = reinterpret_cast<const float*>(ws + L.r_off);
@@ -660,7 +662,7 @@ wmd_status wmd_query_device_tol(wmd_corpus* c, const int32_t* d_q_ids, const flo
   if (st != WMD_OK) return st;
   DeviceGuard g(c->device);
   const int cls = vr_class(v_r);
-  const int VR = kClassVR[cls];
+  const int VR = kClassKVR[cls];
   const WsLayout L = ws_layout(c, VR, prec);
   char* ws = static_cast<char*>(d_ws);
   const float* r = reinterpret_cast<const float*>(ws + L.r_off);

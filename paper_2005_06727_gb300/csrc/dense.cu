@@ -151,7 +151,7 @@ extern "C" {
 
 size_t wmd_dense_workspace_bytes(const wmd_corpus* c, int32_t v_r) {
   if (!c || v_r <= 0 || v_r > WMD_MAX_VR) return 0;
-  return dense_layout(c, kClassVR[vr_class(v_r)]).total;
+  return dense_layout(c, kClassKVR[vr_class(v_r)]).total;
 }
 
 wmd_status wmd_dense_load_c(wmd_corpus* c, void* d_ws, size_t ws_bytes, void* stream) {
@@ -184,7 +184,7 @@ wmd_status wmd_query_dense(wmd_corpus* c, const int32_t* d_q_ids, const float* d
   if (!c) return set_error(WMD_ERR_INVALID_ARG, "corpus is NULL");
   if (v_r <= 0 || v_r > WMD_MAX_VR) return set_error(WMD_ERR_INVALID_ARG, "v_r out of range");
   if (max_iter < 0) return set_error(WMD_ERR_INVALID_ARG, "max_iter must be >= 0");
-  const int VR = kClassVR[vr_class(v_r)];
+  const int VR = kClassKVR[vr_class(v_r)];
   const DenseLayout L = dense_layout(c, VR);
   if (!d_ws || ws_bytes < L.total) return set_error(WMD_ERR_INVALID_ARG, "workspace too small");
   if (!d_out && c->N > 0) return set_error(WMD_ERR_INVALID_ARG, "d_out is NULL");

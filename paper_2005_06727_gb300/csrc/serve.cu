@@ -249,7 +249,7 @@ wmd_status compact(const wmd_corpus* c, const int32_t* ids, const float* w, int3
   out->w.resize(vr);
   out->v_r = vr;
   out->cls = vr_class(vr);
-  out->VR = kClassVR[out->cls];
+  out->VR = kClassKVR[out->cls];
   out->lambda = lambda;
   return WMD_OK;
 }

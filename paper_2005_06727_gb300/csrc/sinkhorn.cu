@@ -35,7 +35,9 @@ int rows_per_warp(int cls, int var) {
     case 2: return cls_rows<2>(var);
     case 3: return cls_rows<3>(var);
     case 4: return cls_rows<4>(var);
-    default: return cls_rows<5>(var);
+    case 5: return cls_rows<5>(var);
+    case 6: return cls_rows<6>(var);
+    default: return cls_rows<7>(var);
   }
 }
 
@@ -46,7 +48,9 @@ int warps_per_cta(int cls, int var) {
     case 2: return cls_warps<2>(var);
     case 3: return cls_warps<3>(var);
     case 4: return cls_warps<4>(var);
-    default: return cls_warps<5>(var);
+    case 5: return cls_warps<5>(var);
+    case 6: return cls_warps<6>(var);
+    default: return cls_warps<7>(var);
   }
 }
 

@@ -36,9 +36,14 @@ wmd_status cuda_error(cudaError_t e, const char* what);
   } while (0)
 
 // ---------------------------------------------------------------- query width classes
-// The query is padded to one of these widths (VR); K rows have VR entries.
-constexpr int kNumClasses = 6;
-constexpr int kClassVR[kNumClasses] = {8, 16, 32, 64, 128, 256};
+// The fused loop pads the query to one of these widths (its register tile,
+// kClassVR); the cdist kernel, K and the workspace use the power of two at or
+// above it (kClassKVR: K rows have that many entries, and the loop reads the
+// first kClassVR of them).  The 96- and 192-wide tiles save a quarter of the
+// loop's work for queries just above 64 and 128 words.
+constexpr int kNumClasses = 8;
+constexpr int kClassVR[kNumClasses] = {8, 16, 32, 64, 96, 128, 192, 256};
+constexpr int kClassKVR[kNumClasses] = {8, 16, 32, 64, 128, 128, 256, 256};
 
 inline int vr_class(int v_r) {
   for (int c = 0; c < kNumClasses; ++c)
@@ -46,10 +51,17 @@ inline int vr_class(int v_r) {
   return -1;
 }
 
+// The class whose loop tile is `width` wide, or -1.
+inline int class_of_width(int width) {
+  for (int c = 0; c < kNumClasses; ++c)
+    if (kClassVR[c] == width) return c;
+  return -1;
+}
+
 // Fused-loop tile variants per class (sinkhorn.cu) and the rows one warp of
 // variant `var` keeps in registers (row groups x rows per lane).
 constexpr int kMaxVariants = 2;
-constexpr int kClassVariants[kNumClasses] = {2, 2, 2, 2, 2, 2};
+constexpr int kClassVariants[kNumClasses] = {2, 2, 2, 2, 2, 2, 2, 2};
 int rows_per_warp(int cls, int var);
 int warps_per_cta(int cls, int var);  // 4 or 8
 
@@ -146,10 +158,10 @@ struct wmd_corpus {
 
 namespace wmd {
 
-// Workspace carve-up for one query of class VR: the padded query weights r
-// (VR floats) followed by lambda (float VR) and the final step's scale
-// -ln 2 / lambda (a double at float VR + 2); the query's error slots
-// (cdist_err_slots ints); and the word-major K (U x VR).
+// Workspace carve-up for one query whose K rows are VR wide (kClassKVR of its
+// class): the padded query weights r (VR floats) followed by lambda (float VR)
+// and the final step's scale -ln 2 / lambda (a double at float VR + 2); the
+// query's error slots (cdist_err_slots ints); and the word-major K (U x VR).
 struct WsLayout {
   size_t r_off, err_off, k_off, total;
   int n_err;
@@ -161,7 +173,7 @@ struct WsLayout {
 // slot that a memset clears first.
 constexpr int kRangeFlag = 0x20000000;
 constexpr float kRangeLimit = 87.33654f;  // -ln(FLT_MIN): K = exp(-lambda M) below is subnormal
-// Error slots one query of width class VR uses (the cdist kernel's CTAs over
+// Error slots one query of K width VR uses (the cdist kernel's CTAs over
 // all its column slices, or 1 for the CUDA-core kernel).
 int cdist_err_slots(const wmd_corpus* c, int VR);
 // CTAs of one tensor-core cdist launch.
