@@ -350,7 +350,7 @@ def run_reference(args, w):
 
 # ------------------------------------------------------------------ batched and served
 # the fused loop's query-width classes (the width of its register tile)
-LOOP_CLASS_WIDTHS = (8, 16, 32, 64, 96, 128, 192, 256)
+LOOP_CLASS_WIDTHS = (8, 16, 32, 48, 64, 96, 128, 192, 256)
 
 
 def autotune_classes(corpus, qs, w):

@@ -409,10 +409,10 @@ wmd_status wmd_query_dense(wmd_corpus* corpus, const int32_t* d_q_ids, const flo
 
 /* ---------------------------------------------------------------------------
  * Tile variants of the fused loop and their autotuner.  Every query width
- * class (v_r rounded up to 8, 16, 32, 64, 96, 128, 192 or 256: the width of
- * the loop's register tile; K itself is computed for v_r rounded up to a
- * power of two, and the 96- and 192-wide tiles read the first columns of
- * it) has one or more register-tile shapes for the fused SDDMM/SpMM loop
+ * class (v_r rounded up to 8, 16, 32, 48, 64, 96, 128, 192 or 256: the
+ * width of the loop's register tile; K itself is computed for v_r rounded up
+ * to a power of two, and the 48-, 96- and 192-wide tiles read the first
+ * columns of it) has one or more register-tile shapes for the fused SDDMM/SpMM loop
  * (same arithmetic, same results within rounding); they trade work per
  * cross-lane reduction against resident warps.  wmd_loop_variant_count: how many exist for queries of v_r
  * words.  wmd_set_loop_variant: use `variant` for v_r's class and `prec` on

@@ -37,7 +37,8 @@ int rows_per_warp(int cls, int var) {
     case 4: return cls_rows<4>(var);
     case 5: return cls_rows<5>(var);
     case 6: return cls_rows<6>(var);
-    default: return cls_rows<7>(var);
+    case 7: return cls_rows<7>(var);
+    default: return cls_rows<8>(var);
   }
 }
 
@@ -50,7 +51,8 @@ int warps_per_cta(int cls, int var) {
     case 4: return cls_warps<4>(var);
     case 5: return cls_warps<5>(var);
     case 6: return cls_warps<6>(var);
-    default: return cls_warps<7>(var);
+    case 7: return cls_warps<7>(var);
+    default: return cls_warps<8>(var);
   }
 }
 

@@ -710,11 +710,13 @@ __global__ void __launch_bounds__(NW * 32, MINB) sinkhorn_fused_kernel(LoopParam
 // hiding), and wide queries use 8-warp CTAs so that a team of up to 8 warps
 // keeps a long document's K block resident.  Two lanes per row (no butterfly
 // before the reduce-scatter) pay off for 16-wide queries but not for 32-wide
-// ones (RMAX 6: 2.54 against 2.16 us per iteration).  The 96- and 192-wide
-// classes take the 128- and 256-wide tiles with 12 columns per lane instead
-// of 16 (the 96-wide one also as three 4-warp CTAs per SM, whose K block is
-// as large as the 64-wide class's).  The autotuner (wmd_autotune) picks one
-// per class and precision by timing.
+// ones (RMAX 6: 2.54 against 2.16 us per iteration).  The 48-, 96- and
+// 192-wide classes have 12 columns per lane (4, 8 and 16 lanes per row), so
+// that a query just above a power of two does not pay for a quarter of
+// padding columns; the 96-wide one also runs as three 4-warp CTAs per SM,
+// whose K block is as large as the 64-wide class's.  (A 24-wide tile, two
+// lanes per row, was slower than the 32-wide one for 19-word queries.)  The autotuner (wmd_autotune) picks one per class and
+// precision by timing.
 template <int CLS, int V> struct Var;
 template <> struct Var<0, 0> { static constexpr int VR = 8, PI = 2, RMAX = 12, MINB = 4, NW = 4; };
 template <> struct Var<0, 1> { static constexpr int VR = 8, PI = 2, RMAX = 24, MINB = 2, NW = 4; };
@@ -722,16 +724,18 @@ template <> struct Var<1, 0> { static constexpr int VR = 16, PI = 4, RMAX = 24, 
 template <> struct Var<1, 1> { static constexpr int VR = 16, PI = 2, RMAX = 12, MINB = 3, NW = 4; };
 template <> struct Var<2, 0> { static constexpr int VR = 32, PI = 4, RMAX = 12, MINB = 3, NW = 4; };
 template <> struct Var<2, 1> { static constexpr int VR = 32, PI = 4, RMAX = 8, MINB = 4, NW = 4; };
-template <> struct Var<3, 0> { static constexpr int VR = 64, PI = 8, RMAX = 12, MINB = 3, NW = 4; };
-template <> struct Var<3, 1> { static constexpr int VR = 64, PI = 8, RMAX = 8, MINB = 4, NW = 4; };
-template <> struct Var<4, 0> { static constexpr int VR = 96, PI = 8, RMAX = 8, MINB = 1, NW = 8; };
-template <> struct Var<4, 1> { static constexpr int VR = 96, PI = 8, RMAX = 8, MINB = 3, NW = 4; };
-template <> struct Var<5, 0> { static constexpr int VR = 128, PI = 8, RMAX = 8, MINB = 1, NW = 8; };
-template <> struct Var<5, 1> { static constexpr int VR = 128, PI = 8, RMAX = 8, MINB = 2, NW = 4; };
-template <> struct Var<6, 0> { static constexpr int VR = 192, PI = 16, RMAX = 8, MINB = 1, NW = 8; };
-template <> struct Var<6, 1> { static constexpr int VR = 192, PI = 16, RMAX = 8, MINB = 2, NW = 4; };
-template <> struct Var<7, 0> { static constexpr int VR = 256, PI = 16, RMAX = 8, MINB = 1, NW = 8; };
-template <> struct Var<7, 1> { static constexpr int VR = 256, PI = 16, RMAX = 8, MINB = 2, NW = 4; };
+template <> struct Var<3, 0> { static constexpr int VR = 48, PI = 4, RMAX = 8, MINB = 3, NW = 4; };
+template <> struct Var<3, 1> { static constexpr int VR = 48, PI = 4, RMAX = 4, MINB = 4, NW = 4; };
+template <> struct Var<4, 0> { static constexpr int VR = 64, PI = 8, RMAX = 12, MINB = 3, NW = 4; };
+template <> struct Var<4, 1> { static constexpr int VR = 64, PI = 8, RMAX = 8, MINB = 4, NW = 4; };
+template <> struct Var<5, 0> { static constexpr int VR = 96, PI = 8, RMAX = 8, MINB = 1, NW = 8; };
+template <> struct Var<5, 1> { static constexpr int VR = 96, PI = 8, RMAX = 8, MINB = 3, NW = 4; };
+template <> struct Var<6, 0> { static constexpr int VR = 128, PI = 8, RMAX = 8, MINB = 1, NW = 8; };
+template <> struct Var<6, 1> { static constexpr int VR = 128, PI = 8, RMAX = 8, MINB = 2, NW = 4; };
+template <> struct Var<7, 0> { static constexpr int VR = 192, PI = 16, RMAX = 8, MINB = 1, NW = 8; };
+template <> struct Var<7, 1> { static constexpr int VR = 192, PI = 16, RMAX = 8, MINB = 2, NW = 4; };
+template <> struct Var<8, 0> { static constexpr int VR = 256, PI = 16, RMAX = 8, MINB = 1, NW = 8; };
+template <> struct Var<8, 1> { static constexpr int VR = 256, PI = 16, RMAX = 8, MINB = 2, NW = 4; };
 
 template <int CLS, int V, bool CONV, typename KT>
 cudaError_t launch_var(const LoopParams& p, int n_items, int nq, cudaStream_t s) {
@@ -790,7 +794,8 @@ cudaError_t dispatch_loop(int cls, int var, const LoopParams& p, int n_items, in
     case 4: return launch_cls<4, CONV, KT>(var, p, n_items, nq, s);
     case 5: return launch_cls<5, CONV, KT>(var, p, n_items, nq, s);
     case 6: return launch_cls<6, CONV, KT>(var, p, n_items, nq, s);
-    default: return launch_cls<7, CONV, KT>(var, p, n_items, nq, s);
+    case 7: return launch_cls<7, CONV, KT>(var, p, n_items, nq, s);
+    default: return launch_cls<8, CONV, KT>(var, p, n_items, nq, s);
   }
 }
 

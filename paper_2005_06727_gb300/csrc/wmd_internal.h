@@ -39,11 +39,11 @@ wmd_status cuda_error(cudaError_t e, const char* what);
 // The fused loop pads the query to one of these widths (its register tile,
 // kClassVR); the cdist kernel, K and the workspace use the power of two at or
 // above it (kClassKVR: K rows have that many entries, and the loop reads the
-// first kClassVR of them).  The 96- and 192-wide tiles save a quarter of the
-// loop's work for queries just above 64 and 128 words.
-constexpr int kNumClasses = 8;
-constexpr int kClassVR[kNumClasses] = {8, 16, 32, 64, 96, 128, 192, 256};
-constexpr int kClassKVR[kNumClasses] = {8, 16, 32, 64, 128, 128, 256, 256};
+// first kClassVR of them).  The 48-, 96- and 192-wide tiles save a quarter
+// of the loop's work for queries just above 32, 64 and 128 words.
+constexpr int kNumClasses = 9;
+constexpr int kClassVR[kNumClasses] = {8, 16, 32, 48, 64, 96, 128, 192, 256};
+constexpr int kClassKVR[kNumClasses] = {8, 16, 32, 64, 64, 128, 128, 256, 256};
 
 inline int vr_class(int v_r) {
   for (int c = 0; c < kNumClasses; ++c)
@@ -61,7 +61,7 @@ inline int class_of_width(int width) {
 // Fused-loop tile variants per class (sinkhorn.cu) and the rows one warp of
 // variant `var` keeps in registers (row groups x rows per lane).
 constexpr int kMaxVariants = 2;
-constexpr int kClassVariants[kNumClasses] = {2, 2, 2, 2, 2, 2, 2, 2};
+constexpr int kClassVariants[kNumClasses] = {2, 2, 2, 2, 2, 2, 2, 2, 2};
 int rows_per_warp(int cls, int var);
 int warps_per_cta(int cls, int var);  // 4 or 8
 

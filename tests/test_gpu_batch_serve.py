@@ -29,7 +29,8 @@ def setup(wmd):
     c = synth.make_corpus(V, N, 5, 80, 102)
     corpus = wmd.Corpus.from_synth(vecs, c)
     rng = np.random.default_rng(7)
-    widths = [1, 3, 8, 9, 16, 17, 30, 32, 33, 64, 65, 100, 128, 129, 200, 256, 80, 96, 97, 150, 192, 193]
+    widths = [1, 3, 8, 9, 16, 17, 30, 32, 33, 64, 65, 100, 128, 129, 200, 256, 80, 96, 97, 150, 192, 193,
+              20, 40, 48, 49]
     queries = [synth.make_query(V, int(vr), 300 + i) for i, vr in enumerate(widths)]
     queries += [synth.make_query(V, int(rng.integers(5, 129)), 400 + i) for i in range(12)]
     return vecs, c, corpus, queries
@@ -95,7 +96,7 @@ def test_query_into_pinned_output_buffers(wmd, setup):
 
 def test_batch_against_oracle(wmd, setup):
     vecs, c, corpus, queries = setup
-    sel = [0, 6, 11, 15, 17, 19, 20, 24]  # v_r 1, 30, 100, 256, 96, 150, 192 and a random one
+    sel = [0, 6, 11, 15, 17, 19, 20, 23, 24, 28]  # v_r 1, 30, 100, 256, 96, 150, 192, 40, 48, random
     got = corpus.query_batch([queries[i] for i in sel], 10.0, 15)
     for row, i in enumerate(sel):
         want = orc.sinkhorn_wmd_sparse(queries[i][0], queries[i][1], c.row_ptr, c.doc_idx, c.val,

@@ -120,6 +120,7 @@ def test_paper_shaped_sampled_documents(wmd):
     (30, [1, 2, 0, 95, 97, 193, 700]),            # shared-memory finish; 1, 2, 4 warps
     (64, [47, 49, 97, 200, 400]),                 # register finish; teams of warps
     (200, [5, 13, 49, 300, 0]),                   # 8-warp CTAs
+    (40, [3, 65, 129, 257, 0]),                   # 48-wide tile
     (90, [5, 33, 65, 129, 257, 0]),               # 96-wide tile
     (150, [5, 17, 33, 65, 129, 0]),               # 192-wide tile
 ])

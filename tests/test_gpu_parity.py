@@ -117,8 +117,8 @@ def test_large_workload_sampled_documents(wmd):
 
 
 # ---------------------------------------------------------------- query widths and document shapes
-@pytest.mark.parametrize("v_r", [1, 2, 7, 8, 9, 16, 17, 31, 32, 33, 64, 65, 96, 97, 100, 128, 129, 192,
-                                 193, 200, 256])
+@pytest.mark.parametrize("v_r", [1, 2, 7, 8, 9, 16, 17, 31, 32, 33, 48, 49, 64, 65, 96, 97, 100, 128,
+                                 129, 192, 193, 200, 256])
 def test_query_widths(wmd, v_r):
     """Every padded width class, ragged widths on both sides of each boundary."""
     V, N = 3000, 61
@@ -137,6 +137,7 @@ def test_query_widths(wmd, v_r):
     (64, [47, 48, 49, 96, 97, 200, 400]),
     (8, [383, 384, 385, 1000]),
     (200, [5, 12, 13, 48, 49, 300]),
+    (40, [3, 63, 64, 65, 128, 129, 256, 257, 400]),        # 48-wide tile
     (90, [5, 32, 33, 64, 65, 128, 129, 256, 257, 300]),    # 96-wide tile: 1-8 warps, chunked
     (150, [5, 16, 17, 32, 33, 64, 65, 128, 129, 200]),     # 192-wide tile
 ])
@@ -385,7 +386,7 @@ def test_paper_shaped_with_both_cdist_kernels(wmd, monkeypatch, kernel):
 
 
 # ---------------------------------------------------------------- fused-loop tile variants
-@pytest.mark.parametrize("v_r", [6, 16, 30, 64, 80, 100, 150, 200])
+@pytest.mark.parametrize("v_r", [6, 16, 30, 40, 64, 80, 100, 150, 200])
 def test_every_loop_variant_matches_oracle(wmd, v_r):
     """Each register-tile variant of each width class gives the oracle's
     values (documents long enough for teams of 1, 2 and 4 warps and for the
@@ -419,7 +420,7 @@ def test_every_loop_variant_matches_oracle(wmd, v_r):
 
 
 # ---------------------------------------------------------------- partitions (team sizes)
-@pytest.mark.parametrize("v_r", [6, 30, 64, 80, 100, 150, 200])
+@pytest.mark.parametrize("v_r", [6, 30, 40, 64, 80, 100, 150, 200])
 def test_every_partition_matches_oracle(wmd, v_r):
     """Every partition of the documents into teams (fill 50, 75, 100, 200:
     spread over more warps, the default, or long documents re-read from L2
