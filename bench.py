@@ -349,19 +349,16 @@ def run_reference(args, w):
 
 
 # ------------------------------------------------------------------ batched and served
-# the fused loop's query-width classes (the width of its register tile)
-LOOP_CLASS_WIDTHS = (8, 16, 32, 48, 64, 96, 128, 192, 256)
-
-
 def autotune_classes(corpus, qs, w):
-    """Autotune every width class that one of the queries qs falls in (with
-    the first such query), untimed."""
-    lo = 0
-    for vr in LOOP_CLASS_WIDTHS:
-        q = next((q for q in qs if lo < len(q[0]) <= vr), None)
-        if q is not None:
+    """Autotune every width class of the fused loop that one of the queries
+    qs falls in (with the first such query), untimed."""
+    from paper_2005_06727_gb300 import wmd as _w
+    seen = set()
+    for q in qs:
+        width = _w.loop_width(len(q[0]))
+        if width not in seen:
+            seen.add(width)
             corpus.autotune(q[0], q[1], w.lam, w.max_iter)
-        lo = vr
 
 
 def bench_batched(wmd, device, reps=2, with_oracle=True):

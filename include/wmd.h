@@ -412,9 +412,12 @@ wmd_status wmd_query_dense(wmd_corpus* corpus, const int32_t* d_q_ids, const flo
  * class (v_r rounded up to 8, 16, 32, 48, 64, 96, 128, 192 or 256: the
  * width of the loop's register tile; K itself is computed for v_r rounded up
  * to a power of two, and the 48-, 96- and 192-wide tiles read the first
- * columns of it) has one or more register-tile shapes for the fused SDDMM/SpMM loop
- * (same arithmetic, same results within rounding); they trade work per
- * cross-lane reduction against resident warps.  wmd_loop_variant_count: how many exist for queries of v_r
+ * columns of it) has one or more register-tile shapes for the fused
+ * SDDMM/SpMM loop (same arithmetic, same results within rounding); they trade
+ * work per cross-lane reduction against resident warps.  wmd_loop_width: the
+ * class's tile width for queries of v_r words (the columns every SDDMM and
+ * SpMM works on; 0 for v_r outside [1, WMD_MAX_VR]); host only, needs no GPU.
+ * wmd_loop_variant_count: how many tile variants exist for queries of v_r
  * words.  wmd_set_loop_variant: use `variant` for v_r's class and `prec` on
  * this corpus (all later calls; not thread-safe against running queries).
  * wmd_get_loop_variant: the variant in use for v_r's class and `prec` (-1
@@ -447,6 +450,7 @@ wmd_status wmd_query_dense(wmd_corpus* corpus, const int32_t* d_q_ids, const flo
  * is appended to the cache file, and corpora of the same shape loaded later
  * start from it.
  * ------------------------------------------------------------------------- */
+int32_t wmd_loop_width(int32_t v_r);
 int32_t wmd_loop_variant_count(int32_t v_r);
 wmd_status wmd_set_loop_variant(wmd_corpus* corpus, int32_t v_r, wmd_precision prec,
                                 int32_t variant);

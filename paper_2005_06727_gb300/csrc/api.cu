@@ -700,6 +700,11 @@ wmd_status wmd_query_device_topk(wmd_corpus* c, const int32_t* d_q_ids, const fl
   return wmd_topk(d_out, c->N, k, d_idx, d_val, stream);
 }
 
+int32_t wmd_loop_width(int32_t v_r) {
+  const int cls = v_r > 0 && v_r <= WMD_MAX_VR ? vr_class(v_r) : -1;
+  return cls >= 0 ? kClassVR[cls] : 0;
+}
+
 int32_t wmd_loop_variant_count(int32_t v_r) {
   const int cls = vr_class(v_r);
   return v_r > 0 && cls >= 0 ? kClassVariants[cls] : 0;

@@ -110,6 +110,7 @@ _SIGS = {
     "wmd_query_device_noalloc": (C.c_int, [_P, _P, _P, C.c_int32, C.c_float, C.c_int32, C.c_int,
                                            _P, _P]),
     "wmd_query_batch": (C.c_int, [_P, C.c_int32, _P, _P, _P, _P, C.c_int32, C.c_int, _P]),
+    "wmd_loop_width": (C.c_int32, [C.c_int32]),
     "wmd_loop_variant_count": (C.c_int32, [C.c_int32]),
     "wmd_set_loop_variant": (C.c_int, [_P, C.c_int32, C.c_int, C.c_int32]),
     "wmd_get_loop_variant": (C.c_int32, [_P, C.c_int32, C.c_int]),
@@ -173,6 +174,11 @@ def measure_fp32_peak(device: int = 0, packed: bool = True) -> float:
     out = C.c_double(0.0)
     _check(lib().wmd_measure_fp32_peak(int(device), 1 if packed else 0, C.byref(out)))
     return float(out.value)
+
+
+def loop_width(v_r: int) -> int:
+    """``wmd_loop_width``: the fused loop's tile width for v_r query words."""
+    return int(lib().wmd_loop_width(int(v_r)))
 
 
 def loop_variant_count(v_r: int) -> int:

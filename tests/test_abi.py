@@ -154,3 +154,17 @@ def test_measure_fp32_peak_rejects_null_output(lib):
 def test_partition_entry_points_on_null_corpus(lib):
     assert lib.wmd_get_loop_partition(None, 30, 0) == -1
     assert lib.wmd_set_loop_partition(None, 30, 0, 100) == wmd.WMD_ERR_INVALID_ARG
+
+
+def test_loop_width_classes(lib):
+    """wmd_loop_width (host only): v_r rounded up to the tile widths 8, 16,
+    32, 48, 64, 96, 128, 192, 256, and 0 outside [1, WMD_MAX_VR]."""
+    widths = (8, 16, 32, 48, 64, 96, 128, 192, 256)
+    lo = 0
+    for w in widths:
+        for v_r in (lo + 1, (lo + 1 + w) // 2, w):
+            assert wmd.loop_width(v_r) == w, (v_r, w)
+        lo = w
+    assert sorted({wmd.loop_width(v) for v in range(1, 257)}) == list(widths)
+    assert wmd.loop_width(0) == 0 and wmd.loop_width(-3) == 0 and wmd.loop_width(257) == 0
+    assert all(wmd.loop_variant_count(v) >= 1 for v in (1, 48, 49, 96, 97, 192, 193, 256))
